@@ -1,0 +1,122 @@
+"""The outer subspace iteration of ChASE for pseudo-hermitian H (oracle; test infrastructure).
+
+Algorithm 3 (Section 4), step by step:
+
+ 1. W_+ <- randn(2n, nevex); its lower half is scaled by gamma = 1e-3 so the
+    search space starts on the S-positive side (Section 4.6).
+ 2. mu_1, mu_nevex, mu_N from pseudo-hermitian Lanczos (Section 4.1).
+ 3. while locked < nev:
+    a. W_+ <- p(H^2) W_+                      (Section 4.2)
+    b. W_- <- K conj(W_+)                     (Theorem relation_polynomial)
+    c. Q <- [S Y_+, S Y_-, W_+, W_-] R^{-1}    (Section 4.3), keep Q[:, 2 locked:]
+    d. Ritz values and W_+ = Q Z_+             (Algorithm 2)
+    e. residuals of the positive half          (Section 4.5)
+    f. lock converged positive pairs, Y_- = K conj(Y_+)
+
+Readings where the paper is silent (the same ones the CUDA driver follows):
+
+* residual r_i = ||H w_i - lambda_i w_i||_2 / rho_hat with ||w_i|| = 1 and
+  rho_hat = max |theta| of the Lanczos Ritz values (no beta padding);
+* lock every i among the first (nev - locked) active pairs (ascending lambda)
+  with r_i <= tol;
+* after locking, mu_nevex <- largest non-locked positive Ritz value
+  (Section 4.1) and mu_1 <- min(mu_1, lambda_1);
+* per-vector degree (Section 6 cites a formula not available here):
+  t_i = (lambda_i^2 - c)/e, rho_i = 1/(|t_i| + sqrt(t_i^2 - 1)) (1 when
+  |t_i| <= 1), deg_i = clamp(ceil(ln(tol/r_i)/ln(rho_i)) + 1, deg_min, deg_max);
+  the first iteration uses ``deg`` for every column.
+"""
+from __future__ import annotations
+
+import math
+import numpy as np
+
+from .chebyshev import chebyshev_filter, coefficients
+from .dense import fix_phase
+from .lanczos import spectral_bounds, lanczos_tridiagonal, ritz_and_weights
+from .qr import cholesky_qr2
+from .rayleigh_ritz import rayleigh_ritz, residuals
+
+GAMMA = 1e-3
+
+
+def k_conj(W: np.ndarray) -> np.ndarray:
+    """K conj(W) with K = [[0, I], [I, 0]]."""
+    n = W.shape[0] // 2
+    return np.concatenate([W[n:].conj(), W[:n].conj()], axis=0)
+
+
+def s_flip(W: np.ndarray) -> np.ndarray:
+    """S W with S = diag(I, -I)."""
+    n = W.shape[0] // 2
+    return np.concatenate([W[:n], -W[n:]], axis=0)
+
+
+def rho_hat(A, B, starts, steps):
+    """max |theta| over the Lanczos runs (no beta padding)."""
+    m = 0.0
+    for v0 in starts:
+        al, be = lanczos_tridiagonal(A, B, np.asarray(v0, dtype=np.complex128), steps)
+        th, _ = ritz_and_weights(al, be)
+        m = max(m, float(np.abs(th).max()))
+    return m
+
+
+def degrees(ritz, res, tol, mu1, mu_nevex, muN, deg_min, deg_max):
+    c, e, _ = coefficients(mu1, mu_nevex, muN)
+    out = np.empty(len(ritz), dtype=int)
+    for i, (lam, r) in enumerate(zip(ritz, res)):
+        t = (lam * lam - c) / e
+        if abs(t) <= 1.0 or r <= 0.0:
+            d = deg_max if r > tol else deg_min
+        else:
+            rho = 1.0 / (abs(t) + math.sqrt(t * t - 1.0))
+            d = math.ceil(math.log(tol / r) / math.log(rho)) + 1 if r > tol else deg_min
+        out[i] = min(max(d, deg_min), deg_max)
+    return out
+
+
+def solve(A, B, nev, nex, deg, tol, W0raw, starts, lanczos_steps=26, deg_min=None,
+          deg_max=None, maxiter=25):
+    """Returns dict(lam[nev], V[2n, nev], iterations, history, mu)."""
+    n = A.shape[0]
+    nevex = nev + nex
+    deg_min = deg if deg_min is None else deg_min
+    deg_max = deg if deg_max is None else deg_max
+    W = np.array(W0raw, dtype=np.complex128).T.copy()   # (2n, nevex)
+    W[n:, :] *= GAMMA
+    mu1, mu_nevex, muN = spectral_bounds(A, B, starts, lanczos_steps, nevex)
+    rhat = rho_hat(A, B, starts, lanczos_steps)
+    Yp = np.zeros((2 * n, 0), dtype=np.complex128)
+    lam_locked = np.zeros(0)
+    degs = np.full(nevex, deg, dtype=int)
+    history = []
+    it = 0
+    while Yp.shape[1] < nev and it < maxiter:
+        it += 1
+        locked = Yp.shape[1]
+        Wf = chebyshev_filter(A, B, W, degs, mu1, mu_nevex, muN)
+        X = np.concatenate([s_flip(Yp), s_flip(k_conj(Yp)), Wf, k_conj(Wf)], axis=1)
+        Q, used_hh = cholesky_qr2(X)
+        Q = Q[:, 2 * locked:]
+        ritz, Wpos = rayleigh_ritz(A, B, Q)
+        res = residuals(A, B, Wpos, ritz) / rhat
+        history.append(dict(ritz=ritz.copy(), res=res.copy(), degs=degs.copy(),
+                            locked=locked, householder=used_hh,
+                            mu=(mu1, mu_nevex, muN)))
+        want = min(nev - locked, len(ritz))
+        conv = [i for i in range(want) if res[i] <= tol]
+        keep = [i for i in range(len(ritz)) if i not in set(conv)]
+        if conv:
+            Yp = np.concatenate([Yp, Wpos[:, conv]], axis=1)
+            lam_locked = np.concatenate([lam_locked, ritz[conv]])
+        W = Wpos[:, keep]
+        if Yp.shape[1] >= nev or not keep:
+            break
+        mu_nevex = float(ritz[keep].max())
+        mu1 = min(mu1, float(ritz[0]))
+        degs = degrees(ritz[keep], res[keep], tol, mu1, mu_nevex, muN, deg_min, deg_max)
+    order = np.argsort(lam_locked)[:nev]
+    V = fix_phase(Yp[:, order]) if len(order) else Yp
+    return dict(lam=lam_locked[order], V=V, iterations=it, history=history,
+                mu=(mu1, mu_nevex, muN), converged=len(order))
