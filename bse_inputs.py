@@ -70,8 +70,9 @@ def spectrum(kind: str, n: int, rng: np.random.Generator) -> np.ndarray:
     """Planted eigenvalues d of A for the named distribution.
 
     - "uniform:lo:hi"  d ~ U[lo, hi]
-    - "groups8"        8 groups of n/8 values, group j ~ U[c_j, c_j + 0.25] with
-                       c_j = 1 + 38.75 j / 7 (clustered spectrum inside [1, 40])
+    - "groups8"        8 bands of n/8 values, band j ~ U[c_j, c_j + 4.375] with
+                       c_j = 1 + 4.875 j: a spectrum clustered in 8 groups on
+                       [1, 39.5], separated by gaps of 0.5
     - "gapband"        d ~ U[1, 50] with 5 % of the values replaced by U[1, 1.49]
                        (a dense band at the bottom of the positive spectrum)
     """
@@ -82,8 +83,8 @@ def spectrum(kind: str, n: int, rng: np.random.Generator) -> np.ndarray:
         d = np.empty(n)
         bounds = np.linspace(0, n, 9).astype(int)
         for j in range(8):
-            c = 1.0 + 38.75 * j / 7.0
-            d[bounds[j]:bounds[j + 1]] = rng.uniform(c, c + 0.25, size=bounds[j + 1] - bounds[j])
+            c = 1.0 + 4.875 * j
+            d[bounds[j]:bounds[j + 1]] = rng.uniform(c, c + 4.375, size=bounds[j + 1] - bounds[j])
         return d
     if kind == "gapband":
         d = rng.uniform(1.0, 50.0, size=n)

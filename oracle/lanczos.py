@@ -18,10 +18,14 @@ tau_j are the weights of the spectral density of v (Lin, Saad & Yang, SIAM Rev.
 * mu_1     = min |theta| over all start vectors
 * mu_N     = max |theta| + |beta_last| (upper bound after Zhou, Linear Algebra
              Appl. 435, 2011)
-* mu_nevex = positive-axis quantile: the weights of the theta > 0 are averaged
-             over the start vectors and renormalised; the cumulative weight is
-             linearly interpolated between (mu_1, 0) and the successive
-             (theta_j, C_j), and mu_nevex is where it reaches nevex / n.
+* mu_nevex = positive-axis quantile of the density of eigenvalues.  In the
+             S H inner product the weight an eigenvalue lambda receives from a
+             random start vector is proportional to lambda times its share of
+             the start vector, so the counting density is recovered with the
+             weights tau_j / theta_j.  These are pooled over the start vectors
+             for theta > 0 and renormalised; the cumulative weight is linearly
+             interpolated between (mu_1, 0) and the successive (theta_j, C_j),
+             and mu_nevex is where it reaches nevex / n.
 """
 from __future__ import annotations
 
@@ -87,7 +91,7 @@ def spectral_bounds(A, B, starts, steps: int, nevex: int):
     muN = max(np.abs(th).max() + b for th, b in zip(thetas, betas))
     # positive-axis density, averaged over start vectors
     th_pos = np.concatenate([th[th > 0] for th in thetas])
-    w_pos = np.concatenate([ta[th > 0] for th, ta in zip(thetas, taus)])
+    w_pos = np.concatenate([ta[th > 0] / th[th > 0] for th, ta in zip(thetas, taus)])
     order = np.argsort(th_pos)
     th_pos = th_pos[order]
     w_pos = w_pos[order] / w_pos.sum()

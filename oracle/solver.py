@@ -20,11 +20,20 @@ Readings where the paper is silent (the same ones the CUDA driver follows):
 * lock every i among the first (nev - locked) active pairs (ascending lambda)
   with r_i <= tol;
 * after locking, mu_nevex <- largest non-locked positive Ritz value
-  (Section 4.1) and mu_1 <- min(mu_1, lambda_1);
-* per-vector degree (Section 6 cites a formula not available here):
-  t_i = (lambda_i^2 - c)/e, rho_i = 1/(|t_i| + sqrt(t_i^2 - 1)) (1 when
-  |t_i| <= 1), deg_i = clamp(ceil(ln(tol/r_i)/ln(rho_i)) + 1, deg_min, deg_max);
-  the first iteration uses ``deg`` for every column.
+  (Section 4.1) among those below mu_N: a Ritz value above the Lanczos upper
+  bound of the spectrum is spurious (Theorem field_of_values_ritz_hermitian_variant
+  and the remark after it) and is ignored; mu_1 <- min(mu_1, lambda_1);
+* mu_1 is only the normalisation point of the filter (p(mu_1^2) = 1) and must
+  stay below mu_nevex, otherwise it falls inside the damped interval where the
+  scaled recurrence divides by values of T_j near zero; mu_1 <- min(mu_1,
+  mu_nevex / 2) is applied after every update (a lower mu_1 only rescales);
+* per-vector degree from the convergence rate (Section 6 cites a formula not
+  available here): the predicted rate per H^2 step is
+  rho_i = 1/(|t_i| + sqrt(t_i^2 - 1)) with t_i = (lambda_i^2 - c)/e (1 when
+  |t_i| <= 1); once a column has a residual history, the observed rate
+  (r_i / r_i_prev)^(1/deg_i_prev) is used instead when it is slower; then
+  deg_i = clamp(ceil(ln(tol/r_i)/ln(rho_i)) + 1, deg_min, deg_max).  The first
+  iteration uses ``deg`` for every column.
 """
 from __future__ import annotations
 
@@ -62,16 +71,20 @@ def rho_hat(A, B, starts, steps):
     return m
 
 
-def degrees(ritz, res, tol, mu1, mu_nevex, muN, deg_min, deg_max):
+def degrees(ritz, res, tol, mu1, mu_nevex, muN, deg_min, deg_max, prev_res=None, prev_deg=None):
     c, e, _ = coefficients(mu1, mu_nevex, muN)
     out = np.empty(len(ritz), dtype=int)
     for i, (lam, r) in enumerate(zip(ritz, res)):
         t = (lam * lam - c) / e
-        if abs(t) <= 1.0 or r <= 0.0:
-            d = deg_max if r > tol else deg_min
+        rho = 1.0 if abs(t) <= 1.0 else 1.0 / (abs(t) + math.sqrt(t * t - 1.0))
+        if prev_res is not None and np.isfinite(prev_res[i]) and 0.0 < r < prev_res[i]:
+            rho = max(rho, (r / prev_res[i]) ** (1.0 / prev_deg[i]))
+        if r <= tol:
+            d = deg_min
+        elif rho >= 1.0:
+            d = deg_max
         else:
-            rho = 1.0 / (abs(t) + math.sqrt(t * t - 1.0))
-            d = math.ceil(math.log(tol / r) / math.log(rho)) + 1 if r > tol else deg_min
+            d = math.ceil(math.log(tol / r) / math.log(rho)) + 1
         out[i] = min(max(d, deg_min), deg_max)
     return out
 
@@ -86,10 +99,12 @@ def solve(A, B, nev, nex, deg, tol, W0raw, starts, lanczos_steps=26, deg_min=Non
     W = np.array(W0raw, dtype=np.complex128).T.copy()   # (2n, nevex)
     W[n:, :] *= GAMMA
     mu1, mu_nevex, muN = spectral_bounds(A, B, starts, lanczos_steps, nevex)
+    mu1 = min(mu1, 0.5 * mu_nevex)
     rhat = rho_hat(A, B, starts, lanczos_steps)
     Yp = np.zeros((2 * n, 0), dtype=np.complex128)
     lam_locked = np.zeros(0)
     degs = np.full(nevex, deg, dtype=int)
+    prev_res = np.full(nevex, np.inf)
     history = []
     it = 0
     while Yp.shape[1] < nev and it < maxiter:
@@ -113,9 +128,15 @@ def solve(A, B, nev, nex, deg, tol, W0raw, starts, lanczos_steps=26, deg_min=Non
         W = Wpos[:, keep]
         if Yp.shape[1] >= nev or not keep:
             break
-        mu_nevex = float(ritz[keep].max())
-        mu1 = min(mu1, float(ritz[0]))
-        degs = degrees(ritz[keep], res[keep], tol, mu1, mu_nevex, muN, deg_min, deg_max)
+        cand = ritz[keep][ritz[keep] < muN]
+        if len(cand):
+            mu_nevex = float(cand.max())
+        if ritz[0] > 0:
+            mu1 = min(mu1, float(ritz[0]))
+        mu1 = min(mu1, 0.5 * mu_nevex)
+        degs = degrees(ritz[keep], res[keep], tol, mu1, mu_nevex, muN, deg_min, deg_max,
+                       prev_res=prev_res[keep], prev_deg=degs[keep])
+        prev_res = res[keep]
     order = np.argsort(lam_locked)[:nev]
     V = fix_phase(Yp[:, order]) if len(order) else Yp
     return dict(lam=lam_locked[order], V=V, iterations=it, history=history,
