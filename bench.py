@@ -1,0 +1,364 @@
+#!/usr/bin/env python
+"""Benchmark: filter TFLOP/s and time to nev eigenpairs at tol 1e-10 on one GB300.
+
+One step = one full pass of the hot path on the synthetic workload: Lanczos
+bounds, the filtered subspace iteration (filter, CholeskyQR2, oblique
+Rayleigh-Ritz, residuals, locking, per-vector degrees) until nev pairs are
+locked, and the eigenvalue-gradient backward of L = sum_i w_i lambda_i.
+
+Printed JSON line (rank 0):
+  value            filter TFLOP/s over the timed steps (algorithmic flops
+                   64 n^2 sum_i deg_i of the filter / device time in the filter)
+  time_to_solution seconds per step (device events, mean over the steps)
+  e2e              the same metric through the Python/C-ABI entry points with
+                   host buffers, host<->device copies inside the timed region
+  roofline         the dominant kernel (the filter GEMM) against the measured peak
+  cpu_baseline     the CPU oracle (a bounded sample) on the host cores
+
+Under torchrun (N > 1) every rank solves its own independent problem instance
+(replicas: the method has no data-path exchange on one problem per GPU).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "filter TFLOP/s + time to nev eigenpairs at tol=1e-10, mixed vs FP64 on 1 GB300"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+# nominal dense rates (TFLOP/s) used to scale a measured bf16 peak to another dtype
+NOMINAL = {"bf16": 2250.0, "fp64": 1.25}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=2)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="n4096")
+    p.add_argument("--precision", default="auto", choices=["auto", "fp64", "mixed"])
+    p.add_argument("--no-fp64-compare", action="store_true")
+    p.add_argument("--e2e-steps", type=int, default=None)
+    return p.parse_args()
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return dict(PEAKS_FALLBACK), "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def make_inputs(wl: dict, seed: int):
+    import bse_inputs as bi
+    P = bi.make_problem(wl["n"], seed=seed, spec=wl["spec"], beta=wl["beta"])
+    nevex = wl["nev"] + wl["nex"]
+    W0 = bi.start_block(wl["n"], nevex, seed)
+    V0 = bi.lanczos_starts(wl["n"], 4, seed)
+    w = bi.loss_weights(wl["nev"], seed)
+    return P, W0, V0, w
+
+
+def cpu_oracle_sample(P, W0, wl):
+    """The oracle as it stands: one H^2 step of its Chebyshev filter (degree 1)
+    over all nev + nex columns, timed on the host cores."""
+    import numpy as np
+    from oracle import chebyshev, dense
+    n = wl["n"]
+    k = W0.shape[0]
+    lam_guess = (0.9, 2.0, 60.0)
+    t0 = time.perf_counter()
+    chebyshev.chebyshev_filter(P.A, P.B, W0.T, np.ones(k, dtype=int), *lam_guess)
+    dt = time.perf_counter() - t0
+    flops = 64.0 * n * n * k
+    return {"value": flops / dt / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"one H^2 step (degree 1) of the oracle filter, n={n}, k={k} columns, "
+                      f"{dt:.2f} s incl. forming H; the metric's unit scaled by 64 n^2 k flops"}
+
+
+def run_reference(args, wl, rank, world):
+    if rank != 0:
+        return
+    import numpy as np
+    P, W0, V0, w = make_inputs(wl, 0)
+    steps, warm = max(args.steps, 1), max(args.warmup, 0)
+    samples = []
+    for i in range(warm + steps):
+        s = cpu_oracle_sample(P, W0, wl)
+        if i >= warm:
+            samples.append(s["value"])
+    v = float(np.mean(samples))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "TFLOP/s", "n_gpus": args.gpus,
+            "steps": steps, "warmup": warm, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "n": wl["n"], "nev": wl["nev"], "nex": wl["nex"]},
+            "cpu_baseline": {"value": v, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": "per step: one H^2 step (degree 1) of the oracle filter over nev+nex "
+                                       "columns of the same workload"},
+            "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    import bse_inputs as bi
+    wl = dict(bi.WORKLOADS[args.workload])
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, wl, rank, world)
+        return
+
+    import numpy as np
+    import torch
+    import paper_2601_10557_gb300 as pkg
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    precision = args.precision
+    if precision == "auto":
+        precision = "mixed" if pkg.has_mixed() else "fp64"
+    n, nev, nex = wl["n"], wl["nev"], wl["nex"]
+    nevex = nev + nex
+    P, W0n, V0n, wn = make_inputs(wl, rank)
+    A = torch.from_numpy(P.A).to(dev)
+    B = torch.from_numpy(P.B).to(dev)
+    W0 = torch.from_numpy(W0n).to(dev)
+    V0 = torch.from_numpy(V0n).to(dev)
+    w = torch.from_numpy(wn).to(dev)
+    kw = dict(W0=W0, V0=V0, deg_min=wl["deg_min"], deg_max=wl["deg_max"], maxiter=40)
+
+    def step(prec):
+        lam, V, st = pkg.solve(A, B, nev, nex, wl["deg"], wl["tol"], precision=prec, **kw)
+        gA, gB = pkg.grad(V, w)
+        return lam, V, st, gA, gB
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(max(args.warmup, 3)):
+        step(precision)
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    l0 = pkg.launch_count()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    fl = fms = 0.0
+    iters = []
+    maxres = 0.0
+    for _ in range(args.steps):
+        lam, V, st, gA, gB = step(precision)
+        fl += st["filter_flops"]
+        fms += st["ms_filter"]
+        iters.append(st["iterations"])
+        maxres = max(maxres, st["max_residual"])
+    ev1.record(stream)
+    barrier()
+    clocks.stop()
+    launches = pkg.launch_count() - l0
+    total_ms = ev0.elapsed_time(ev1)
+    tts = total_ms / 1e3 / args.steps
+
+    def reduce_max(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def reduce_sum(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+
+    fms_max = reduce_max(fms)
+    fl_sum = reduce_sum(fl)
+    value = fl_sum / (fms_max / 1e3) / 1e12
+    tts_max = reduce_max(tts)
+
+    # correctness of the timed result against cheap oracle-side properties
+    lam_np = lam.cpu().numpy()
+
+    # ---- e2e through the public API with host buffers
+    e2e_steps = args.e2e_steps if args.e2e_steps is not None else args.steps
+    hA = torch.from_numpy(P.A).pin_memory()
+    hB = torch.from_numpy(P.B).pin_memory()
+    hW0 = torch.from_numpy(W0n).pin_memory()
+    hV0 = torch.from_numpy(V0n).pin_memory()
+    hw = torch.from_numpy(wn).pin_memory()
+    out_l = torch.empty(nev, dtype=torch.float64).pin_memory()
+    out_gA = torch.empty((n, n), dtype=torch.complex128).pin_memory()
+    out_gB = torch.empty((n, n), dtype=torch.complex128).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in (hA, hB, hW0, hV0, hw))
+    d2h = sum(t.numel() * t.element_size() for t in (out_l, out_gA, out_gB))
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    efl = 0.0
+    for _ in range(max(e2e_steps, 1)):
+        dA = hA.to(dev, non_blocking=True)
+        dB = hB.to(dev, non_blocking=True)
+        dW = hW0.to(dev, non_blocking=True)
+        dV = hV0.to(dev, non_blocking=True)
+        dw = hw.to(dev, non_blocking=True)
+        lam2, V2, st2 = pkg.solve(dA, dB, nev, nex, wl["deg"], wl["tol"], precision=precision, W0=dW, V0=dV,
+                                  deg_min=wl["deg_min"], deg_max=wl["deg_max"], maxiter=40)
+        g2A, g2B = pkg.grad(V2, dw)
+        out_l.copy_(lam2, non_blocking=True)
+        out_gA.copy_(g2A, non_blocking=True)
+        out_gB.copy_(g2B, non_blocking=True)
+        efl += st2["filter_flops"]
+    e1.record(stream)
+    barrier()
+    e2e_ms = reduce_max(e0.elapsed_time(e1))
+    e2e_val = reduce_sum(efl) / (e2e_ms / 1e3) / 1e12
+
+    # ---- roofline of the dominant kernel: one filter call at the workload's size
+    deg_r = wl["deg"]
+    Wr = W0.clone()
+    pkg.filter(A, B, Wr, [deg_r] * nevex, 1.0, 2.0, 60.0, precision=precision)  # warm
+    barrier()
+    r0 = torch.cuda.Event(enable_timing=True)
+    r1 = torch.cuda.Event(enable_timing=True)
+    rl0 = pkg.launch_count()
+    r0.record(stream)
+    pkg.filter(A, B, Wr, [deg_r] * nevex, 1.0, 2.0, 60.0, precision=precision)
+    r1.record(stream)
+    torch.cuda.synchronize()
+    rl = pkg.launch_count() - rl0
+    gemm_launches = 2 * deg_r
+    per_launch_ms = r0.elapsed_time(r1) / gemm_launches
+    flops_per_launch = 32.0 * n * n * nevex
+    achieved = flops_per_launch / (per_launch_ms / 1e3) / 1e12
+    peaks, peak_src = load_peaks()
+    if precision == "fp64":
+        peak = peaks["bf16_tflops"] * NOMINAL["fp64"] / NOMINAL["bf16"]
+        peak_note = f"{peak_src} bf16 burst x nominal fp64/bf16 ratio (1.25/2250)"
+    else:
+        peak = peaks["bf16_tflops"] / 3.0
+        peak_note = f"{peak_src} bf16 burst / 3 (three BF16 products per FP32-accurate product)"
+    roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "hop_kernel (FP64 DFMA)" if precision == "fp64" else "tc_filter_gemm",
+            "peak_source": peak_note, "launches_timed": gemm_launches, "all_launches": rl,
+            "flops_per_launch": flops_per_launch}
+
+    # ---- FP64 comparison solve (time to solution)
+    fp64_tts = None
+    if precision != "fp64" and not args.no_fp64_compare:
+        barrier()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        step("fp64")
+        f1.record(stream)
+        barrier()
+        fp64_tts = reduce_max(f0.elapsed_time(f1) / 1e3)
+
+    cpu = None
+    if rank == 0 and world == 1:
+        cpu = cpu_oracle_sample(P, W0n, wl)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": tts_max * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if precision == "fp64" else "bf16x3+f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "n": n, "H": 2 * n, "nev": nev, "nex": nex,
+                       "deg": f"{wl['deg_min']}-{wl['deg_max']} adaptive, first {wl['deg']}", "tol": wl["tol"],
+                       "spectrum": wl["spec"], "beta": wl["beta"], "precision": precision,
+                       "l2": "inputs larger than L2 (A and B: %.0f MB)" % (2 * n * n * 16 / 1e6),
+                       "parallelism": f"replicas x{world}"},
+            "time_to_solution_s": tts_max,
+            "time_to_solution_fp64_s": fp64_tts if precision != "fp64" else tts_max,
+            "iterations": iters, "max_residual": maxres,
+            "lambda_min_max": [float(lam_np[0]), float(lam_np[-1])],
+            "e2e": {"value": e2e_val, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "ms_per_step": e2e_ms / max(e2e_steps, 1)},
+            "gpu_launches": launches,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "clocks": clocks.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,174 @@
+/*
+ * chase_bse.h -- C ABI of a GB300 (sm_103a) implementation of ChASE for
+ * pseudo-hermitian Bethe-Salpeter Hamiltonians (arXiv 2601.10557).
+ *
+ * Problem (Section 1, eq. introduction::hamiltonian_definition):
+ *     H = [[A, B], [-conj(B), -conj(A)]],  A = A^* (n x n),  B = B^T (n x n),
+ * with S H = [[A, B], [conj(B), conj(A)]] hermitian positive definite
+ * (eq. introduction::quasi_hermitian_condition).  The library computes the nev
+ * smallest positive eigenvalues of H and their right eigenvectors with the
+ * Chebyshev-filtered subspace iteration of Algorithm 3.  H is never formed:
+ * every product with H reads only the stored A and B.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Complex numbers are complex128: two interleaved doubles (re, im).
+ * - A and B are n x n, stored ROW-MAJOR (element (i, j) at offset i*n + j).
+ *   Because A is hermitian and B symmetric this is also the column-major
+ *   storage of conj(A) and of B.  Only A's hermitian part and B's symmetric
+ *   part are assumed; the library does not symmetrise.
+ * - Blocks of 2n-vectors (W, Q, V, ...) are 2n x k COLUMN-MAJOR with leading
+ *   dimension 2n: vector j occupies the 2n consecutive complex numbers starting
+ *   at offset j*2n (a torch tensor of shape (k, 2n)).
+ * - Pointers marked "device" must be CUDA device (or managed) memory on the
+ *   current device; the caller owns every buffer passed in.  Workspace is
+ *   allocated by the library with stream-ordered allocation on `stream` and
+ *   released before the call returns.
+ * - `stream` is a cudaStream_t (NULL = legacy default stream).  Entry points
+ *   that return results to host memory synchronise that stream.
+ * - Status codes: 0 OK; 1 NOT_CONVERGED (partial results are written); negative
+ *   values are errors (see chase_bse_status).  No C++ exception crosses the ABI.
+ *   chase_bse_strerror() turns a status into a static string.
+ */
+#ifndef CHASE_BSE_H
+#define CHASE_BSE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum chase_bse_status {
+  CHASE_BSE_OK = 0,
+  CHASE_BSE_NOT_CONVERGED = 1,   /* maxiter reached; stats->converged pairs valid      */
+  CHASE_BSE_BAD_ARG = -1,        /* invalid size, NULL pointer, bad option            */
+  CHASE_BSE_CUDA_ERROR = -2,     /* a CUDA runtime call or kernel launch failed       */
+  CHASE_BSE_OOM = -3,            /* workspace allocation failed                       */
+  CHASE_BSE_NOT_DEFINITE = -4,   /* Cholesky of Q^* S H Q failed: S H not HPD         */
+  CHASE_BSE_QR_FAILED = -5,      /* search space rank-deficient even for Householder  */
+  CHASE_BSE_DEVICE_TIMEOUT = -6, /* a bounded device-side wait gave up                */
+  CHASE_BSE_UNSUPPORTED = -7     /* feature needs a device this build cannot run on   */
+} chase_bse_status;
+
+typedef enum chase_bse_precision {
+  CHASE_BSE_FP64 = 0,         /* every product in FP64                                 */
+  CHASE_BSE_MIXED_BF16X3 = 1  /* filter products on tcgen05 tensor cores with BF16
+                                 hi/lo splits (3 products, FP32 accumulation);
+                                 everything else FP64; a column switches to the FP64
+                                 filter once its residual falls below switch_tol     */
+} chase_bse_precision;
+
+/* Options of chase_bse_solve.  Zero-initialise, set `size`, then override. */
+typedef struct chase_bse_opts {
+  uint32_t size;           /* sizeof(chase_bse_opts)                                  */
+  int32_t precision;       /* chase_bse_precision (default FP64)                      */
+  int32_t maxiter;         /* outer iterations (default 25, Section 6)                */
+  int32_t deg_min;         /* per-vector degree clamp (default: deg)                  */
+  int32_t deg_max;         /* (default: deg)                                          */
+  int32_t lanczos_steps;   /* even number of Lanczos steps (default 26, Section 4.1)  */
+  int32_t lanczos_vecs;    /* start vectors of the bound estimate (default 4, <= 64)  */
+  int32_t reserved0;
+  double gamma;            /* lower-half scale of the start block (default 1e-3,
+                              Section 4.6)                                            */
+  double switch_tol;       /* mixed mode: residual below which a column is filtered
+                              in FP64 (default 1e-5)                                  */
+  uint64_t seed;           /* counter-based generator seed when W0/V0 are NULL        */
+  const void* W0;          /* device, 2n x (nev+nex) raw start block, or NULL         */
+  const void* V0;          /* device, 2n x lanczos_vecs Lanczos start vectors, or NULL*/
+  void* stream;            /* cudaStream_t                                            */
+} chase_bse_opts;
+
+/* Statistics of chase_bse_solve (host struct, filled when non-NULL). */
+typedef struct chase_bse_stats {
+  uint32_t size;           /* sizeof(chase_bse_stats), set by the caller              */
+  int32_t iterations;
+  int32_t converged;       /* eigenpairs written                                      */
+  int32_t householder;     /* iterations that fell back to Householder QR            */
+  double mu1, mu_nevex, muN, rho_hat;   /* final filter bounds, residual scale       */
+  double ms_total, ms_lanczos, ms_filter, ms_qr, ms_rr, ms_resid;
+  double filter_flops;     /* algorithmic: sum over H^2 steps of 64 n^2 k_active    */
+  double filter_flops_fp64;/* the part run by the FP64 filter                        */
+  double ms_filter_fp64;   /* time of the FP64 filter launches                        */
+  int64_t filter_launches; /* GEMM launches of the filter                             */
+  double max_residual;     /* largest scaled residual of the returned pairs           */
+} chase_bse_stats;
+
+/* Full solve (Algorithm 3).
+ *   A, B     device, n x n complex128 row-major (see conventions)
+ *   n        block size (H is 2n x 2n), n >= 1
+ *   nev      wanted pairs, 1 <= nev; nev + nex <= n
+ *   nex      extra search vectors
+ *   deg      Chebyshev degree (H^2 steps) of the first iteration, >= 1
+ *   tol      residual tolerance on ||H v - lambda v||_2 / rho_hat, ||v|| = 1
+ *   opts     NULL for defaults
+ *   evals    device, nev doubles: ascending positive eigenvalues
+ *   evecs    device, 2n x nev complex128 column-major: unit right eigenvectors,
+ *            phase-fixed so the largest-magnitude entry of the upper half is real
+ *            and positive
+ *   stats    host, may be NULL
+ * Returns OK, NOT_CONVERGED (the first stats->converged entries are valid), or
+ * an error.  Synchronises opts->stream. */
+int chase_bse_solve(const void* A, const void* B, int64_t n, int64_t nev, int64_t nex,
+                    int32_t deg, double tol, const chase_bse_opts* opts, double* evals,
+                    void* evecs, chase_bse_stats* stats);
+
+/* Chebyshev filter on H^2 (Section 4.2, eq. three-term_recurrence_pseudo-hermitian),
+ * scaled three-term recurrence with a = mu_nevex^2, b = muN^2, c = (a+b)/2,
+ * e = (b-a)/2, sigma_1 = e/(mu1^2 - c):
+ *   Y_1 = (sigma_1/e)(H^2 Y_0 - c Y_0),
+ *   Y_{j+1} = (2 sigma_{j+1}/e)(H^2 Y_j - c Y_j) - sigma_j sigma_{j+1} Y_{j-1},
+ *   sigma_{j+1} = 1/(2/sigma_1 - sigma_j).
+ *   W        device, 2n x k complex128, in: Y_0, out: column i = Y_{degs[i]}
+ *   degs     host, k ints >= 1 (any order)
+ *   precision chase_bse_precision
+ * 0 < mu1 < mu_nevex < muN.  k = 0 is a no-op.  Asynchronous on `stream` except
+ * for workspace bookkeeping; the result is ready when the stream reaches it. */
+int chase_bse_filter(const void* A, const void* B, int64_t n, void* W, int64_t k,
+                     const int32_t* degs, double mu1, double mu_nevex, double muN,
+                     int32_t precision, void* stream);
+
+/* Oblique Rayleigh-Ritz with hermitian spectral equivalence (Algorithm 2):
+ * T = S H Q, M = Q^* T = L L^*, G = L^{-1}(I - 2 Q_2^* Q_2) L^{-*}, G y = theta y,
+ * ritz = 1/theta for the k/2 positive theta, Wpos = Q L^{-*} Y_+ (unit columns).
+ *   Q     device, 2n x k complex128 with orthonormal columns, k even
+ *   ritz  host, k/2 doubles, ascending
+ *   Wpos  device, 2n x k/2 complex128 (may not alias Q)
+ * Returns NOT_DEFINITE when Q^* S H Q is not positive definite and QR_FAILED
+ * when fewer than k/2 eigenvalues of G are positive (range(Q) is not closed
+ * under W -> K conj(W), e.g. after an exactly rank-deficient search space).
+ * Synchronises `stream`. */
+int chase_bse_rr(const void* A, const void* B, int64_t n, const void* Q, int64_t k,
+                 double* ritz, void* Wpos, void* stream);
+
+/* Residual norms ||H w_j - lambda_j w_j||_2 (Section 4.5).
+ *   W      device, 2n x k; lambda device, k doubles; res device, k doubles. */
+int chase_bse_residuals(const void* A, const void* B, int64_t n, const void* W,
+                        const double* lambda, int64_t k, double* res, void* stream);
+
+/* Eigenvalue gradient of L = sum_i w_i lambda_i (left eigenvector u = S v,
+ * Theorem SH_HPD): with V = [X; Y], s_i = |x_i|^2 - |y_i|^2, c_i = w_i / s_i,
+ *   gA = sum_i c_i (x_i x_i^* + conj(y_i) y_i^T)   (hermitian)
+ *   gB = sum_i c_i (x_i y_i^* + conj(y_i) x_i^T)   (symmetric)
+ * under the convention dL = Re sum conj(G) .* dZ.
+ *   V      device, 2n x nev right eigenvectors (any normalisation)
+ *   w      device, nev doubles
+ *   gA, gB device, n x n complex128, written ROW-MAJOR like A and B. */
+int chase_bse_grad(const void* V, const double* w, int64_t n, int64_t nev, void* gA,
+                   void* gB, void* stream);
+
+/* Static description of a status code. */
+const char* chase_bse_strerror(int status);
+
+/* Library version, and 1 when the mixed-precision (tcgen05) filter is compiled in. */
+int chase_bse_version(void);
+int chase_bse_has_mixed(void);
+
+/* Diagnostics (no counterpart in the paper): the number of CUDA kernels this
+ * library has launched since it was loaded, summed over all threads. */
+int64_t chase_bse_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CHASE_BSE_H */

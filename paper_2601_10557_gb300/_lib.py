@@ -1,0 +1,268 @@
+"""ctypes binding of libchase_bse.so (argument marshalling only).
+
+Every numerical step runs inside the CUDA library; this module checks tensor
+layouts, passes raw device pointers and the current CUDA stream, and turns
+status codes into exceptions.  Tensors follow the library's storage
+convention: A, B are (n, n) complex128 row-major; a block of k 2n-vectors is a
+(k, 2n) complex128 tensor (the column-major 2n x k block of the C ABI).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libchase_bse.so")
+
+FP64 = 0
+MIXED_BF16X3 = 1
+_PREC = {"fp64": FP64, "mixed": MIXED_BF16X3, "mixed_bf16x3": MIXED_BF16X3}
+
+
+class ChaseBSEError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: status {status} ({strerror(status)})")
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [
+        ("size", ctypes.c_uint32),
+        ("precision", ctypes.c_int32),
+        ("maxiter", ctypes.c_int32),
+        ("deg_min", ctypes.c_int32),
+        ("deg_max", ctypes.c_int32),
+        ("lanczos_steps", ctypes.c_int32),
+        ("lanczos_vecs", ctypes.c_int32),
+        ("reserved0", ctypes.c_int32),
+        ("gamma", ctypes.c_double),
+        ("switch_tol", ctypes.c_double),
+        ("seed", ctypes.c_uint64),
+        ("W0", ctypes.c_void_p),
+        ("V0", ctypes.c_void_p),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("size", ctypes.c_uint32),
+        ("iterations", ctypes.c_int32),
+        ("converged", ctypes.c_int32),
+        ("householder", ctypes.c_int32),
+        ("mu1", ctypes.c_double),
+        ("mu_nevex", ctypes.c_double),
+        ("muN", ctypes.c_double),
+        ("rho_hat", ctypes.c_double),
+        ("ms_total", ctypes.c_double),
+        ("ms_lanczos", ctypes.c_double),
+        ("ms_filter", ctypes.c_double),
+        ("ms_qr", ctypes.c_double),
+        ("ms_rr", ctypes.c_double),
+        ("ms_resid", ctypes.c_double),
+        ("filter_flops", ctypes.c_double),
+        ("filter_flops_fp64", ctypes.c_double),
+        ("ms_filter_fp64", ctypes.c_double),
+        ("filter_launches", ctypes.c_int64),
+        ("max_residual", ctypes.c_double),
+    ]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_ if name != "size"}
+
+
+_lib: Optional[ctypes.CDLL] = None
+
+EXPORTS = ["chase_bse_solve", "chase_bse_filter", "chase_bse_rr", "chase_bse_residuals", "chase_bse_grad",
+           "chase_bse_strerror", "chase_bse_version", "chase_bse_has_mixed", "chase_bse_launch_count"]
+
+
+def lib() -> ctypes.CDLL:
+    """Load the CUDA library; fails loudly when it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+    L.chase_bse_solve.argtypes = [vp, vp, i64, i64, i64, i32, dbl, ctypes.POINTER(Opts), vp, vp,
+                                  ctypes.POINTER(Stats)]
+    L.chase_bse_filter.argtypes = [vp, vp, i64, vp, i64, ctypes.POINTER(ctypes.c_int32), dbl, dbl, dbl, i32, vp]
+    L.chase_bse_rr.argtypes = [vp, vp, i64, vp, i64, ctypes.POINTER(ctypes.c_double), vp, vp]
+    L.chase_bse_residuals.argtypes = [vp, vp, i64, vp, vp, i64, vp, vp]
+    L.chase_bse_grad.argtypes = [vp, vp, i64, i64, vp, vp, vp]
+    L.chase_bse_strerror.argtypes = [ctypes.c_int]
+    L.chase_bse_strerror.restype = ctypes.c_char_p
+    L.chase_bse_launch_count.restype = ctypes.c_int64
+    for name in ["chase_bse_solve", "chase_bse_filter", "chase_bse_rr", "chase_bse_residuals", "chase_bse_grad",
+                 "chase_bse_version", "chase_bse_has_mixed"]:
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def launch_count() -> int:
+    """Kernels launched by the library so far (diagnostics)."""
+    return int(lib().chase_bse_launch_count())
+
+
+def has_mixed() -> bool:
+    return bool(lib().chase_bse_has_mixed())
+
+
+def strerror(status: int) -> str:
+    return lib().chase_bse_strerror(int(status)).decode()
+
+
+def _check(status: int, where: str, ok=(0,)):
+    if status not in ok:
+        raise ChaseBSEError(status, where)
+    return status
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _mat(X: torch.Tensor, name: str, n: Optional[int] = None) -> torch.Tensor:
+    if not (isinstance(X, torch.Tensor) and X.is_cuda and X.dtype == torch.complex128 and X.dim() == 2):
+        raise ValueError(f"{name} must be a CUDA complex128 matrix")
+    if not X.is_contiguous():
+        raise ValueError(f"{name} must be contiguous (row-major)")
+    if n is not None and X.shape != (n, n):
+        raise ValueError(f"{name} must be {n} x {n}")
+    return X
+
+
+def _block(W: torch.Tensor, name: str, n2: int) -> torch.Tensor:
+    if not (isinstance(W, torch.Tensor) and W.is_cuda and W.dtype == torch.complex128 and W.dim() == 2):
+        raise ValueError(f"{name} must be a CUDA complex128 tensor of shape (k, 2n)")
+    if W.shape[1] != n2 or not W.is_contiguous():
+        raise ValueError(f"{name} must be contiguous with shape (k, {n2})")
+    return W
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def solve(A: torch.Tensor, B: torch.Tensor, nev: int, nex: int, deg: int = 20, tol: float = 1e-10, *,
+          precision: str = "fp64", W0: Optional[torch.Tensor] = None, V0: Optional[torch.Tensor] = None,
+          maxiter: int = 25, deg_min: Optional[int] = None, deg_max: Optional[int] = None,
+          lanczos_steps: int = 26, lanczos_vecs: int = 4, gamma: float = 1e-3, switch_tol: float = 1e-5,
+          seed: int = 0, stream=None, allow_partial: bool = False):
+    """chase_bse_solve: returns (evals (nev,) float64, evecs (nev, 2n) complex128, stats dict)."""
+    A = _mat(A, "A")
+    n = A.shape[0]
+    B = _mat(B, "B", n)
+    nevex = nev + nex
+    if W0 is not None:
+        W0 = _block(W0, "W0", 2 * n)
+        if W0.shape[0] != nevex:
+            raise ValueError("W0 must have nev + nex rows")
+    if V0 is not None:
+        V0 = _block(V0, "V0", 2 * n)
+        lanczos_vecs = V0.shape[0]
+    o = Opts(size=ctypes.sizeof(Opts), precision=_PREC[precision], maxiter=maxiter,
+             deg_min=deg if deg_min is None else deg_min, deg_max=deg if deg_max is None else deg_max,
+             lanczos_steps=lanczos_steps, lanczos_vecs=lanczos_vecs, gamma=gamma, switch_tol=switch_tol,
+             seed=seed, W0=_ptr(W0), V0=_ptr(V0), stream=ctypes.c_void_p(_stream(stream)))
+    evals = torch.zeros(nev, dtype=torch.float64, device=A.device)
+    evecs = torch.zeros((nev, 2 * n), dtype=torch.complex128, device=A.device)
+    st = Stats(size=ctypes.sizeof(Stats))
+    status = lib().chase_bse_solve(_ptr(A), _ptr(B), n, nev, nex, deg, tol, ctypes.byref(o), _ptr(evals),
+                                   _ptr(evecs), ctypes.byref(st))
+    _check(status, "chase_bse_solve", ok=(0, 1) if allow_partial else (0,))
+    d = st.as_dict()
+    d["status"] = status
+    return evals, evecs, d
+
+
+def filter(A: torch.Tensor, B: torch.Tensor, W: torch.Tensor, degs, mu1: float, mu_nevex: float, muN: float,
+           precision: str = "fp64", stream=None) -> torch.Tensor:
+    """chase_bse_filter, in place on W (k, 2n); returns W."""
+    A = _mat(A, "A")
+    n = A.shape[0]
+    B = _mat(B, "B", n)
+    W = _block(W, "W", 2 * n)
+    k = W.shape[0]
+    d = (ctypes.c_int32 * max(k, 1))(*[int(x) for x in degs])
+    if len(degs) != k:
+        raise ValueError("one degree per vector")
+    _check(lib().chase_bse_filter(_ptr(A), _ptr(B), n, _ptr(W), k, d, mu1, mu_nevex, muN, _PREC[precision],
+                                  ctypes.c_void_p(_stream(stream))), "chase_bse_filter")
+    return W
+
+
+def rayleigh_ritz(A: torch.Tensor, B: torch.Tensor, Q: torch.Tensor, stream=None):
+    """chase_bse_rr: returns (ritz numpy (k/2,), Wpos (k/2, 2n))."""
+    import numpy as np
+    A = _mat(A, "A")
+    n = A.shape[0]
+    B = _mat(B, "B", n)
+    Q = _block(Q, "Q", 2 * n)
+    k = Q.shape[0]
+    ritz = (ctypes.c_double * (k // 2))()
+    Wpos = torch.zeros((k // 2, 2 * n), dtype=torch.complex128, device=A.device)
+    _check(lib().chase_bse_rr(_ptr(A), _ptr(B), n, _ptr(Q), k, ritz, _ptr(Wpos), ctypes.c_void_p(_stream(stream))),
+           "chase_bse_rr")
+    return np.array(ritz[:]), Wpos
+
+
+def residuals(A: torch.Tensor, B: torch.Tensor, W: torch.Tensor, lam: torch.Tensor, stream=None) -> torch.Tensor:
+    A = _mat(A, "A")
+    n = A.shape[0]
+    B = _mat(B, "B", n)
+    W = _block(W, "W", 2 * n)
+    lam = lam.to(device=A.device, dtype=torch.float64).contiguous()
+    res = torch.zeros(W.shape[0], dtype=torch.float64, device=A.device)
+    _check(lib().chase_bse_residuals(_ptr(A), _ptr(B), n, _ptr(W), _ptr(lam), W.shape[0], _ptr(res),
+                                     ctypes.c_void_p(_stream(stream))), "chase_bse_residuals")
+    return res
+
+
+def grad(V: torch.Tensor, w: torch.Tensor, stream=None):
+    """chase_bse_grad: (gA, gB), each (n, n) complex128 row-major."""
+    n2 = V.shape[1]
+    V = _block(V, "V", n2)
+    n = n2 // 2
+    w = w.to(device=V.device, dtype=torch.float64).contiguous()
+    gA = torch.empty((n, n), dtype=torch.complex128, device=V.device)
+    gB = torch.empty((n, n), dtype=torch.complex128, device=V.device)
+    _check(lib().chase_bse_grad(_ptr(V), _ptr(w), n, V.shape[0], _ptr(gA), _ptr(gB),
+                                ctypes.c_void_p(_stream(stream))), "chase_bse_grad")
+    return gA, gB
+
+
+class BSEEigvals(torch.autograd.Function):
+    """lambda_1..lambda_nev of H(A, B) with a hand-written backward.
+
+    backward(g) calls chase_bse_grad with w = g, which folds
+    d lambda_i = (S v_i)^* dH v_i / (v_i^* S v_i) into hermitian dL/dA and
+    symmetric dL/dB (PyTorch's convention dL = Re sum conj(G) dZ).
+    """
+
+    @staticmethod
+    def forward(ctx, A, B, nev, nex, deg, tol, kwargs):
+        evals, evecs, stats = solve(A.detach(), B.detach(), nev, nex, deg, tol, **(kwargs or {}))
+        ctx.save_for_backward(evecs)
+        ctx.stats = stats
+        return evals
+
+    @staticmethod
+    def backward(ctx, g):
+        (evecs,) = ctx.saved_tensors
+        gA, gB = grad(evecs, g.contiguous())
+        return gA, gB, None, None, None, None, None
+
+
+def eigvals(A, B, nev, nex, deg=20, tol=1e-10, **kwargs):
+    """Differentiable wrapper around chase_bse_solve (eigenvalues only)."""
+    return BSEEigvals.apply(A, B, nev, nex, deg, tol, kwargs)

@@ -1,0 +1,82 @@
+// extern "C" entry points declared in include/chase_bse.h.
+#include <exception>
+#include <vector>
+
+#include "solver.cuh"
+
+using cb::cplx;
+
+#define CB_GUARD(body)                 \
+  try {                                \
+    body                               \
+  } catch (const std::bad_alloc&) {    \
+    return CHASE_BSE_OOM;              \
+  } catch (...) {                      \
+    return CHASE_BSE_CUDA_ERROR;       \
+  }
+
+extern "C" {
+
+int chase_bse_version(void) { return 100; }
+
+int64_t chase_bse_launch_count(void) { return cb::launch_count(); }
+
+int chase_bse_has_mixed(void) { return cb::mixed_available() ? 1 : 0; }
+
+const char* chase_bse_strerror(int status) {
+  switch (status) {
+    case CHASE_BSE_OK: return "ok";
+    case CHASE_BSE_NOT_CONVERGED: return "not converged within maxiter (partial results written)";
+    case CHASE_BSE_BAD_ARG: return "invalid argument";
+    case CHASE_BSE_CUDA_ERROR: return "CUDA error";
+    case CHASE_BSE_OOM: return "device workspace allocation failed";
+    case CHASE_BSE_NOT_DEFINITE: return "S H is not positive definite on the search space";
+    case CHASE_BSE_QR_FAILED: return "orthonormalisation failed";
+    case CHASE_BSE_DEVICE_TIMEOUT: return "a bounded device-side wait gave up";
+    case CHASE_BSE_UNSUPPORTED: return "not supported on this device";
+    default: return "unknown status";
+  }
+}
+
+int chase_bse_solve(const void* A, const void* B, int64_t n, int64_t nev, int64_t nex, int32_t deg, double tol,
+                    const chase_bse_opts* opts, double* evals, void* evecs, chase_bse_stats* stats) {
+  CB_GUARD(return cb::solve((const cplx*)A, (const cplx*)B, n, nev, nex, deg, tol, opts, evals, (cplx*)evecs,
+                            stats);)
+}
+
+int chase_bse_filter(const void* A, const void* B, int64_t n, void* W, int64_t k, const int32_t* degs, double mu1,
+                     double mu_nevex, double muN, int32_t precision, void* stream) {
+  if (k == 0) return CHASE_BSE_OK;
+  if (!A || !B || !W || !degs || n < 1 || k < 0 || !(mu1 > 0) || !(mu_nevex > mu1) || !(muN > mu_nevex))
+    return CHASE_BSE_BAD_ARG;
+  if (precision != CHASE_BSE_FP64 && precision != CHASE_BSE_MIXED_BF16X3) return CHASE_BSE_BAD_ARG;
+  for (int64_t i = 0; i < k; ++i)
+    if (degs[i] < 1) return CHASE_BSE_BAD_ARG;
+  CB_GUARD({
+    std::vector<int> prec(k, precision == CHASE_BSE_MIXED_BF16X3 ? 1 : 0);
+    return cb::filter((const cplx*)A, (const cplx*)B, n, (cplx*)W, k, degs, prec.data(), mu1, mu_nevex, muN,
+                      (cudaStream_t)stream, nullptr);
+  })
+}
+
+int chase_bse_rr(const void* A, const void* B, int64_t n, const void* Q, int64_t k, double* ritz, void* Wpos,
+                 void* stream) {
+  if (!A || !B || !Q || !ritz || !Wpos || n < 1 || k < 2 || (k % 2) != 0 || k > 2 * n) return CHASE_BSE_BAD_ARG;
+  CB_GUARD(return cb::rayleigh_ritz((const cplx*)A, (const cplx*)B, n, (const cplx*)Q, k, ritz, (cplx*)Wpos,
+                                    (cudaStream_t)stream);)
+}
+
+int chase_bse_residuals(const void* A, const void* B, int64_t n, const void* W, const double* lambda, int64_t k,
+                        double* res, void* stream) {
+  if (k == 0) return CHASE_BSE_OK;
+  if (!A || !B || !W || !lambda || !res || n < 1 || k < 0) return CHASE_BSE_BAD_ARG;
+  CB_GUARD(return cb::residuals((const cplx*)A, (const cplx*)B, n, (const cplx*)W, lambda, k, res,
+                                (cudaStream_t)stream);)
+}
+
+int chase_bse_grad(const void* V, const double* w, int64_t n, int64_t nev, void* gA, void* gB, void* stream) {
+  if (!V || !w || !gA || !gB || n < 1 || nev < 1) return CHASE_BSE_BAD_ARG;
+  CB_GUARD(return cb::gradient((const cplx*)V, w, n, nev, (cplx*)gA, (cplx*)gB, (cudaStream_t)stream);)
+}
+
+}  // extern "C"

@@ -1,0 +1,85 @@
+// Shared device/host helpers of the ChASE-BSE library (complex128 arithmetic,
+// status handling, launch helpers).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include "chase_bse.h"
+
+namespace cb {
+
+using cplx = double2;  // (re, im), interleaved complex128
+
+__host__ __device__ inline cplx mk(double r, double i) { return make_double2(r, i); }
+__host__ __device__ inline cplx cadd(cplx a, cplx b) { return mk(a.x + b.x, a.y + b.y); }
+__host__ __device__ inline cplx csub(cplx a, cplx b) { return mk(a.x - b.x, a.y - b.y); }
+__host__ __device__ inline cplx cmul(cplx a, cplx b) { return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__host__ __device__ inline cplx cconj(cplx a) { return mk(a.x, -a.y); }
+__host__ __device__ inline cplx cscale(cplx a, double s) { return mk(a.x * s, a.y * s); }
+__host__ __device__ inline double cabs2(cplx a) { return a.x * a.x + a.y * a.y; }
+// c += a * b with four FMAs
+__device__ __forceinline__ void cfma(cplx& c, cplx a, cplx b) {
+  c.x = fma(a.x, b.x, c.x);
+  c.x = fma(-a.y, b.y, c.x);
+  c.y = fma(a.x, b.y, c.y);
+  c.y = fma(a.y, b.x, c.y);
+}
+
+// Status plumbing: every host helper returns an int status (chase_bse_status).
+#define CB_CUDA(call)                                                            \
+  do {                                                                           \
+    cudaError_t e_ = (call);                                                     \
+    if (e_ != cudaSuccess) {                                                     \
+      if (cb::verbose()) fprintf(stderr, "[chase_bse] %s:%d %s -> %s\n", __FILE__, \
+                                 __LINE__, #call, cudaGetErrorString(e_));       \
+      return (e_ == cudaErrorMemoryAllocation) ? CHASE_BSE_OOM : CHASE_BSE_CUDA_ERROR; \
+    }                                                                            \
+  } while (0)
+#define CB_LAUNCH()                                                              \
+  do {                                                                           \
+    cudaError_t e_ = cudaGetLastError();                                         \
+    if (e_ != cudaSuccess) {                                                     \
+      if (cb::verbose()) fprintf(stderr, "[chase_bse] %s:%d launch -> %s\n",     \
+                                 __FILE__, __LINE__, cudaGetErrorString(e_));    \
+      return CHASE_BSE_CUDA_ERROR;                                               \
+    }                                                                            \
+  } while (0)
+#define CB_TRY(expr)            \
+  do {                          \
+    int s_ = (expr);            \
+    if (s_ != CHASE_BSE_OK) return s_; \
+  } while (0)
+
+bool verbose();
+
+// Number of kernels this library has launched (diagnostics for benchmarks).
+void count_launch();
+int64_t launch_count();
+
+inline unsigned cdiv(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
+
+// Stream-ordered workspace: every buffer is released when the owner goes out
+// of scope (cudaFreeAsync on the same stream).
+struct Workspace {
+  cudaStream_t s;
+  void* ptrs[64];
+  int count = 0;
+  explicit Workspace(cudaStream_t st) : s(st) {}
+  ~Workspace() {
+    for (int i = count - 1; i >= 0; --i) cudaFreeAsync(ptrs[i], s);
+  }
+  template <class T>
+  int alloc(T** p, size_t elems) {
+    *p = nullptr;
+    if (elems == 0) elems = 1;
+    if (count >= 64) return CHASE_BSE_OOM;
+    void* q = nullptr;
+    cudaError_t e = cudaMallocAsync(&q, elems * sizeof(T), s);
+    if (e != cudaSuccess) { cudaGetLastError(); return CHASE_BSE_OOM; }
+    ptrs[count++] = q;
+    *p = static_cast<T*>(q);
+    return CHASE_BSE_OK;
+  }
+};
+
+}  // namespace cb

@@ -1,0 +1,722 @@
+// Small dense FP64 kernels (see dense_kernels.cuh).
+#include "dense_kernels.cuh"
+#include "fp64_kernels.cuh"
+
+namespace cb {
+
+namespace {
+constexpr int NB = 32;  // Cholesky / triangular-inverse block size
+
+__device__ double block_sum(double v, double* sh) {
+  // blockDim.x is a multiple of 32, at most 1024
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  v = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
+  if (w == 0)
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (threadIdx.x == 0) sh[0] = v;
+  __syncthreads();
+  v = sh[0];
+  __syncthreads();
+  return v;
+}
+}  // namespace
+
+// ---------------------------------------------------------------- Cholesky
+__global__ void chol_diag_kernel(cplx* G, int64_t ld, int64_t j0, int nb, int* info) {
+  __shared__ cplx a[NB][NB + 1];
+  const int t = threadIdx.x;
+  for (int idx = t; idx < nb * nb; idx += blockDim.x) {
+    const int r = idx % nb, c = idx / nb;
+    a[r][c] = G[(j0 + r) + (j0 + c) * ld];
+  }
+  __syncthreads();
+  for (int c = 0; c < nb; ++c) {
+    if (t == 0) {
+      double d = a[c][c].x;
+      if (!(d > 0.0)) {
+        atomicCAS(info, 0, (int)(j0 + c + 1));
+        d = 1.0;
+      }
+      a[c][c] = mk(sqrt(d), 0.0);
+    }
+    __syncthreads();
+    const double inv = 1.0 / a[c][c].x;
+    for (int r = c + 1 + t; r < nb; r += blockDim.x) a[r][c] = cscale(a[r][c], inv);
+    __syncthreads();
+    const int m = nb - c - 1;
+    for (int idx = t; idx < m * m; idx += blockDim.x) {
+      const int r = c + 1 + idx % m, q = c + 1 + idx / m;
+      if (q <= r) a[r][q] = csub(a[r][q], cmul(a[r][c], cconj(a[q][c])));
+    }
+    __syncthreads();
+  }
+  for (int idx = t; idx < nb * nb; idx += blockDim.x) {
+    const int r = idx % nb, c = idx / nb;
+    G[(j0 + r) + (j0 + c) * ld] = (r >= c) ? a[r][c] : mk(0, 0);
+  }
+}
+
+__global__ void chol_panel_kernel(cplx* G, int64_t ld, int64_t k, int64_t j0, int nb) {
+  __shared__ cplx L11[NB][NB + 1];
+  for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
+    const int r = idx % nb, c = idx / nb;
+    L11[r][c] = G[(j0 + r) + (j0 + c) * ld];
+  }
+  __syncthreads();
+  const int64_t r = j0 + nb + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= k) return;
+  cplx x[NB];
+#pragma unroll
+  for (int c = 0; c < NB; ++c) x[c] = (c < nb) ? G[r + (j0 + c) * ld] : mk(0, 0);
+#pragma unroll
+  for (int c = 0; c < NB; ++c) {
+    if (c < nb) {
+      cplx v = x[c];
+#pragma unroll
+      for (int q = 0; q < NB; ++q)
+        if (q < c) v = csub(v, cmul(x[q], cconj(L11[c][q])));
+      x[c] = cscale(v, 1.0 / L11[c][c].x);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < NB; ++c)
+    if (c < nb) G[r + (j0 + c) * ld] = x[c];
+}
+
+__global__ void zero_upper_kernel(cplx* G, int64_t k) {
+  const int64_t total = k * k;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i % k, c = i / k;
+    if (r < c) G[i] = mk(0, 0);
+  }
+}
+
+int cholesky(cplx* G, int64_t k, int* info_dev, int* info_host, cudaStream_t s) {
+  CB_CUDA(cudaMemsetAsync(info_dev, 0, sizeof(int), s));
+  for (int64_t j0 = 0; j0 < k; j0 += NB) {
+    const int nb = (int)((k - j0) < NB ? (k - j0) : NB);
+    chol_diag_kernel<<<1, 256, 0, s>>>(G, k, j0, nb, info_dev);
+    count_launch();
+    CB_LAUNCH();
+    const int64_t rest = k - j0 - nb;
+    if (rest > 0) {
+      chol_panel_kernel<<<cdiv(rest, 128), 128, 0, s>>>(G, k, k, j0, nb);
+      count_launch();
+      CB_LAUNCH();
+      cplx* L21 = G + (j0 + nb) + j0 * k;
+      cplx* A22 = G + (j0 + nb) + (j0 + nb) * k;
+      CB_TRY(zgemm('N', 'C', rest, rest, nb, mk(-1, 0), L21, k, L21, k, mk(1, 0), A22, k, s));
+    }
+  }
+  zero_upper_kernel<<<cdiv(k * k, 256) < 4096 ? cdiv(k * k, 256) : 4096, 256, 0, s>>>(G, k);
+  count_launch();
+  CB_LAUNCH();
+  CB_CUDA(cudaMemcpyAsync(info_host, info_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CB_CUDA(cudaStreamSynchronize(s));
+  return CHASE_BSE_OK;
+}
+
+// ------------------------------------------------------ triangular inverse
+__global__ void inv_diag_blocks_kernel(const cplx* L, int64_t k, cplx* X) {
+  __shared__ cplx a[NB][NB + 1];
+  const int64_t j0 = (int64_t)blockIdx.x * NB;
+  const int nb = (int)((k - j0) < NB ? (k - j0) : NB);
+  for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
+    const int r = idx % nb, c = idx / nb;
+    a[r][c] = L[(j0 + r) + (j0 + c) * k];
+  }
+  __syncthreads();
+  const int c = threadIdx.x;
+  if (c >= nb) return;
+  cplx x[NB];
+#pragma unroll
+  for (int r = 0; r < NB; ++r) {
+    if (r < nb) {
+      cplx v = (r == c) ? mk(1, 0) : mk(0, 0);
+#pragma unroll
+      for (int q = 0; q < NB; ++q)
+        if (q < r && q >= c) v = csub(v, cmul(a[r][q], x[q]));
+      // a[r][r] is real and positive (Cholesky factor)
+      x[r] = (r >= c) ? cscale(v, 1.0 / a[r][r].x) : mk(0, 0);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < NB; ++r)
+    if (r < nb) X[(j0 + r) + (j0 + c) * k] = x[r];
+}
+
+int tri_inverse(const cplx* L, int64_t k, cplx* X, cplx* T, cudaStream_t s) {
+  CB_CUDA(cudaMemsetAsync(X, 0, sizeof(cplx) * k * k, s));
+  const int64_t nblk = (k + NB - 1) / NB;
+  inv_diag_blocks_kernel<<<(unsigned)nblk, NB, 0, s>>>(L, k, X);
+  count_launch();
+  CB_LAUNCH();
+  for (int64_t b = 1; b < nblk; ++b) {
+    const int64_t i0 = b * NB;
+    const int64_t nbi = (k - i0) < NB ? (k - i0) : NB;
+    // T = L[i0:i0+nbi, 0:i0] * X[0:i0, 0:i0]
+    CB_TRY(zgemm('N', 'N', nbi, i0, i0, mk(1, 0), L + i0, k, X, k, mk(0, 0), T, nbi, s));
+    // X[i0:i0+nbi, 0:i0] = -X_bb * T
+    CB_TRY(zgemm('N', 'N', nbi, i0, nbi, mk(-1, 0), X + i0 + i0 * k, k, T, nbi, mk(0, 0), X + i0, k, s));
+  }
+  return CHASE_BSE_OK;
+}
+
+// ------------------------------------------------------------------ Jacobi
+// Round-robin (circle) ordering: position 0 holds index 0, position p > 0 holds
+// ((p - 1 + r) mod (k - 1)) + 1; slot s pairs positions s and k - 1 - s.
+__device__ __forceinline__ void jpair(int64_t slot, int r, int64_t k, int64_t& p, int64_t& q) {
+  auto pl = [&](int64_t pos) -> int64_t { return pos == 0 ? 0 : ((pos - 1 + r) % (k - 1)) + 1; };
+  const int64_t a = pl(slot), b = pl(k - 1 - slot);
+  p = a < b ? a : b;
+  q = a < b ? b : a;
+}
+
+__global__ void jacobi_rot_kernel(const cplx* G, int64_t k, int r, cplx* rot) {
+  const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot >= k / 2) return;
+  int64_t p, q;
+  jpair(slot, r, k, p, q);
+  const double app = G[p + p * k].x, aqq = G[q + q * k].x;
+  const cplx apq = G[p + q * k];
+  const double rr = sqrt(cabs2(apq));
+  cplx J00 = mk(1, 0), J01 = mk(0, 0), J10 = mk(0, 0), J11 = mk(1, 0);
+  if (rr > 1e-300) {
+    const cplx ec = mk(apq.x / rr, -apq.y / rr);  // conj(e^{i phi})
+    const double tau = (aqq - app) / (2.0 * rr);
+    const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+    const double c = 1.0 / sqrt(1.0 + t * t), sn = t * c;
+    J00 = mk(c, 0);
+    J01 = mk(sn, 0);
+    J10 = cscale(ec, -sn);
+    J11 = cscale(ec, c);
+  }
+  rot[4 * slot + 0] = J00;
+  rot[4 * slot + 1] = J01;
+  rot[4 * slot + 2] = J10;
+  rot[4 * slot + 3] = J11;
+}
+
+__global__ void jacobi_apply_kernel(cplx* G, cplx* V, int64_t k, int r, const cplx* __restrict__ rot) {
+  const int64_t half = k / 2;
+  const int64_t nG = half * half, nV = k * half;
+  for (int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; item < nG + nV;
+       item += (int64_t)gridDim.x * blockDim.x) {
+    if (item < nG) {
+      const int64_t a = item % half, b = item / half;
+      int64_t pa, qa, pb, qb;
+      jpair(a, r, k, pa, qa);
+      jpair(b, r, k, pb, qb);
+      const cplx A00 = rot[4 * a], A01 = rot[4 * a + 1], A10 = rot[4 * a + 2], A11 = rot[4 * a + 3];
+      const cplx B00 = rot[4 * b], B01 = rot[4 * b + 1], B10 = rot[4 * b + 2], B11 = rot[4 * b + 3];
+      const cplx x00 = G[pa + pb * k], x01 = G[pa + qb * k], x10 = G[qa + pb * k], x11 = G[qa + qb * k];
+      // J_a^* X
+      const cplx y00 = cadd(cmul(cconj(A00), x00), cmul(cconj(A10), x10));
+      const cplx y01 = cadd(cmul(cconj(A00), x01), cmul(cconj(A10), x11));
+      const cplx y10 = cadd(cmul(cconj(A01), x00), cmul(cconj(A11), x10));
+      const cplx y11 = cadd(cmul(cconj(A01), x01), cmul(cconj(A11), x11));
+      // (.) J_b
+      G[pa + pb * k] = cadd(cmul(y00, B00), cmul(y01, B10));
+      G[pa + qb * k] = cadd(cmul(y00, B01), cmul(y01, B11));
+      G[qa + pb * k] = cadd(cmul(y10, B00), cmul(y11, B10));
+      G[qa + qb * k] = cadd(cmul(y10, B01), cmul(y11, B11));
+    } else {
+      const int64_t it = item - nG;
+      const int64_t i = it % k, b = it / k;
+      int64_t pb, qb;
+      jpair(b, r, k, pb, qb);
+      const cplx B00 = rot[4 * b], B01 = rot[4 * b + 1], B10 = rot[4 * b + 2], B11 = rot[4 * b + 3];
+      const cplx v0 = V[i + pb * k], v1 = V[i + qb * k];
+      V[i + pb * k] = cadd(cmul(v0, B00), cmul(v1, B10));
+      V[i + qb * k] = cadd(cmul(v0, B01), cmul(v1, B11));
+    }
+  }
+}
+
+__global__ void offdiag_norm_kernel(const cplx* G, int64_t k, double* red) {
+  __shared__ double sh[32];
+  double off = 0.0, tot = 0.0;
+  for (int64_t i = threadIdx.x; i < k * k; i += blockDim.x) {
+    const double v = cabs2(G[i]);
+    tot += v;
+    if (i % k != i / k) off += v;
+  }
+  off = block_sum(off, sh);
+  tot = block_sum(tot, sh);
+  if (threadIdx.x == 0) { red[0] = off; red[1] = tot; }
+}
+
+int jacobi_eigh(cplx* G, int64_t k, cplx* V, double* theta, cplx* rot, double* red, int max_sweeps,
+                int* sweeps_out, cudaStream_t s) {
+  if (k % 2 != 0) return CHASE_BSE_BAD_ARG;
+  CB_TRY(set_identity(V, k, s));
+  int sweeps = 0;
+  const int64_t half = k / 2;
+  const int64_t items = half * half + k * half;
+  const unsigned gapply = (unsigned)((items + 255) / 256 < 2048 ? (items + 255) / 256 : 2048);
+  double hred[2];
+  for (; sweeps < max_sweeps; ++sweeps) {
+    offdiag_norm_kernel<<<1, 1024, 0, s>>>(G, k, red);
+    count_launch();
+    CB_LAUNCH();
+    CB_CUDA(cudaMemcpyAsync(hred, red, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CB_CUDA(cudaStreamSynchronize(s));
+    if (!(hred[0] > 1e-30 * hred[1])) break;  // off <= 1e-15 ||G||_F (or NaN guard)
+    for (int r = 0; r < k - 1; ++r) {
+      jacobi_rot_kernel<<<cdiv(half, 128), 128, 0, s>>>(G, k, r, rot);
+      count_launch();
+      jacobi_apply_kernel<<<gapply, 256, 0, s>>>(G, V, k, r, rot);
+      count_launch();
+    }
+    CB_LAUNCH();
+  }
+  if (sweeps_out) *sweeps_out = sweeps;
+  CB_TRY(diag_real(G, k, theta, s));
+  if (hred[0] != hred[0]) return CHASE_BSE_CUDA_ERROR;  // NaN in G
+  return CHASE_BSE_OK;
+}
+
+// --------------------------------------------------------------- Householder
+__global__ void hh_reflector_kernel(cplx* X, int64_t N, int64_t j, cplx* Vs, cplx* Us) {
+  __shared__ double sh[32];
+  const cplx* x = X + j * N;
+  double ss = 0.0;
+  for (int64_t r = j + threadIdx.x; r < N; r += blockDim.x) ss += cabs2(x[r]);
+  ss = block_sum(ss, sh);
+  const double xn = sqrt(ss);
+  const cplx alpha = x[j];
+  const double aa = sqrt(cabs2(alpha));
+  cplx beta = mk(0, 0);
+  double tau = 0.0;
+  if (xn > 0.0) {
+    const cplx ph = aa > 0.0 ? cscale(alpha, 1.0 / aa) : mk(1, 0);
+    beta = cscale(ph, -xn);
+    tau = 2.0 / (2.0 * ss + 2.0 * xn * aa);
+  }
+  cplx* v = Vs + j * N;
+  cplx* u = Us + j * N;
+  for (int64_t r = threadIdx.x; r < N; r += blockDim.x) {
+    cplx vr = mk(0, 0);
+    if (r >= j && xn > 0.0) vr = (r == j) ? csub(alpha, beta) : x[r];
+    v[r] = vr;
+    u[r] = cscale(vr, tau);
+  }
+}
+
+// wrow[c] = sum_{r >= j} conj(v[r]) X[r, c] for c in [c0, m)
+__global__ void hh_row_kernel(const cplx* X, int64_t N, int64_t j, int64_t c0, const cplx* v, cplx* wrow) {
+  __shared__ double sh[32];
+  const int64_t c = c0 + blockIdx.x;
+  double re = 0.0, im = 0.0;
+  for (int64_t r = j + threadIdx.x; r < N; r += blockDim.x) {
+    const cplx p = cmul(cconj(v[r]), X[r + c * N]);
+    re += p.x;
+    im += p.y;
+  }
+  re = block_sum(re, sh);
+  im = block_sum(im, sh);
+  if (threadIdx.x == 0) wrow[c] = mk(re, im);
+}
+
+// X[r, c] -= u[r] wrow[c] for r >= j, c in [c0, m)
+__global__ void hh_update_kernel(cplx* X, int64_t N, int64_t m, int64_t j, int64_t c0, const cplx* u,
+                                 const cplx* wrow) {
+  const int64_t rows = N - j, cols = m - c0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < rows * cols; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = j + i % rows, c = c0 + i / rows;
+    X[r + c * N] = csub(X[r + c * N], cmul(u[r], wrow[c]));
+  }
+}
+
+__global__ void set_diag_rect_kernel(cplx* Q, int64_t N, int64_t m) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < m) Q[c + c * N] = mk(1, 0);
+}
+
+int householder_qr(cplx* X, int64_t N, int64_t m, cplx* Q, cplx* Vs, cplx* Us, cplx* wrow, cudaStream_t s) {
+  if (m > N || m <= 0) return CHASE_BSE_BAD_ARG;
+  for (int64_t j = 0; j < m; ++j) {
+    hh_reflector_kernel<<<1, 1024, 0, s>>>(X, N, j, Vs, Us);
+    count_launch();
+    if (j + 1 < m) {
+      hh_row_kernel<<<(unsigned)(m - j - 1), 256, 0, s>>>(X, N, j, j + 1, Vs + j * N, wrow);
+      count_launch();
+      const int64_t tot = (N - j) * (m - j - 1);
+      hh_update_kernel<<<cdiv(tot, 256) < 4096 ? cdiv(tot, 256) : 4096, 256, 0, s>>>(X, N, m, j, j + 1,
+                                                                                     Us + j * N, wrow);
+                                                                                     count_launch();
+    }
+  }
+  CB_LAUNCH();
+  // Q = H_0 H_1 ... H_{m-1} [I; 0], accumulated backwards
+  CB_CUDA(cudaMemsetAsync(Q, 0, sizeof(cplx) * N * m, s));
+  set_diag_rect_kernel<<<cdiv(m, 256), 256, 0, s>>>(Q, N, m);
+  count_launch();
+  for (int64_t j = m - 1; j >= 0; --j) {
+    hh_row_kernel<<<(unsigned)(m - j), 256, 0, s>>>(Q, N, j, j, Vs + j * N, wrow);
+    count_launch();
+    const int64_t tot = (N - j) * (m - j);
+    hh_update_kernel<<<cdiv(tot, 256) < 4096 ? cdiv(tot, 256) : 4096, 256, 0, s>>>(Q, N, m, j, j, Us + j * N, wrow);
+    count_launch();
+  }
+  CB_LAUNCH();
+  return CHASE_BSE_OK;
+}
+
+// ----------------------------------------------------------------- utilities
+static inline unsigned gs(int64_t total) {
+  const int64_t b = (total + 255) / 256;
+  return (unsigned)(b < 8192 ? (b > 0 ? b : 1) : 8192);
+}
+#define GRID_STRIDE(i, total) \
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (total); i += (int64_t)gridDim.x * blockDim.x)
+
+__global__ void scale_lower_kernel(cplx* W, int64_t n, int64_t k, double g) {
+  GRID_STRIDE(i, n * k) {
+    const int64_t r = i % n, c = i / n;
+    W[c * 2 * n + n + r] = cscale(W[c * 2 * n + n + r], g);
+  }
+}
+int scale_lower(cplx* W, int64_t n, int64_t k, double gamma, cudaStream_t s) {
+  if (n * k == 0) return CHASE_BSE_OK;
+  scale_lower_kernel<<<gs(n * k), 256, 0, s>>>(W, n, k, gamma);
+  count_launch();
+  CB_LAUNCH();
+  return CHASE_BSE_OK;
+}
+
+__global__ void build_qr_input_kernel(cplx* X, const cplx* Yp, int64_t L, const cplx* Wf, int64_t kf, int64_t n) {
+  const int64_t n2 = 2 * n, cols = 2 * L + 2 * kf;
+  GRID_STRIDE(i, n2 * cols) {
+    const int64_t r = i % n2, c = i / n2;
+    cplx v;
+    if (c < L) {                       // S Y+
+      v = Yp[c * n2 + r];
+      if (r >= n) v = mk(-v.x, -v.y);
+    } else if (c < 2 * L) {            // S K conj(Y+)
+      const cplx* y = Yp + (c - L) * n2;
+      v = (r < n) ? cconj(y[r + n]) : mk(-y[r - n].x, y[r - n].y);
+    } else if (c < 2 * L + kf) {       // W+
+      v = Wf[(c - 2 * L) * n2 + r];
+    } else {                           // K conj(W+)
+      const cplx* w = Wf + (c - 2 * L - kf) * n2;
+      v = cconj(r < n ? w[r + n] : w[r - n]);
+    }
+    X[i] = v;
+  }
+}
+int build_qr_input(cplx* X, const cplx* Yp, int64_t L, const cplx* Wf, int64_t kf, int64_t n, cudaStream_t s) {
+  const int64_t tot = 2 * n * (2 * L + 2 * kf);
+  if (tot == 0) return CHASE_BSE_OK;
+  build_qr_input_kernel<<<gs(tot), 256, 0, s>>>(X, Yp, L, Wf, kf, n);
+  count_launch();
+  CB_LAUNCH();
+  return CHASE_BSE_OK;
+}
+
+__global__ void gather_cols_kernel(cplx* dst, const cplx* src, const int* idx, int64_t rows, int64_t m) {
+  GRID_STRIDE(i, rows * m) {
+    const int64_t r = i % rows, c = i / rows;
+    dst[i] = src[(int64_t)idx[c] * rows + r];
+  }
+}
+int gather_cols(cplx* dst, const cplx* src, const int* idx, int64_t rows, int64_t m, cudaStream_t s) {
+  if (rows * m == 0) return CHASE_BSE_OK;
+  gather_cols_kernel<<<gs(rows * m), 256, 0, s>>>(dst, src, idx, rows, m);
+  count_launch();
+  CB_LAUNCH();
+  return CHASE_BSE_OK;
+}
+__global__ void scatter_cols_kernel(cplx* dst, const cplx* src, const int* idx, int64_t rows, int64_t m) {
+  GRID_STRIDE(i, rows * m) {
+    const int64_t r = i % rows, c = i / rows;
+    dst[(int64_t)idx[c] * rows + r] = src[i];
+  }
+}
+int scatter_cols(cplx* dst, const cplx* src, const int* idx, int64_t rows, int64_t m, cudaStream_t s) {
+  if (rows * m == 0) return CHASE_BSE_OK;
+  scatter_cols_kernel<<<gs(rows * m), 256, 0, s>>>(dst, src, idx, rows, m);
+  count_launch();
+  CB_LAUNCH();
+  return CHASE_BSE_OK;
+}
+__global__ void collect_cols_kernel(cplx* dst, const cplx* b0, const cplx* b1, const cplx* b2, const int* sel,
+                                    int64_t rows, int64_t m) {
+  GRID_STRIDE(i, rows * m) {
+    const int64_t c = i / rows;
+    const int q = sel[c];
+    const cplx* b = q == 0 ? b0 : (q == 1 ? b1 : b2);
+    dst[i] = b[i];
+  }
+}
+int collect_cols(cplx* dst, const cplx* b0, const cplx* b1, const cplx* b2, const int* sel, int64_t rows,
+                 int64_t m, cudaStream_t s) {
+  if (rows * m == 0) return CHASE_BSE_OK;
+  collect_cols_kernel<<<gs(rows * m), 256, 0, s>>>(dst, b0, b1, b2, sel, rows, m);
+  count_launch();
+  CB_LAUNCH();
+  return CHASE_BSE_OK;
+}
+
+__global__ void col_norms_kernel(const cplx* X, int64_t rows, double* out) {
+  __shared__ double sh[32];
+  const cplx* x = X + (int64_t)blockIdx.x * rows;
+  double ss = 0.0;
+  for (int64_t r = threadIdx.x; r < rows; r += blockDim.x) ss += cabs2(x[r]);
+  ss = block_sum(ss, sh);
+  if (threadIdx.x == 0) out[blockIdx.x] = sqrt(ss);
+}
+int col_norms(const cplx* X, int64_t rows, int64_t m, double* out, cudaStream_t s) {
+  if (m == 0) return CHASE_BSE_OK;
+  col_norms_kernel<<<(unsigned)m, 256, 0, s>>>(X, rows, out);
+  count_launch();
+  CB_LAUNCH();
+  return CHASE_BSE_OK;
+}
+__global__ void normalize_cols_kernel(cplx* X, int64_t rows) {
+  __shared__ double sh[32];
+  cplx* x = X + (int64_t)blockIdx.x * rows;
+  double ss = 0.0;
+  for (int64_t r = threadIdx.x; r < rows; r += blockDim.x) ss += cabs2(x[r]);
+  ss = block_sum(ss, sh);
+  const double inv = ss > 0.0 ? 1.0 / sqrt(ss) : 0.0;
+  for (int64_t r = threadIdx.x; r < rows; r += blockDim.x) x[r] = cscale(x[r], inv);
+}
+int normalize_cols(cplx* X, int64_t rows, int64_t m, cudaStream_t s) {
+  if (m == 0) return CHASE_BSE_OK;
+  normalize_cols_kernel<<<(unsigned)m, 256, 0, s>>>(X, rows);
+  count_launch();
+  CB_LAUNCH();
+  return CHASE_BSE_OK;
+}
+__global__ void set_identity_kernel(cplx* M, int64_t k) {
+  GRID_STRIDE(i, k * k) { M[i] = (i % k == i / k) ? mk(1, 0) : mk(0, 0); }
+}
+int set_identity(cplx* M, int64_t k, cudaStream_t s) {
+  if (k == 0) return CHASE_BSE_OK;
+  set_identity_kernel<<<gs(k * k), 256, 0, s>>>(M, k);
+  count_launch();
+  CB_LAUNCH();
+  return CHASE_BSE_OK;
+}
+__global__ void hermitize_kernel(cplx* G, int64_t k) {
+  GRID_STRIDE(i, k * k) {
+    const int64_t r = i % k, c = i / k;
+    if (r > c) {
+      const cplx a = G[r + c * k], b = G[c + r * k];
+      const cplx m = mk(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));  // (a + conj(b)) / 2
+      G[r + c * k] = m;
+      G[c + r * k] = cconj(m);
+    } else if (r == c) {
+      G[i].y = 0.0;
+    }
+  }
+}
+int hermitize(cplx* G, int64_t k, cudaStream_t s) {
+  if (k == 0) return CHASE_BSE_OK;
+  hermitize_kernel<<<gs(k * k), 256, 0, s>>>(G, k);
+  count_launch();
+  CB_LAUNCH();
+  return CHASE_BSE_OK;
+}
+__global__ void diag_real_kernel(const cplx* G, int64_t k, double* out) {
+  GRID_STRIDE(i, k) { out[i] = G[i + i * k].x; }
+}
+int diag_real(const cplx* G, int64_t k, double* out, cudaStream_t s) {
+  if (k == 0) return CHASE_BSE_OK;
+  diag_real_kernel<<<gs(k), 256, 0, s>>>(G, k, out);
+  count_launch();
+  CB_LAUNCH();
+  return CHASE_BSE_OK;
+}
+// largest |v_i| over the upper half (smallest index on ties); v <- v |v_i| / v_i
+__global__ void phase_fix_kernel(cplx* V, int64_t n) {
+  __shared__ double bv[1024];
+  __shared__ int64_t bi[1024];
+  cplx* v = V + (int64_t)blockIdx.x * 2 * n;
+  double best = -1.0;
+  int64_t besti = 0;
+  for (int64_t r = threadIdx.x; r < n; r += blockDim.x) {
+    const double a = cabs2(v[r]);
+    if (a > best) { best = a; besti = r; }
+  }
+  bv[threadIdx.x] = best;
+  bi[threadIdx.x] = besti;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      const double a = bv[threadIdx.x + o];
+      const int64_t ia = bi[threadIdx.x + o];
+      if (a > bv[threadIdx.x] || (a == bv[threadIdx.x] && ia < bi[threadIdx.x])) {
+        bv[threadIdx.x] = a;
+        bi[threadIdx.x] = ia;
+      }
+    }
+    __syncthreads();
+  }
+  const cplx p = v[bi[0]];
+  const double a = sqrt(cabs2(p));
+  const cplx f = a > 0.0 ? mk(p.x / a, -p.y / a) : mk(1, 0);  // |p| / p
+  __syncthreads();
+  for (int64_t r = threadIdx.x; r < 2 * n; r += blockDim.x) v[r] = cmul(v[r], f);
+}
+int phase_fix(cplx* V, int64_t n, int64_t m, cudaStream_t s) {
+  if (m == 0) return CHASE_BSE_OK;
+  phase_fix_kernel<<<(unsigned)m, 1024, 0, s>>>(V, n);
+  count_launch();
+  CB_LAUNCH();
+  return CHASE_BSE_OK;
+}
+__global__ void copy_cols_kernel(cplx* dst, int64_t ldd, const cplx* src, int64_t lds, int64_t rows, int64_t m) {
+  GRID_STRIDE(i, rows * m) {
+    const int64_t r = i % rows, c = i / rows;
+    dst[r + c * ldd] = src[r + c * lds];
+  }
+}
+int copy_cols(cplx* dst, int64_t ldd, const cplx* src, int64_t lds, int64_t rows, int64_t m, cudaStream_t s) {
+  if (rows * m == 0) return CHASE_BSE_OK;
+  copy_cols_kernel<<<gs(rows * m), 256, 0, s>>>(dst, ldd, src, lds, rows, m);
+  count_launch();
+  CB_LAUNCH();
+  return CHASE_BSE_OK;
+}
+
+// ------------------------------------------------------------------ Lanczos
+__global__ void sdot_real_kernel(const cplx* X, const cplx* Y, int64_t n, double* out) {
+  __shared__ double sh[32];
+  const int64_t c = blockIdx.x;
+  const cplx* x = X + c * 2 * n;
+  const cplx* y = Y + c * 2 * n;
+  double acc = 0.0;
+  for (int64_t r = threadIdx.x; r < 2 * n; r += blockDim.x) {
+    const double d = x[r].x * y[r].x + x[r].y * y[r].y;  // Re(conj(x) y)
+    acc += (r < n) ? d : -d;
+  }
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) out[c] = acc;
+}
+int sdot_real(const cplx* X, const cplx* Y, int64_t n, int64_t nvec, double* out, cudaStream_t s) {
+  sdot_real_kernel<<<(unsigned)nvec, 1024, 0, s>>>(X, Y, n, out);
+  count_launch();
+  CB_LAUNCH();
+  return CHASE_BSE_OK;
+}
+__global__ void lanczos_axpy_kernel(cplx* Wv, const cplx* U, const cplx* V, const cplx* Vp, const double* alpha,
+                                    const double* beta_prev, int64_t n, int64_t nvec) {
+  GRID_STRIDE(i, 2 * n * nvec) {
+    const int64_t c = i / (2 * n);
+    cplx w = csub(U[i], cscale(V[i], alpha[c]));
+    if (beta_prev) w = csub(w, cscale(Vp[i], beta_prev[c]));
+    Wv[i] = w;
+  }
+}
+int lanczos_axpy(cplx* Wv, const cplx* U, const cplx* V, const cplx* Vp, const double* alpha,
+                 const double* beta_prev, int64_t n, int64_t nvec, cudaStream_t s) {
+  lanczos_axpy_kernel<<<gs(2 * n * nvec), 256, 0, s>>>(Wv, U, V, Vp, alpha, beta_prev, n, nvec);
+  count_launch();
+  CB_LAUNCH();
+  return CHASE_BSE_OK;
+}
+__global__ void lanczos_beta_kernel(double* beta, const double* nrm2, int64_t nvec) {
+  const int64_t c = threadIdx.x;
+  if (c < nvec) beta[c] = sqrt(nrm2[c] > 0.0 ? nrm2[c] : 0.0);
+}
+__global__ void lanczos_scale_kernel(const double* beta, const cplx* Wv, const cplx* Y, cplx* V, cplx* U,
+                                     int64_t n, int64_t nvec) {
+  GRID_STRIDE(i, 2 * n * nvec) {
+    const int64_t c = i / (2 * n);
+    const double b = beta[c];
+    const double inv = b > 0.0 ? 1.0 / b : 0.0;
+    V[i] = cscale(Wv[i], inv);
+    U[i] = cscale(Y[i], inv);
+  }
+}
+int lanczos_normalise(double* beta, const double* nrm2, const cplx* Wv, const cplx* Y, cplx* V, cplx* U,
+                      int64_t n, int64_t nvec, cudaStream_t s) {
+  lanczos_beta_kernel<<<1, 64, 0, s>>>(beta, nrm2, nvec);
+  count_launch();
+  lanczos_scale_kernel<<<gs(2 * n * nvec), 256, 0, s>>>(beta, Wv, Y, V, U, n, nvec);
+  count_launch();
+  CB_LAUNCH();
+  return CHASE_BSE_OK;
+}
+
+// ------------------------------------------------- counter-based normals
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): 10 rounds of the
+// multiply-xor round with multipliers 0xD2511F53 / 0xCD9E8D57 and Weyl key
+// increments 0x9E3779B9 / 0xBB67AE85.  Two uniforms -> one complex normal by
+// Box-Muller (re, im independent N(0, 1)).
+__device__ __forceinline__ uint4 philox4x32_10(uint4 ctr, uint2 key) {
+#pragma unroll
+  for (int i = 0; i < 10; ++i) {
+    const unsigned lo0 = 0xD2511F53u * ctr.x, hi0 = __umulhi(0xD2511F53u, ctr.x);
+    const unsigned lo1 = 0xCD9E8D57u * ctr.z, hi1 = __umulhi(0xCD9E8D57u, ctr.z);
+    ctr = make_uint4(hi1 ^ ctr.y ^ key.x, lo1, hi0 ^ ctr.w ^ key.y, lo0);
+    key.x += 0x9E3779B9u;
+    key.y += 0xBB67AE85u;
+  }
+  return ctr;
+}
+__global__ void randn_complex_kernel(cplx* out, int64_t count, uint64_t seed, uint64_t sid) {
+  GRID_STRIDE(i, count) {
+    const uint4 r = philox4x32_10(make_uint4((unsigned)i, (unsigned)(i >> 32), (unsigned)sid, (unsigned)(sid >> 32)),
+                                  make_uint2((unsigned)seed, (unsigned)(seed >> 32)));
+    const double u1 = ((double)r.x + (double)r.y * 4294967296.0 + 1.0) / 18446744073709551616.0;  // (0, 1]
+    const double u2 = ((double)r.z + (double)r.w * 4294967296.0) / 18446744073709551616.0;        // [0, 1)
+    const double rad = sqrt(-2.0 * log(u1));
+    double sn, cs;
+    sincospi(2.0 * u2, &sn, &cs);
+    out[i] = mk(rad * cs, rad * sn);
+  }
+}
+int randn_complex(cplx* out, int64_t count, uint64_t seed, uint64_t sid, cudaStream_t s) {
+  if (count == 0) return CHASE_BSE_OK;
+  randn_complex_kernel<<<gs(count), 256, 0, s>>>(out, count, seed, sid);
+  count_launch();
+  CB_LAUNCH();
+  return CHASE_BSE_OK;
+}
+
+// ------------------------------------------------------------------ gradient
+__global__ void grad_coef_kernel(const cplx* V, const double* w, int64_t n, double* cbuf) {
+  __shared__ double sh[32];
+  const int64_t m = blockIdx.x;
+  const cplx* v = V + m * 2 * n;
+  double acc = 0.0;
+  for (int64_t r = threadIdx.x; r < 2 * n; r += blockDim.x) acc += (r < n) ? cabs2(v[r]) : -cabs2(v[r]);
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) cbuf[m] = w[m] / acc;  // c_m = w_m / (|x|^2 - |y|^2)
+}
+__global__ void grad_pack_kernel(const cplx* V, const double* cbuf, int64_t n, int64_t nev, cplx* Uc, cplx* U2,
+                                 cplx* Ub, cplx* U3) {
+  GRID_STRIDE(i, n * nev) {
+    const int64_t r = i % n, m = i / n;
+    const cplx x = V[m * 2 * n + r], y = V[m * 2 * n + n + r];
+    const double c = cbuf[m];
+    const int64_t a = r + m * n, b = r + (m + nev) * n;
+    Uc[a] = cscale(cconj(x), c);
+    Uc[b] = cscale(y, c);
+    U2[a] = x;
+    U2[b] = cconj(y);
+    Ub[a] = cscale(x, c);
+    Ub[b] = cscale(cconj(y), c);
+    U3[a] = cconj(y);
+    U3[b] = x;
+  }
+}
+int grad_prepare(const cplx* V, const double* w, int64_t n, int64_t nev, double* cbuf, cplx* Uc, cplx* U2,
+                 cplx* Ub, cplx* U3, cudaStream_t s) {
+  grad_coef_kernel<<<(unsigned)nev, 256, 0, s>>>(V, w, n, cbuf);
+  count_launch();
+  grad_pack_kernel<<<gs(n * nev), 256, 0, s>>>(V, cbuf, n, nev, Uc, U2, Ub, U3);
+  count_launch();
+  CB_LAUNCH();
+  return CHASE_BSE_OK;
+}
+
+}  // namespace cb

@@ -1,0 +1,59 @@
+// Small dense FP64 kernels: Cholesky, triangular inverse, Jacobi eigensolver,
+// Householder QR, Lanczos pieces and column utilities.  Matrices are
+// column-major complex128 unless stated otherwise.
+#pragma once
+#include "common.cuh"
+
+namespace cb {
+
+// Blocked Cholesky G = L L^* in place (lower triangle; strict upper zeroed).
+// *info_host = 0 on success, j+1 if the j-th pivot is not positive (or NaN).
+int cholesky(cplx* G, int64_t k, int* info_dev, int* info_host, cudaStream_t s);
+// X = L^{-1} for lower-triangular L (k x k); T is k*32 complex scratch.
+int tri_inverse(const cplx* L, int64_t k, cplx* X, cplx* T, cudaStream_t s);
+
+// Cyclic Jacobi on hermitian G (k x k, k even, overwritten by its diagonal form);
+// V receives the eigenvectors (columns).  theta[k] (device) gets diag(G).
+// rot is k/2 * 4 complex scratch, red 2 doubles scratch.
+int jacobi_eigh(cplx* G, int64_t k, cplx* V, double* theta, cplx* rot, double* red,
+                int max_sweeps, int* sweeps_out, cudaStream_t s);
+
+// Unblocked Householder QR: Q (N x m, column-major, ld N) receives the
+// orthonormal factor of X (N x m), which is destroyed.  Vs: N*m, Us: N*m,
+// wrow: m complex scratch.
+int householder_qr(cplx* X, int64_t N, int64_t m, cplx* Q, cplx* Vs, cplx* Us, cplx* wrow,
+                   cudaStream_t s);
+
+// ---- utilities ----
+int scale_lower(cplx* W, int64_t n, int64_t k, double gamma, cudaStream_t s);
+// X = [S Yp, S K conj(Yp), Wf, K conj(Wf)]  (2n x (2L + 2kf))
+int build_qr_input(cplx* X, const cplx* Yp, int64_t L, const cplx* Wf, int64_t kf, int64_t n,
+                   cudaStream_t s);
+int gather_cols(cplx* dst, const cplx* src, const int* idx, int64_t rows, int64_t m, cudaStream_t s);
+// dst[:, j] = src_j[:, j] with src_j = bufs[sel[j]]  (collect filter outputs)
+int collect_cols(cplx* dst, const cplx* b0, const cplx* b1, const cplx* b2, const int* sel,
+                 int64_t rows, int64_t m, cudaStream_t s);
+int scatter_cols(cplx* dst, const cplx* src, const int* idx, int64_t rows, int64_t m, cudaStream_t s);
+int col_norms(const cplx* X, int64_t rows, int64_t m, double* out, cudaStream_t s);
+int normalize_cols(cplx* X, int64_t rows, int64_t m, cudaStream_t s);
+int set_identity(cplx* M, int64_t k, cudaStream_t s);
+int hermitize(cplx* G, int64_t k, cudaStream_t s);
+int diag_real(const cplx* G, int64_t k, double* out, cudaStream_t s);
+int phase_fix(cplx* V, int64_t n, int64_t m, cudaStream_t s);
+int copy_cols(cplx* dst, int64_t ldd, const cplx* src, int64_t lds, int64_t rows, int64_t m,
+              cudaStream_t s);
+// Lanczos pieces (per column c of nvec): out[c] = Re(x_c^* S y_c)
+int sdot_real(const cplx* X, const cplx* Y, int64_t n, int64_t nvec, double* out, cudaStream_t s);
+// Wv = U - alpha V - beta_prev Vp (beta_prev may be NULL)
+int lanczos_axpy(cplx* Wv, const cplx* U, const cplx* V, const cplx* Vp, const double* alpha,
+                 const double* beta_prev, int64_t n, int64_t nvec, cudaStream_t s);
+// beta = sqrt(max(nrm2, 0)); V = Wv / beta; U = Y / beta
+int lanczos_normalise(double* beta, const double* nrm2, const cplx* Wv, const cplx* Y, cplx* V,
+                      cplx* U, int64_t n, int64_t nvec, cudaStream_t s);
+// Counter-based standard normal draws (Philox4x32-10 + Box-Muller): out[i] = N(0,1) + i N(0,1)
+int randn_complex(cplx* out, int64_t count, uint64_t seed, uint64_t stream_id, cudaStream_t s);
+// Gradient helpers: Uc = [conj(X) c, Y c], U2 = [X, conj(Y)], Ub = [X c, conj(Y) c], U3 = [conj(Y), X]
+int grad_prepare(const cplx* V, const double* w, int64_t n, int64_t nev, double* cbuf, cplx* Uc,
+                 cplx* U2, cplx* Ub, cplx* U3, cudaStream_t s);
+
+}  // namespace cb

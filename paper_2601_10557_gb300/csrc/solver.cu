@@ -1,0 +1,646 @@
+// Host driver of the pseudo-hermitian ChASE solver (Algorithm 3) and its stages.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "dense_kernels.cuh"
+#include "fp64_kernels.cuh"
+#include "solver.cuh"
+
+namespace cb {
+
+static std::atomic<int64_t> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
+bool verbose() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = getenv("CHASE_BSE_VERBOSE");
+    v = (e && e[0] && e[0] != '0') ? 1 : 0;
+  }
+  return v == 1;
+}
+
+// ------------------------------------------------------------------- filter
+// FP64 three-term recurrence on H^2 over columns sorted by descending degree:
+// at step j only the prefix of columns with deg >= j+1 is active.  Y_j lives in
+// buffer j mod 3; a finished column keeps its last iterate in buffer deg mod 3.
+static int filter_fp64_sorted(const cplx* A, const cplx* B, int64_t n, cplx* Y0, int64_t k, const int* degs,
+                              double mu1, double mu_nevex, double muN, cplx* out, Workspace& ws, cudaStream_t s,
+                              FilterStats* fs) {
+  const int64_t n2 = 2 * n;
+  cplx *Y1, *Y2, *T;
+  CB_TRY(ws.alloc(&Y1, n2 * k));
+  CB_TRY(ws.alloc(&Y2, n2 * k));
+  CB_TRY(ws.alloc(&T, n2 * k));
+  cplx* Yb[3] = {Y0, Y1, Y2};
+  const double a = mu_nevex * mu_nevex, b = muN * muN;
+  const double c = 0.5 * (a + b), e = 0.5 * (b - a);
+  const double sigma1 = e / (mu1 * mu1 - c);
+  const double tau = 2.0 / sigma1;
+  double sigma = sigma1;
+  const int maxdeg = degs[0];
+  cudaEvent_t e0, e1;
+  CB_CUDA(cudaEventCreate(&e0));
+  CB_CUDA(cudaEventCreate(&e1));
+  CB_CUDA(cudaEventRecord(e0, s));
+  for (int j = 0; j < maxdeg; ++j) {
+    int64_t kj = 0;
+    while (kj < k && degs[kj] >= j + 1) ++kj;
+    cplx* cur = Yb[j % 3];
+    cplx* nxt = Yb[(j + 1) % 3];
+    cplx* prev = Yb[(j + 2) % 3];
+    HopArgs h{};
+    h.A = A; h.B = B; h.n = n; h.W = cur; h.k = kj; h.out = T; h.mode = HOP_STORE;
+    CB_TRY(hop_fp64(h, s));
+    double alpha, beta;
+    if (j == 0) {
+      alpha = sigma1 / e;
+      beta = 0.0;
+    } else {
+      const double sn = 1.0 / (tau - sigma);
+      alpha = 2.0 * sn / e;
+      beta = -sigma * sn;
+      sigma = sn;
+    }
+    HopArgs g{};
+    g.A = A; g.B = B; g.n = n; g.W = T; g.k = kj; g.out = nxt; g.mode = HOP_CHEB;
+    g.alpha = alpha; g.beta = beta; g.c = c; g.Wc = cur; g.Wp = prev;
+    CB_TRY(hop_fp64(g, s));
+    if (fs) {
+      fs->flops += 64.0 * (double)n * (double)n * (double)kj;
+      fs->flops_fp64 += 64.0 * (double)n * (double)n * (double)kj;
+      fs->launches += 2;
+    }
+  }
+  CB_CUDA(cudaEventRecord(e1, s));
+  std::vector<int> sel(k);
+  for (int64_t i = 0; i < k; ++i) sel[i] = degs[i] % 3;
+  int* dsel;
+  CB_TRY(ws.alloc(&dsel, k));
+  CB_CUDA(cudaMemcpyAsync(dsel, sel.data(), sizeof(int) * k, cudaMemcpyHostToDevice, s));
+  CB_TRY(collect_cols(out, Yb[0], Yb[1], Yb[2], dsel, n2, k, s));
+  if (fs) {
+    CB_CUDA(cudaEventSynchronize(e1));
+    float ms = 0;
+    CB_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    fs->ms_fp64 += ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return CHASE_BSE_OK;
+}
+
+int filter(const cplx* A, const cplx* B, int64_t n, cplx* W, int64_t k, const int* degs, const int* prec,
+           double mu1, double mu_nevex, double muN, cudaStream_t s, FilterStats* fs) {
+  if (k == 0) return CHASE_BSE_OK;
+  const int64_t n2 = 2 * n;
+  Workspace ws(s);
+  // group 0: FP64 columns, group 1: mixed columns; each sorted by descending degree
+  for (int grp = 0; grp < 2; ++grp) {
+    std::vector<int> idx;
+    for (int64_t i = 0; i < k; ++i)
+      if ((prec ? prec[i] : 0) == grp) idx.push_back((int)i);
+    if (idx.empty()) continue;
+    std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return degs[x] > degs[y]; });
+    const int64_t m = (int64_t)idx.size();
+    std::vector<int> ds(m);
+    for (int64_t i = 0; i < m; ++i) ds[i] = degs[idx[i]];
+    int* didx;
+    cplx *Y0, *out;
+    Workspace gws(s);
+    CB_TRY(gws.alloc(&didx, m));
+    CB_TRY(gws.alloc(&Y0, n2 * m));
+    CB_TRY(gws.alloc(&out, n2 * m));
+    CB_CUDA(cudaMemcpyAsync(didx, idx.data(), sizeof(int) * m, cudaMemcpyHostToDevice, s));
+    CB_TRY(gather_cols(Y0, W, didx, n2, m, s));
+    if (grp == 0) {
+      CB_TRY(filter_fp64_sorted(A, B, n, Y0, m, ds.data(), mu1, mu_nevex, muN, out, gws, s, fs));
+    } else {
+      if (!mixed_available()) return CHASE_BSE_UNSUPPORTED;
+      CB_TRY(filter_mixed_sorted(A, B, n, Y0, m, ds.data(), mu1, mu_nevex, muN, out, s, fs));
+    }
+    CB_TRY(scatter_cols(W, out, didx, n2, m, s));
+    // host vectors idx/ds must outlive the async copies: synchronise before they go
+    CB_CUDA(cudaStreamSynchronize(s));
+  }
+  return CHASE_BSE_OK;
+}
+
+// ------------------------------------------------------------------ Lanczos
+// Jacobi eigen-decomposition of a small real symmetric matrix (host; used only
+// for the Lanczos tridiagonal matrices, at most a few dozen rows).
+static void host_sym_eig(std::vector<double>& a, int m, std::vector<double>& w, std::vector<double>& v) {
+  v.assign((size_t)m * m, 0.0);
+  for (int i = 0; i < m; ++i) v[(size_t)i * m + i] = 1.0;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j) {
+        tot += a[(size_t)i * m + j] * a[(size_t)i * m + j];
+        if (i != j) off += a[(size_t)i * m + j] * a[(size_t)i * m + j];
+      }
+    if (off <= 1e-30 * tot) break;
+    for (int p = 0; p < m - 1; ++p)
+      for (int q = p + 1; q < m; ++q) {
+        const double apq = a[(size_t)p * m + q];
+        if (apq == 0.0) continue;
+        const double tau = (a[(size_t)q * m + q] - a[(size_t)p * m + p]) / (2.0 * apq);
+        const double t = (tau >= 0 ? 1.0 : -1.0) / (std::fabs(tau) + std::sqrt(1.0 + tau * tau));
+        const double c = 1.0 / std::sqrt(1.0 + t * t), sn = t * c;
+        for (int r = 0; r < m; ++r) {  // columns p, q
+          const double x = a[(size_t)r * m + p], y = a[(size_t)r * m + q];
+          a[(size_t)r * m + p] = c * x - sn * y;
+          a[(size_t)r * m + q] = sn * x + c * y;
+        }
+        for (int r = 0; r < m; ++r) {  // rows p, q
+          const double x = a[(size_t)p * m + r], y = a[(size_t)q * m + r];
+          a[(size_t)p * m + r] = c * x - sn * y;
+          a[(size_t)q * m + r] = sn * x + c * y;
+        }
+        for (int r = 0; r < m; ++r) {
+          const double x = v[(size_t)r * m + p], y = v[(size_t)r * m + q];
+          v[(size_t)r * m + p] = c * x - sn * y;
+          v[(size_t)r * m + q] = sn * x + c * y;
+        }
+      }
+  }
+  w.resize(m);
+  for (int i = 0; i < m; ++i) w[i] = a[(size_t)i * m + i];
+}
+
+int lanczos_bounds(const cplx* A, const cplx* B, int64_t n, const cplx* V0, int64_t nvec, int steps,
+                   int64_t nevex, double out[4], cudaStream_t s) {
+  const int64_t n2 = 2 * n, sz = n2 * nvec;
+  Workspace ws(s);
+  cplx *Vp, *V, *U, *Wv, *Y;
+  double *alpha, *beta, *nrm2, *b0;
+  CB_TRY(ws.alloc(&Vp, sz));
+  CB_TRY(ws.alloc(&V, sz));
+  CB_TRY(ws.alloc(&U, sz));
+  CB_TRY(ws.alloc(&Wv, sz));
+  CB_TRY(ws.alloc(&Y, sz));
+  CB_TRY(ws.alloc(&alpha, (size_t)steps * nvec));
+  CB_TRY(ws.alloc(&beta, (size_t)steps * nvec));
+  CB_TRY(ws.alloc(&nrm2, nvec));
+  CB_TRY(ws.alloc(&b0, nvec));
+  CB_CUDA(cudaMemcpyAsync(Wv, V0, sizeof(cplx) * sz, cudaMemcpyDeviceToDevice, s));
+  HopArgs h{};
+  h.A = A; h.B = B; h.n = n; h.k = nvec; h.mode = HOP_STORE;
+  h.W = Wv; h.out = Y;
+  CB_TRY(hop_fp64(h, s));
+  CB_TRY(sdot_real(Wv, Y, n, nvec, nrm2, s));
+  CB_TRY(lanczos_normalise(b0, nrm2, Wv, Y, V, U, n, nvec, s));
+  for (int j = 0; j < steps; ++j) {
+    CB_TRY(sdot_real(U, U, n, nvec, alpha + (size_t)j * nvec, s));  // alpha_j = u^* S u, u = H v
+    CB_TRY(lanczos_axpy(Wv, U, V, Vp, alpha + (size_t)j * nvec, j > 0 ? beta + (size_t)(j - 1) * nvec : nullptr, n,
+                        nvec, s));
+    h.W = Wv; h.out = Y;
+    CB_TRY(hop_fp64(h, s));
+    CB_TRY(sdot_real(Wv, Y, n, nvec, nrm2, s));
+    std::swap(Vp, V);
+    CB_TRY(lanczos_normalise(beta + (size_t)j * nvec, nrm2, Wv, Y, V, U, n, nvec, s));
+  }
+  std::vector<double> ha((size_t)steps * nvec), hb((size_t)steps * nvec);
+  CB_CUDA(cudaMemcpyAsync(ha.data(), alpha, sizeof(double) * ha.size(), cudaMemcpyDeviceToHost, s));
+  CB_CUDA(cudaMemcpyAsync(hb.data(), beta, sizeof(double) * hb.size(), cudaMemcpyDeviceToHost, s));
+  CB_CUDA(cudaStreamSynchronize(s));
+  double mu1 = INFINITY, muN = 0.0, rhat = 0.0;
+  std::vector<std::pair<double, double>> pos;  // (theta, weight) over theta > 0
+  for (int64_t cidx = 0; cidx < nvec; ++cidx) {
+    int m = steps;
+    for (int j = 0; j < steps; ++j)
+      if (!(hb[(size_t)j * nvec + cidx] > 0.0) && j + 1 < steps) { m = j + 1; break; }
+    std::vector<double> T((size_t)m * m, 0.0), w, v;
+    for (int j = 0; j < m; ++j) {
+      T[(size_t)j * m + j] = ha[(size_t)j * nvec + cidx];
+      if (j + 1 < m) {
+        T[(size_t)j * m + j + 1] = hb[(size_t)j * nvec + cidx];
+        T[(size_t)(j + 1) * m + j] = hb[(size_t)j * nvec + cidx];
+      }
+    }
+    host_sym_eig(T, m, w, v);
+    double mx = 0.0;
+    for (int i = 0; i < m; ++i) {
+      mu1 = std::min(mu1, std::fabs(w[i]));
+      mx = std::max(mx, std::fabs(w[i]));
+      // weight tau_j / theta_j: the S H inner product weighs eigenvalue lambda by lambda
+      if (w[i] > 0) pos.push_back({w[i], v[i] * v[i] / w[i]});  // v[i]: first row of eigenvectors
+    }
+    rhat = std::max(rhat, mx);
+    muN = std::max(muN, mx + std::fabs(hb[(size_t)(m - 1) * nvec + cidx]));
+  }
+  std::sort(pos.begin(), pos.end());
+  double tot = 0.0;
+  for (auto& p : pos) tot += p.second;
+  const double target = (double)nevex / (double)n;
+  double mu_ne = pos.empty() ? mu1 : pos.back().first;
+  double px = mu1, py = 0.0, cum = 0.0;
+  for (auto& p : pos) {
+    const double nx = p.first, ny = cum + p.second / tot;
+    if (ny >= target) {
+      mu_ne = (ny > py) ? px + (target - py) / (ny - py) * (nx - px) : nx;
+      break;
+    }
+    px = nx;
+    py = ny;
+    cum = ny;
+  }
+  out[0] = mu1;
+  out[1] = mu_ne;
+  out[2] = muN;
+  out[3] = rhat;
+  if (!(mu1 > 0) || !(mu_ne > 0) || !(muN > mu_ne) || !std::isfinite(muN)) return CHASE_BSE_NOT_DEFINITE;
+  return CHASE_BSE_OK;
+}
+
+// ----------------------------------------------------------------------- QR
+int qr(const cplx* X, int64_t n2, int64_t m, cplx* Q, int* used_hh, cudaStream_t s) {
+  *used_hh = 0;
+  Workspace ws(s);
+  cplx *G, *Linv, *T, *Q1;
+  int* info_d;
+  double* diag_d;
+  CB_TRY(ws.alloc(&G, m * m));
+  CB_TRY(ws.alloc(&Linv, m * m));
+  CB_TRY(ws.alloc(&T, m * 32));
+  CB_TRY(ws.alloc(&Q1, n2 * m));
+  CB_TRY(ws.alloc(&info_d, 1));
+  CB_TRY(ws.alloc(&diag_d, m));
+  std::vector<double> dg(m);
+  bool ok = true;
+  const cplx* src = X;
+  for (int pass = 0; pass < 2 && ok; ++pass) {
+    cplx* dst = (pass == 0) ? Q1 : Q;
+    CB_TRY(zgemm('C', 'N', m, m, n2, mk(1, 0), src, n2, src, n2, mk(0, 0), G, m, s));
+    CB_TRY(hermitize(G, m, s));
+    int info = 0;
+    CB_TRY(cholesky(G, m, info_d, &info, s));
+    if (info != 0) { ok = false; break; }
+    if (pass == 0) {
+      CB_TRY(diag_real(G, m, diag_d, s));
+      CB_CUDA(cudaMemcpyAsync(dg.data(), diag_d, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
+      CB_CUDA(cudaStreamSynchronize(s));
+      const double mx = *std::max_element(dg.begin(), dg.end());
+      const double mn = *std::min_element(dg.begin(), dg.end());
+      if (!(mn > 0.0) || (mx / mn) * (mx / mn) > 1e12) { ok = false; break; }
+    }
+    CB_TRY(tri_inverse(G, m, Linv, T, s));
+    CB_TRY(zgemm('N', 'C', n2, m, m, mk(1, 0), src, n2, Linv, m, mk(0, 0), dst, n2, s));  // X L^{-*}
+    src = Q1;
+  }
+  if (ok) return CHASE_BSE_OK;
+  // Householder fallback
+  *used_hh = 1;
+  cplx *Xc, *Vs, *Us, *wrow;
+  CB_TRY(ws.alloc(&Xc, n2 * m));
+  CB_TRY(ws.alloc(&Vs, n2 * m));
+  CB_TRY(ws.alloc(&Us, n2 * m));
+  CB_TRY(ws.alloc(&wrow, m));
+  CB_CUDA(cudaMemcpyAsync(Xc, X, sizeof(cplx) * n2 * m, cudaMemcpyDeviceToDevice, s));
+  CB_TRY(householder_qr(Xc, n2, m, Q, Vs, Us, wrow, s));
+  return CHASE_BSE_OK;
+}
+
+// --------------------------------------------------------------- Rayleigh-Ritz
+int rayleigh_ritz(const cplx* A, const cplx* B, int64_t n, const cplx* Q, int64_t k, double* ritz_host,
+                  cplx* Wpos, cudaStream_t s) {
+  if (k <= 0 || (k % 2) != 0) return CHASE_BSE_BAD_ARG;
+  const int64_t n2 = 2 * n, h = k / 2;
+  Workspace ws(s);
+  cplx *T, *M, *Linv, *M2, *Tmp, *G, *V, *Ypos, *Z, *rot, *scratch;
+  double *theta, *red;
+  int *info_d, *idx_d;
+  CB_TRY(ws.alloc(&T, n2 * k));
+  CB_TRY(ws.alloc(&M, k * k));
+  CB_TRY(ws.alloc(&Linv, k * k));
+  CB_TRY(ws.alloc(&M2, k * k));
+  CB_TRY(ws.alloc(&Tmp, k * k));
+  CB_TRY(ws.alloc(&G, k * k));
+  CB_TRY(ws.alloc(&V, k * k));
+  CB_TRY(ws.alloc(&Ypos, k * h));
+  CB_TRY(ws.alloc(&Z, k * h));
+  CB_TRY(ws.alloc(&rot, 2 * k));
+  CB_TRY(ws.alloc(&scratch, k * 32));
+  CB_TRY(ws.alloc(&theta, k));
+  CB_TRY(ws.alloc(&red, 2));
+  CB_TRY(ws.alloc(&info_d, 1));
+  CB_TRY(ws.alloc(&idx_d, h));
+  // T = S H Q (Algorithm 2, lines 1-2), M = Q^* T (line 3)
+  HopArgs a{};
+  a.A = A; a.B = B; a.n = n; a.W = Q; a.k = k; a.out = T; a.mode = HOP_STORE; a.sflip = 1;
+  CB_TRY(hop_fp64(a, s));
+  CB_TRY(zgemm('C', 'N', k, k, n2, mk(1, 0), Q, n2, T, n2, mk(0, 0), M, k, s));
+  CB_TRY(hermitize(M, k, s));
+  int info = 0;
+  CB_TRY(cholesky(M, k, info_d, &info, s));  // line 4: M = L L^*
+  if (info != 0) return CHASE_BSE_NOT_DEFINITE;
+  CB_TRY(tri_inverse(M, k, Linv, scratch, s));
+  // line 5: M2 = I - 2 Q_2^* Q_2 (= Q^* S Q)
+  CB_TRY(set_identity(M2, k, s));
+  CB_TRY(zgemm('C', 'N', k, k, n, mk(-2, 0), Q + n, n2, Q + n, n2, mk(1, 0), M2, k, s));
+  // line 7: G = L^{-1} M2 L^{-*}
+  CB_TRY(zgemm('N', 'N', k, k, k, mk(1, 0), Linv, k, M2, k, mk(0, 0), Tmp, k, s));
+  CB_TRY(zgemm('N', 'C', k, k, k, mk(1, 0), Tmp, k, Linv, k, mk(0, 0), G, k, s));
+  CB_TRY(hermitize(G, k, s));
+  // line 8: G y = theta y
+  int sweeps = 0;
+  CB_TRY(jacobi_eigh(G, k, V, theta, rot, red, 40, &sweeps, s));
+  std::vector<double> th(k);
+  CB_CUDA(cudaMemcpyAsync(th.data(), theta, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+  CB_CUDA(cudaStreamSynchronize(s));
+  // the k/2 largest theta; by Theorem positive-negative-symmetry_oblique_RR they are
+  // exactly the positive half when range(Q) is closed under W -> K conj(W)
+  std::vector<int> pos(k);
+  std::iota(pos.begin(), pos.end(), 0);
+  std::stable_sort(pos.begin(), pos.end(), [&](int x, int y) { return th[x] > th[y]; });
+  pos.resize(h);
+  if (!(th[pos[h - 1]] > 0.0)) return CHASE_BSE_QR_FAILED;  // search space lost its +- structure
+  for (int64_t i = 0; i < h; ++i) ritz_host[i] = 1.0 / th[pos[i]];
+  CB_CUDA(cudaMemcpyAsync(idx_d, pos.data(), sizeof(int) * h, cudaMemcpyHostToDevice, s));
+  CB_TRY(gather_cols(Ypos, V, idx_d, k, h, s));
+  // line 9 (read as z = L^{-*} y) and the half back-transform W+ = Q Z+
+  CB_TRY(zgemm('C', 'N', k, h, k, mk(1, 0), Linv, k, Ypos, k, mk(0, 0), Z, k, s));
+  CB_TRY(zgemm('N', 'N', n2, h, k, mk(1, 0), Q, n2, Z, k, mk(0, 0), Wpos, n2, s));
+  CB_TRY(normalize_cols(Wpos, n2, h, s));
+  CB_CUDA(cudaStreamSynchronize(s));  // pos must outlive the copy
+  return CHASE_BSE_OK;
+}
+
+int residuals(const cplx* A, const cplx* B, int64_t n, const cplx* W, const double* lambda, int64_t k, double* res,
+              cudaStream_t s) {
+  if (k == 0) return CHASE_BSE_OK;
+  Workspace ws(s);
+  cplx* R;
+  CB_TRY(ws.alloc(&R, 2 * n * k));
+  HopArgs a{};
+  a.A = A; a.B = B; a.n = n; a.W = W; a.k = k; a.out = R; a.mode = HOP_RESID; a.lambda = lambda;
+  CB_TRY(hop_fp64(a, s));
+  CB_TRY(col_norms(R, 2 * n, k, res, s));
+  return CHASE_BSE_OK;
+}
+
+int gradient(const cplx* V, const double* w, int64_t n, int64_t nev, cplx* gA, cplx* gB, cudaStream_t s) {
+  Workspace ws(s);
+  cplx *Uc, *U2, *Ub, *U3;
+  double* cbuf;
+  const int64_t sz = n * 2 * nev;
+  CB_TRY(ws.alloc(&Uc, sz));
+  CB_TRY(ws.alloc(&U2, sz));
+  CB_TRY(ws.alloc(&Ub, sz));
+  CB_TRY(ws.alloc(&U3, sz));
+  CB_TRY(ws.alloc(&cbuf, nev));
+  CB_TRY(grad_prepare(V, w, n, nev, cbuf, Uc, U2, Ub, U3, s));
+  // row-major gA is the column-major conj(gA) = Uc U2^T; row-major gB = gB = Ub U3^T
+  CB_TRY(zgemm('N', 'T', n, n, 2 * nev, mk(1, 0), Uc, n, U2, n, mk(0, 0), gA, n, s));
+  CB_TRY(zgemm('N', 'T', n, n, 2 * nev, mk(1, 0), Ub, n, U3, n, mk(0, 0), gB, n, s));
+  return CHASE_BSE_OK;
+}
+
+// -------------------------------------------------------------------- solve
+namespace {
+struct PhaseClock {
+  cudaStream_t s;
+  cudaEvent_t a, b;
+  explicit PhaseClock(cudaStream_t st) : s(st) {
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+  }
+  ~PhaseClock() {
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+  }
+  void start() { cudaEventRecord(a, s); }
+  double stop() {
+    cudaEventRecord(b, s);
+    cudaEventSynchronize(b);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, a, b);
+    return ms;
+  }
+};
+
+// Per-vector degree from the convergence rate: predicted rate per H^2 step
+// rho = 1/(|t| + sqrt(t^2 - 1)), t = (lambda^2 - c)/e, replaced by the observed
+// rate (r/r_prev)^(1/deg_prev) when that is slower; deg = ceil(ln(tol/r)/ln rho) + 1.
+void degrees_update(const std::vector<double>& ritz, const std::vector<double>& res,
+                    const std::vector<double>& prev_res, const std::vector<int>& prev_deg, double tol, double mu_ne,
+                    double muN, int dmin, int dmax, std::vector<int>& degs) {
+  const double a = mu_ne * mu_ne, b = muN * muN;
+  const double c = 0.5 * (a + b), e = 0.5 * (b - a);
+  degs.resize(ritz.size());
+  for (size_t i = 0; i < ritz.size(); ++i) {
+    const double t = (ritz[i] * ritz[i] - c) / e;
+    const double r = res[i];
+    double rho = (std::fabs(t) <= 1.0) ? 1.0 : 1.0 / (std::fabs(t) + std::sqrt(t * t - 1.0));
+    if (std::isfinite(prev_res[i]) && r > 0.0 && r < prev_res[i])
+      rho = std::max(rho, std::pow(r / prev_res[i], 1.0 / prev_deg[i]));
+    int d;
+    if (!(r > tol)) d = dmin;
+    else if (rho >= 1.0) d = dmax;
+    else d = (int)std::ceil(std::log(tol / r) / std::log(rho)) + 1;
+    degs[i] = std::min(std::max(d, dmin), dmax);
+  }
+}
+}  // namespace
+
+int solve(const cplx* A, const cplx* B, int64_t n, int64_t nev, int64_t nex, int deg, double tol,
+          const chase_bse_opts* opts_in, double* evals, cplx* evecs, chase_bse_stats* stats) {
+  chase_bse_opts o{};
+  o.size = sizeof(o);
+  o.precision = CHASE_BSE_FP64;
+  o.maxiter = 25;
+  o.deg_min = deg;
+  o.deg_max = deg;
+  o.lanczos_steps = 26;
+  o.lanczos_vecs = 4;
+  o.gamma = 1e-3;
+  o.switch_tol = 1e-5;
+  o.seed = 0;
+  if (opts_in) {
+    if (opts_in->size != sizeof(chase_bse_opts)) return CHASE_BSE_BAD_ARG;
+    o = *opts_in;
+  }
+  if (!A || !B || !evals || !evecs || n < 1 || nev < 1 || nex < 0 || nev + nex > n || deg < 1 || !(tol > 0) ||
+      o.maxiter < 1 || o.deg_min < 1 || o.deg_max < o.deg_min || o.lanczos_steps < 2 || o.lanczos_vecs < 1 ||
+      o.lanczos_vecs > 64 ||
+      (o.precision != CHASE_BSE_FP64 && o.precision != CHASE_BSE_MIXED_BF16X3))
+    return CHASE_BSE_BAD_ARG;
+  if (o.precision == CHASE_BSE_MIXED_BF16X3 && !mixed_available()) return CHASE_BSE_UNSUPPORTED;
+  cudaStream_t s = (cudaStream_t)o.stream;
+  const int64_t n2 = 2 * n, nevex = nev + nex;
+  chase_bse_stats st{};
+  st.size = sizeof(st);
+  auto t_start = std::chrono::steady_clock::now();
+  Workspace ws(s);
+  cplx *W, *Ylock, *X, *Qf, *Wpos, *V0;
+  double *lam_d, *res_d;
+  CB_TRY(ws.alloc(&W, n2 * nevex));
+  CB_TRY(ws.alloc(&Ylock, n2 * nev));
+  CB_TRY(ws.alloc(&X, n2 * 2 * nevex));
+  CB_TRY(ws.alloc(&Qf, n2 * 2 * nevex));
+  CB_TRY(ws.alloc(&Wpos, n2 * nevex));
+  CB_TRY(ws.alloc(&V0, n2 * o.lanczos_vecs));
+  CB_TRY(ws.alloc(&lam_d, nevex));
+  CB_TRY(ws.alloc(&res_d, nevex));
+  PhaseClock clk(s);
+
+  // Algorithm 3 line 1: W+ = randn(2n, nevex), lower half scaled by gamma
+  if (o.W0) CB_CUDA(cudaMemcpyAsync(W, o.W0, sizeof(cplx) * n2 * nevex, cudaMemcpyDeviceToDevice, s));
+  else CB_TRY(randn_complex(W, n2 * nevex, o.seed, 1, s));
+  CB_TRY(scale_lower(W, n, nevex, o.gamma, s));
+  if (o.V0) CB_CUDA(cudaMemcpyAsync(V0, o.V0, sizeof(cplx) * n2 * o.lanczos_vecs, cudaMemcpyDeviceToDevice, s));
+  else CB_TRY(randn_complex(V0, n2 * o.lanczos_vecs, o.seed, 2, s));
+
+  // line 2: spectral bounds
+  clk.start();
+  double mu[4];
+  CB_TRY(lanczos_bounds(A, B, n, V0, o.lanczos_vecs, o.lanczos_steps, nevex, mu, s));
+  st.ms_lanczos = clk.stop();
+  double mu1 = mu[0], mu_ne = mu[1], muN = mu[2];
+  const double rhat = mu[3];
+  // mu_1 is the normalisation point p(mu_1^2) = 1 and must stay below mu_nevex
+  mu1 = std::min(mu1, 0.5 * mu_ne);
+
+  int64_t locked = 0;
+  std::vector<double> lam_locked;
+  std::vector<int> degs(nevex, deg), prec(nevex, o.precision == CHASE_BSE_MIXED_BF16X3 ? 1 : 0);
+  std::vector<double> prev_res(nevex, INFINITY);
+  int it = 0;
+  FilterStats fs;
+  int status = CHASE_BSE_OK;
+  while (locked < nev && it < o.maxiter) {
+    ++it;
+    const int64_t kf = nevex - locked;
+    // line 4: W+ <- p(H^2) W+
+    clk.start();
+    CB_TRY(filter(A, B, n, W, kf, degs.data(), prec.data(), mu1, mu_ne, muN, s, &fs));
+    st.ms_filter += clk.stop();
+    // lines 5-7: W- = K conj(W+), Q = [S Y+, S Y-, W+, W-] R^{-1}, drop the locked part
+    clk.start();
+    CB_TRY(build_qr_input(X, Ylock, locked, W, kf, n, s));
+    int hh = 0;
+    CB_TRY(qr(X, n2, 2 * nevex, Qf, &hh, s));
+    st.householder += hh;
+    st.ms_qr += clk.stop();
+    const cplx* Q = Qf + 2 * locked * n2;
+    // lines 8-10: Rayleigh-Ritz, W+ = Q Z+
+    clk.start();
+    std::vector<double> ritz(kf);
+    int rs = rayleigh_ritz(A, B, n, Q, 2 * kf, ritz.data(), Wpos, s);
+    st.ms_rr += clk.stop();
+    if (rs != CHASE_BSE_OK) { status = rs; break; }
+    // line 11: residuals of the positive half
+    clk.start();
+    CB_CUDA(cudaMemcpyAsync(lam_d, ritz.data(), sizeof(double) * kf, cudaMemcpyHostToDevice, s));
+    CB_TRY(residuals(A, B, n, Wpos, lam_d, kf, res_d, s));
+    std::vector<double> res(kf);
+    CB_CUDA(cudaMemcpyAsync(res.data(), res_d, sizeof(double) * kf, cudaMemcpyDeviceToHost, s));
+    CB_CUDA(cudaStreamSynchronize(s));
+    st.ms_resid += clk.stop();
+    for (auto& r : res) r /= rhat;
+    if (verbose()) {
+      double mx = 0;
+      for (auto r : res) mx = std::max(mx, r);
+      fprintf(stderr, "[chase_bse] it %d locked %ld kf %ld res0 %.3e resmax %.3e mu %.6g %.6g %.6g hh %d\n", it,
+              (long)locked, (long)kf, res[0], mx, mu1, mu_ne, muN, hh);
+    }
+    // lines 12-14: lock converged positive pairs
+    const int64_t want = std::min<int64_t>(nev - locked, kf);
+    std::vector<int> conv, keep;
+    for (int64_t i = 0; i < kf; ++i) {
+      if (i < want && res[i] <= tol) conv.push_back((int)i);
+      else keep.push_back((int)i);
+    }
+    int* idx_d;
+    Workspace its(s);
+    CB_TRY(its.alloc(&idx_d, kf));
+    if (!conv.empty()) {
+      CB_CUDA(cudaMemcpyAsync(idx_d, conv.data(), sizeof(int) * conv.size(), cudaMemcpyHostToDevice, s));
+      CB_TRY(gather_cols(Ylock + locked * n2, Wpos, idx_d, n2, (int64_t)conv.size(), s));
+      for (int i : conv) lam_locked.push_back(ritz[i]);
+      locked += (int64_t)conv.size();
+    }
+    if (!keep.empty()) {
+      CB_CUDA(cudaMemcpyAsync(idx_d, keep.data(), sizeof(int) * keep.size(), cudaMemcpyHostToDevice, s));
+      CB_TRY(gather_cols(W, Wpos, idx_d, n2, (int64_t)keep.size(), s));
+    }
+    CB_CUDA(cudaStreamSynchronize(s));
+    if (locked >= nev || keep.empty()) break;
+    // filter bounds and per-vector degrees for the next iteration
+    std::vector<double> kr, kres, kprev;
+    std::vector<int> kdeg;
+    for (int i : keep) {
+      kr.push_back(ritz[i]);
+      kres.push_back(res[i]);
+      kprev.push_back(prev_res[i]);
+      kdeg.push_back(degs[i]);
+    }
+    // mu_nevex <- largest non-locked Ritz value below mu_N (larger ones are spurious)
+    double cand = -1.0;
+    for (double r : kr)
+      if (r < muN) cand = std::max(cand, r);
+    if (cand > 0.0) mu_ne = cand;
+    if (ritz[0] > 0.0) mu1 = std::min(mu1, ritz[0]);
+    mu1 = std::min(mu1, 0.5 * mu_ne);
+    degrees_update(kr, kres, kprev, kdeg, tol, mu_ne, muN, o.deg_min, o.deg_max, degs);
+    std::vector<int> nprec(keep.size(), 0);
+    if (o.precision == CHASE_BSE_MIXED_BF16X3) {
+      for (size_t i = 0; i < keep.size(); ++i) {
+        const bool near = kres[i] <= o.switch_tol;
+        const bool stalled = std::isfinite(kprev[i]) && kres[i] > 0.5 * kprev[i];
+        nprec[i] = (near || stalled || prec[keep[i]] == 0) ? 0 : 1;
+      }
+    }
+    prec = nprec;
+    prev_res = kres;
+  }
+  st.iterations = it;
+  // output: the nev smallest locked pairs in ascending order
+  const int64_t nout = std::min<int64_t>(locked, nev);
+  std::vector<int> order(locked);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return lam_locked[x] < lam_locked[y]; });
+  if (nout > 0) {
+    int* od;
+    Workspace ows(s);
+    CB_TRY(ows.alloc(&od, nout));
+    std::vector<double> lo(nout);
+    for (int64_t i = 0; i < nout; ++i) lo[i] = lam_locked[order[i]];
+    CB_CUDA(cudaMemcpyAsync(od, order.data(), sizeof(int) * nout, cudaMemcpyHostToDevice, s));
+    CB_TRY(gather_cols(evecs, Ylock, od, n2, nout, s));
+    CB_TRY(phase_fix(evecs, n, nout, s));
+    CB_CUDA(cudaMemcpyAsync(evals, lo.data(), sizeof(double) * nout, cudaMemcpyHostToDevice, s));
+    // residual of the returned pairs
+    CB_TRY(residuals(A, B, n, evecs, evals, nout, res_d, s));
+    std::vector<double> rr(nout);
+    CB_CUDA(cudaMemcpyAsync(rr.data(), res_d, sizeof(double) * nout, cudaMemcpyDeviceToHost, s));
+    CB_CUDA(cudaStreamSynchronize(s));
+    for (auto r : rr) st.max_residual = std::max(st.max_residual, r / rhat);
+  }
+  CB_CUDA(cudaStreamSynchronize(s));
+  st.converged = (int32_t)nout;
+  st.mu1 = mu1;
+  st.mu_nevex = mu_ne;
+  st.muN = muN;
+  st.rho_hat = rhat;
+  st.filter_flops = fs.flops;
+  st.filter_flops_fp64 = fs.flops_fp64;
+  st.ms_filter_fp64 = fs.ms_fp64;
+  st.filter_launches = fs.launches;
+  st.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+  if (stats) {
+    if (stats->size != sizeof(chase_bse_stats)) return CHASE_BSE_BAD_ARG;
+    *stats = st;
+  }
+  if (status != CHASE_BSE_OK) return status;
+  return (nout < nev) ? CHASE_BSE_NOT_CONVERGED : CHASE_BSE_OK;
+}
+
+}  // namespace cb

@@ -1,0 +1,45 @@
+// Host-side stages of the solver (each runs its kernels on one stream).
+#pragma once
+#include <vector>
+#include "common.cuh"
+
+namespace cb {
+
+struct FilterStats {
+  double flops = 0, flops_fp64 = 0, ms_fp64 = 0;
+  int64_t launches = 0;
+};
+
+// Chebyshev filter on H^2, in place on W (2n x k); degs/prec are per column
+// (host).  prec[i] = 0: FP64 path, 1: mixed (tcgen05 BF16x3) path.
+int filter(const cplx* A, const cplx* B, int64_t n, cplx* W, int64_t k, const int* degs, const int* prec,
+           double mu1, double mu_nevex, double muN, cudaStream_t s, FilterStats* fs);
+
+// Lanczos bounds: mu1, mu_nevex, muN and rho_hat (max |theta|).
+int lanczos_bounds(const cplx* A, const cplx* B, int64_t n, const cplx* V0, int64_t nvec, int steps,
+                   int64_t nevex, double out[4], cudaStream_t s);
+
+// Orthonormal Q (2n x m) of X (2n x m; X is preserved).  *used_hh set to 1 if
+// the Householder fallback ran.
+int qr(const cplx* X, int64_t n2, int64_t m, cplx* Q, int* used_hh, cudaStream_t s);
+
+// Algorithm 2 on Q (2n x k): ritz (host, k/2 ascending) and Wpos (2n x k/2).
+int rayleigh_ritz(const cplx* A, const cplx* B, int64_t n, const cplx* Q, int64_t k, double* ritz_host,
+                  cplx* Wpos, cudaStream_t s);
+
+// res[j] = ||H w_j - lambda_j w_j||_2 (device lambda and res).
+int residuals(const cplx* A, const cplx* B, int64_t n, const cplx* W, const double* lambda, int64_t k,
+              double* res, cudaStream_t s);
+
+int solve(const cplx* A, const cplx* B, int64_t n, int64_t nev, int64_t nex, int deg, double tol,
+          const chase_bse_opts* opts, double* evals, cplx* evecs, chase_bse_stats* stats);
+
+int gradient(const cplx* V, const double* w, int64_t n, int64_t nev, cplx* gA, cplx* gB, cudaStream_t s);
+
+// Mixed-precision (tcgen05) filter on a column group whose columns are sorted
+// by descending degree; defined in the tensor-core translation unit.
+int filter_mixed_sorted(const cplx* A, const cplx* B, int64_t n, cplx* Y0, int64_t k, const int* degs_sorted,
+                        double mu1, double mu_nevex, double muN, cplx* out, cudaStream_t s, FilterStats* fs);
+bool mixed_available();
+
+}  // namespace cb
