@@ -52,12 +52,17 @@ typedef enum chase_bse_status {
 } chase_bse_status;
 
 typedef enum chase_bse_precision {
-  CHASE_BSE_FP64 = 0,         /* every product in FP64                                 */
-  CHASE_BSE_MIXED_BF16X3 = 1  /* filter products on tcgen05 tensor cores with BF16
-                                 hi/lo splits (3 products, FP32 accumulation);
-                                 everything else FP64; a column switches to the FP64
-                                 filter once its residual falls below switch_tol     */
+  CHASE_BSE_FP64 = 0,          /* every product in FP64 (DFMA)                         */
+  CHASE_BSE_MIXED_BF16X3 = 1,  /* filter products on tcgen05 tensor cores from BF16
+                                  pieces, x = x0 + x1, 3 products, FP32 accumulation
+                                  (about 16-bit accurate); everything else FP64      */
+  CHASE_BSE_MIXED_BF16X6 = 2   /* as above with 3 pieces and 6 products (FP32 class) */
 } chase_bse_precision;
+/* In chase_bse_solve the mixed filter runs, from the second iteration on, on the
+ * correction q(H^2) r2 with r2 = (H^2 - lambda^2) v of each Ritz pair (FP64
+ * residual), q the divided difference of the filter polynomial, so that its
+ * rounding error scales with the residual; a column whose residual is below
+ * switch_tol and stops decreasing is moved to the FP64 filter. */
 
 /* Options of chase_bse_solve.  Zero-initialise, set `size`, then override. */
 typedef struct chase_bse_opts {
@@ -71,8 +76,8 @@ typedef struct chase_bse_opts {
   int32_t reserved0;
   double gamma;            /* lower-half scale of the start block (default 1e-3,
                               Section 4.6)                                            */
-  double switch_tol;       /* mixed mode: residual below which a column is filtered
-                              in FP64 (default 1e-5)                                  */
+  double switch_tol;       /* mixed mode: a column below this residual whose residual
+                              stops decreasing moves to the FP64 filter (default 1e-8) */
   uint64_t seed;           /* counter-based generator seed when W0/V0 are NULL        */
   const void* W0;          /* device, 2n x (nev+nex) raw start block, or NULL         */
   const void* V0;          /* device, 2n x lanczos_vecs Lanczos start vectors, or NULL*/
@@ -90,6 +95,7 @@ typedef struct chase_bse_stats {
   double filter_flops;     /* algorithmic: sum over H^2 steps of 64 n^2 k_active    */
   double filter_flops_fp64;/* the part run by the FP64 filter                        */
   double ms_filter_fp64;   /* time of the FP64 filter launches                        */
+  double ms_filter_mixed;  /* time of the tensor-core filter launches                 */
   int64_t filter_launches; /* GEMM launches of the filter                             */
   double max_residual;     /* largest scaled residual of the returned pairs           */
 } chase_bse_stats;

@@ -19,7 +19,8 @@ LIB_PATH = os.path.join(_HERE, "libchase_bse.so")
 
 FP64 = 0
 MIXED_BF16X3 = 1
-_PREC = {"fp64": FP64, "mixed": MIXED_BF16X3, "mixed_bf16x3": MIXED_BF16X3}
+MIXED_BF16X6 = 2
+_PREC = {"fp64": FP64, "mixed": MIXED_BF16X3, "bf16x3": MIXED_BF16X3, "bf16x6": MIXED_BF16X6}
 
 
 class ChaseBSEError(RuntimeError):
@@ -66,6 +67,7 @@ class Stats(ctypes.Structure):
         ("filter_flops", ctypes.c_double),
         ("filter_flops_fp64", ctypes.c_double),
         ("ms_filter_fp64", ctypes.c_double),
+        ("ms_filter_mixed", ctypes.c_double),
         ("filter_launches", ctypes.c_int64),
         ("max_residual", ctypes.c_double),
     ]
@@ -156,7 +158,7 @@ def _ptr(t: Optional[torch.Tensor]):
 def solve(A: torch.Tensor, B: torch.Tensor, nev: int, nex: int, deg: int = 20, tol: float = 1e-10, *,
           precision: str = "fp64", W0: Optional[torch.Tensor] = None, V0: Optional[torch.Tensor] = None,
           maxiter: int = 25, deg_min: Optional[int] = None, deg_max: Optional[int] = None,
-          lanczos_steps: int = 26, lanczos_vecs: int = 4, gamma: float = 1e-3, switch_tol: float = 1e-5,
+          lanczos_steps: int = 26, lanczos_vecs: int = 4, gamma: float = 1e-3, switch_tol: float = 1e-8,
           seed: int = 0, stream=None, allow_partial: bool = False):
     """chase_bse_solve: returns (evals (nev,) float64, evecs (nev, 2n) complex128, stats dict)."""
     A = _mat(A, "A")

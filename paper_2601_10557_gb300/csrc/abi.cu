@@ -49,13 +49,14 @@ int chase_bse_filter(const void* A, const void* B, int64_t n, void* W, int64_t k
   if (k == 0) return CHASE_BSE_OK;
   if (!A || !B || !W || !degs || n < 1 || k < 0 || !(mu1 > 0) || !(mu_nevex > mu1) || !(muN > mu_nevex))
     return CHASE_BSE_BAD_ARG;
-  if (precision != CHASE_BSE_FP64 && precision != CHASE_BSE_MIXED_BF16X3) return CHASE_BSE_BAD_ARG;
+  if (precision != CHASE_BSE_FP64 && precision != CHASE_BSE_MIXED_BF16X3 && precision != CHASE_BSE_MIXED_BF16X6)
+    return CHASE_BSE_BAD_ARG;
   for (int64_t i = 0; i < k; ++i)
     if (degs[i] < 1) return CHASE_BSE_BAD_ARG;
   CB_GUARD({
-    std::vector<int> prec(k, precision == CHASE_BSE_MIXED_BF16X3 ? 1 : 0);
+    std::vector<int> prec(k, precision == CHASE_BSE_FP64 ? 0 : 1);
     return cb::filter((const cplx*)A, (const cplx*)B, n, (cplx*)W, k, degs, prec.data(), mu1, mu_nevex, muN,
-                      (cudaStream_t)stream, nullptr);
+                      precision == CHASE_BSE_MIXED_BF16X6 ? 6 : 3, nullptr, nullptr, (cudaStream_t)stream, nullptr);
   })
 }
 

@@ -98,7 +98,8 @@ static int filter_fp64_sorted(const cplx* A, const cplx* B, int64_t n, cplx* Y0,
 }
 
 int filter(const cplx* A, const cplx* B, int64_t n, cplx* W, int64_t k, const int* degs, const int* prec,
-           double mu1, double mu_nevex, double muN, cudaStream_t s, FilterStats* fs) {
+           double mu1, double mu_nevex, double muN, int scheme, const double* ritz, const cplx* R, cudaStream_t s,
+           FilterStats* fs) {
   if (k == 0) return CHASE_BSE_OK;
   const int64_t n2 = 2 * n;
   Workspace ws(s);
@@ -124,7 +125,17 @@ int filter(const cplx* A, const cplx* B, int64_t n, cplx* W, int64_t k, const in
       CB_TRY(filter_fp64_sorted(A, B, n, Y0, m, ds.data(), mu1, mu_nevex, muN, out, gws, s, fs));
     } else {
       if (!mixed_available()) return CHASE_BSE_UNSUPPORTED;
-      CB_TRY(filter_mixed_sorted(A, B, n, Y0, m, ds.data(), mu1, mu_nevex, muN, out, s, fs));
+      if (ritz && R) {
+        cplx* Rs;
+        CB_TRY(gws.alloc(&Rs, n2 * m));
+        CB_TRY(gather_cols(Rs, R, didx, n2, m, s));
+        std::vector<double> rs(m);
+        for (int64_t i = 0; i < m; ++i) rs[i] = ritz[idx[i]];
+        CB_TRY(filter_mixed_correction_sorted(A, B, n, Y0, m, ds.data(), rs.data(), Rs, mu1, mu_nevex, muN, out,
+                                              scheme, s, fs));
+      } else {
+        CB_TRY(filter_mixed_sorted(A, B, n, Y0, m, ds.data(), mu1, mu_nevex, muN, out, scheme, s, fs));
+      }
     }
     CB_TRY(scatter_cols(W, out, didx, n2, m, s));
     // host vectors idx/ds must outlive the async copies: synchronise before they go
@@ -374,11 +385,11 @@ int rayleigh_ritz(const cplx* A, const cplx* B, int64_t n, const cplx* Q, int64_
 }
 
 int residuals(const cplx* A, const cplx* B, int64_t n, const cplx* W, const double* lambda, int64_t k, double* res,
-              cudaStream_t s) {
+              cudaStream_t s, cplx* Rout) {
   if (k == 0) return CHASE_BSE_OK;
   Workspace ws(s);
-  cplx* R;
-  CB_TRY(ws.alloc(&R, 2 * n * k));
+  cplx* R = Rout;
+  if (!R) CB_TRY(ws.alloc(&R, 2 * n * k));
   HopArgs a{};
   a.A = A; a.B = B; a.n = n; a.W = W; a.k = k; a.out = R; a.mode = HOP_RESID; a.lambda = lambda;
   CB_TRY(hop_fp64(a, s));
@@ -461,7 +472,7 @@ int solve(const cplx* A, const cplx* B, int64_t n, int64_t nev, int64_t nex, int
   o.lanczos_steps = 26;
   o.lanczos_vecs = 4;
   o.gamma = 1e-3;
-  o.switch_tol = 1e-5;
+  o.switch_tol = 1e-8;
   o.seed = 0;
   if (opts_in) {
     if (opts_in->size != sizeof(chase_bse_opts)) return CHASE_BSE_BAD_ARG;
@@ -470,9 +481,12 @@ int solve(const cplx* A, const cplx* B, int64_t n, int64_t nev, int64_t nex, int
   if (!A || !B || !evals || !evecs || n < 1 || nev < 1 || nex < 0 || nev + nex > n || deg < 1 || !(tol > 0) ||
       o.maxiter < 1 || o.deg_min < 1 || o.deg_max < o.deg_min || o.lanczos_steps < 2 || o.lanczos_vecs < 1 ||
       o.lanczos_vecs > 64 ||
-      (o.precision != CHASE_BSE_FP64 && o.precision != CHASE_BSE_MIXED_BF16X3))
+      (o.precision != CHASE_BSE_FP64 && o.precision != CHASE_BSE_MIXED_BF16X3 &&
+       o.precision != CHASE_BSE_MIXED_BF16X6))
     return CHASE_BSE_BAD_ARG;
-  if (o.precision == CHASE_BSE_MIXED_BF16X3 && !mixed_available()) return CHASE_BSE_UNSUPPORTED;
+  const bool mixed = o.precision != CHASE_BSE_FP64;
+  const int scheme = o.precision == CHASE_BSE_MIXED_BF16X6 ? 6 : 3;
+  if (mixed && !mixed_available()) return CHASE_BSE_UNSUPPORTED;
   cudaStream_t s = (cudaStream_t)o.stream;
   const int64_t n2 = 2 * n, nevex = nev + nex;
   chase_bse_stats st{};
@@ -489,6 +503,12 @@ int solve(const cplx* A, const cplx* B, int64_t n, int64_t nev, int64_t nex, int
   CB_TRY(ws.alloc(&V0, n2 * o.lanczos_vecs));
   CB_TRY(ws.alloc(&lam_d, nevex));
   CB_TRY(ws.alloc(&res_d, nevex));
+  cplx *Rall = nullptr, *Rkeep = nullptr;
+  if (mixed) {
+    CB_TRY(ws.alloc(&Rall, n2 * nevex));
+    CB_TRY(ws.alloc(&Rkeep, n2 * nevex));
+  }
+  std::vector<double> ritz_keep;  // Ritz values of the columns of W (mixed correction form)
   PhaseClock clk(s);
 
   // Algorithm 3 line 1: W+ = randn(2n, nevex), lower half scaled by gamma
@@ -510,7 +530,7 @@ int solve(const cplx* A, const cplx* B, int64_t n, int64_t nev, int64_t nex, int
 
   int64_t locked = 0;
   std::vector<double> lam_locked;
-  std::vector<int> degs(nevex, deg), prec(nevex, o.precision == CHASE_BSE_MIXED_BF16X3 ? 1 : 0);
+  std::vector<int> degs(nevex, deg), prec(nevex, mixed ? 1 : 0);
   std::vector<double> prev_res(nevex, INFINITY);
   int it = 0;
   FilterStats fs;
@@ -520,7 +540,9 @@ int solve(const cplx* A, const cplx* B, int64_t n, int64_t nev, int64_t nex, int
     const int64_t kf = nevex - locked;
     // line 4: W+ <- p(H^2) W+
     clk.start();
-    CB_TRY(filter(A, B, n, W, kf, degs.data(), prec.data(), mu1, mu_ne, muN, s, &fs));
+    const bool corr = mixed && !ritz_keep.empty();
+    CB_TRY(filter(A, B, n, W, kf, degs.data(), prec.data(), mu1, mu_ne, muN, scheme,
+                  corr ? ritz_keep.data() : nullptr, corr ? Rkeep : nullptr, s, &fs));
     st.ms_filter += clk.stop();
     // lines 5-7: W- = K conj(W+), Q = [S Y+, S Y-, W+, W-] R^{-1}, drop the locked part
     clk.start();
@@ -539,7 +561,7 @@ int solve(const cplx* A, const cplx* B, int64_t n, int64_t nev, int64_t nex, int
     // line 11: residuals of the positive half
     clk.start();
     CB_CUDA(cudaMemcpyAsync(lam_d, ritz.data(), sizeof(double) * kf, cudaMemcpyHostToDevice, s));
-    CB_TRY(residuals(A, B, n, Wpos, lam_d, kf, res_d, s));
+    CB_TRY(residuals(A, B, n, Wpos, lam_d, kf, res_d, s, Rall));
     std::vector<double> res(kf);
     CB_CUDA(cudaMemcpyAsync(res.data(), res_d, sizeof(double) * kf, cudaMemcpyDeviceToHost, s));
     CB_CUDA(cudaStreamSynchronize(s));
@@ -570,6 +592,11 @@ int solve(const cplx* A, const cplx* B, int64_t n, int64_t nev, int64_t nex, int
     if (!keep.empty()) {
       CB_CUDA(cudaMemcpyAsync(idx_d, keep.data(), sizeof(int) * keep.size(), cudaMemcpyHostToDevice, s));
       CB_TRY(gather_cols(W, Wpos, idx_d, n2, (int64_t)keep.size(), s));
+      if (mixed) {
+        CB_TRY(gather_cols(Rkeep, Rall, idx_d, n2, (int64_t)keep.size(), s));
+        ritz_keep.clear();
+        for (int i : keep) ritz_keep.push_back(ritz[i]);
+      }
     }
     CB_CUDA(cudaStreamSynchronize(s));
     if (locked >= nev || keep.empty()) break;
@@ -590,12 +617,14 @@ int solve(const cplx* A, const cplx* B, int64_t n, int64_t nev, int64_t nex, int
     if (ritz[0] > 0.0) mu1 = std::min(mu1, ritz[0]);
     mu1 = std::min(mu1, 0.5 * mu_ne);
     degrees_update(kr, kres, kprev, kdeg, tol, mu_ne, muN, o.deg_min, o.deg_max, degs);
+    // precision flags: a tensor-core column moves to the FP64 filter only if its
+    // residual is below switch_tol and stopped decreasing (the correction form
+    // normally converges to FP64 accuracy on the tensor cores)
     std::vector<int> nprec(keep.size(), 0);
-    if (o.precision == CHASE_BSE_MIXED_BF16X3) {
+    if (mixed) {
       for (size_t i = 0; i < keep.size(); ++i) {
-        const bool near = kres[i] <= o.switch_tol;
-        const bool stalled = std::isfinite(kprev[i]) && kres[i] > 0.5 * kprev[i];
-        nprec[i] = (near || stalled || prec[keep[i]] == 0) ? 0 : 1;
+        const bool stalled = std::isfinite(kprev[i]) && kres[i] <= o.switch_tol && kres[i] >= kprev[i];
+        nprec[i] = (stalled || prec[keep[i]] == 0) ? 0 : 1;
       }
     }
     prec = nprec;
@@ -633,6 +662,7 @@ int solve(const cplx* A, const cplx* B, int64_t n, int64_t nev, int64_t nex, int
   st.filter_flops = fs.flops;
   st.filter_flops_fp64 = fs.flops_fp64;
   st.ms_filter_fp64 = fs.ms_fp64;
+  st.ms_filter_mixed = fs.ms_mixed;
   st.filter_launches = fs.launches;
   st.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
   if (stats) {

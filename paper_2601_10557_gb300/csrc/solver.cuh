@@ -6,14 +6,17 @@
 namespace cb {
 
 struct FilterStats {
-  double flops = 0, flops_fp64 = 0, ms_fp64 = 0;
+  double flops = 0, flops_fp64 = 0, ms_fp64 = 0, ms_mixed = 0;
   int64_t launches = 0;
 };
 
 // Chebyshev filter on H^2, in place on W (2n x k); degs/prec are per column
-// (host).  prec[i] = 0: FP64 path, 1: mixed (tcgen05 BF16x3) path.
+// (host).  prec[i] = 0: FP64 path, 1: tensor-core path with `scheme` (3 or 6
+// BF16 products).  With ritz (host, per column) and R (device, 2n x k, the FP64
+// residual vectors H w - ritz w) the tensor-core columns use the correction form.
 int filter(const cplx* A, const cplx* B, int64_t n, cplx* W, int64_t k, const int* degs, const int* prec,
-           double mu1, double mu_nevex, double muN, cudaStream_t s, FilterStats* fs);
+           double mu1, double mu_nevex, double muN, int scheme, const double* ritz, const cplx* R, cudaStream_t s,
+           FilterStats* fs);
 
 // Lanczos bounds: mu1, mu_nevex, muN and rho_hat (max |theta|).
 int lanczos_bounds(const cplx* A, const cplx* B, int64_t n, const cplx* V0, int64_t nvec, int steps,
@@ -27,9 +30,10 @@ int qr(const cplx* X, int64_t n2, int64_t m, cplx* Q, int* used_hh, cudaStream_t
 int rayleigh_ritz(const cplx* A, const cplx* B, int64_t n, const cplx* Q, int64_t k, double* ritz_host,
                   cplx* Wpos, cudaStream_t s);
 
-// res[j] = ||H w_j - lambda_j w_j||_2 (device lambda and res).
+// res[j] = ||H w_j - lambda_j w_j||_2 (device lambda and res); the residual
+// vectors are kept in Rout when it is not NULL (2n x k).
 int residuals(const cplx* A, const cplx* B, int64_t n, const cplx* W, const double* lambda, int64_t k,
-              double* res, cudaStream_t s);
+              double* res, cudaStream_t s, cplx* Rout = nullptr);
 
 int solve(const cplx* A, const cplx* B, int64_t n, int64_t nev, int64_t nex, int deg, double tol,
           const chase_bse_opts* opts, double* evals, cplx* evecs, chase_bse_stats* stats);
@@ -38,8 +42,16 @@ int gradient(const cplx* V, const double* w, int64_t n, int64_t nev, cplx* gA, c
 
 // Mixed-precision (tcgen05) filter on a column group whose columns are sorted
 // by descending degree; defined in the tensor-core translation unit.
+// scheme: 3 = BF16x3, 6 = BF16x6 split products.
 int filter_mixed_sorted(const cplx* A, const cplx* B, int64_t n, cplx* Y0, int64_t k, const int* degs_sorted,
-                        double mu1, double mu_nevex, double muN, cplx* out, cudaStream_t s, FilterStats* fs);
+                        double mu1, double mu_nevex, double muN, cplx* out, int scheme, cudaStream_t s,
+                        FilterStats* fs);
+// Correction form (see tc_filter.cu): V holds Ritz vectors, ritz their values,
+// R = H V - V diag(ritz) (FP64); out = p(H^2) V.
+int filter_mixed_correction_sorted(const cplx* A, const cplx* B, int64_t n, cplx* V, int64_t k,
+                                   const int* degs_sorted, const double* ritz_sorted, const cplx* R, double mu1,
+                                   double mu_nevex, double muN, cplx* out, int scheme, cudaStream_t s,
+                                   FilterStats* fs);
 bool mixed_available();
 
 }  // namespace cb

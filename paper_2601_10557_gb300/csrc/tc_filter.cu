@@ -1,13 +1,692 @@
-// Mixed-precision Chebyshev filter on tcgen05 tensor cores (BF16 x3 split products).
+// Mixed-precision Chebyshev filter on H^2 with tcgen05 tensor cores (sm_103a).
+//
+// One application of H is one real GEMM on 5th-generation tensor cores:
+//   C (n x 4k, FP32 in TMEM) = Pr (n x 4n) * Bop^T,   Bop: 4k x 4n,
+// where Pr holds the rows of P = [A | B] with re/im interleaved along K, and
+// every input vector w_j (2n complex) contributes four K-major rows of Bop:
+//   4j+0: (Re w, -Im w)   4j+1: (Im w, Re w)            -> P w
+//   4j+2: (Re u, -Im u)   4j+3: (Im u, Re u),  u = [conj(w_bot); conj(w_top)] -> P u
+// so that (H w)_top = P w and (H w)_bot = -conj(P u) land in four adjacent
+// accumulator columns of the same TMEM lane (row i of the tile).
+//
+// Split products on BF16 tensor cores: an operand x is written as a sum of
+// BF16 pieces x = x0 + x1 (+ x2), x0 = bf16(x), x1 = bf16(x - x0), ..., and the
+// product keeps the cross terms down to the target accuracy, all accumulated
+// into one FP32 TMEM accumulator:
+//   BF16x3: 2 pieces each, x0 y0 + x0 y1 + x1 y0          (~16 bits, ~1.5e-5)
+//   BF16x6: 3 pieces each, adds x0 y2 + x1 y1 + x2 y0      (FP32 class, ~2e-7)
+//
+// Kernel structure (one 128 x BN output tile per CTA, 256 threads):
+//   warp 0   TMA producer: the A and B pieces of 64 K-elements (128B swizzle)
+//            into a 2-stage shared-memory ring, mbarrier transaction counts
+//   warp 1   allocates BN TMEM columns; one lane issues the tcgen05.mma of a
+//            stage (4 K-steps x products) and commits the stage to the producer
+//   warps 4-7 epilogue: tcgen05.ld of their 32 TMEM lanes, then either
+//            (mode 0) store the next GEMM's B-operand planes, or
+//            (mode 1) the fused three-term recurrence in FP32 plus the planes, or
+//            (mode 2) Z = H X + gamma_col * X (no planes).
+// Every mbarrier wait is bounded (2 s of %globaltimer); on expiry the kernel
+// sets an error flag, waits (bounded) for its own copies in flight, frees its
+// TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "dense_kernels.cuh"
+#include "fp64_kernels.cuh"
 #include "solver.cuh"
 
 namespace cb {
+namespace tc {
 
-bool mixed_available() { return false; }
+constexpr int BM = 128, BK = 64, STAGES = 2;
+constexpr int A_BYTES = BM * BK * 2;  // 16 KB per piece
+constexpr int THREADS = 256;
+constexpr int GROUP_M = 8;  // tile raster: GROUP_M row tiles x all column tiles per group
 
-int filter_mixed_sorted(const cplx*, const cplx*, int64_t, cplx*, int64_t, const int*, double, double, double, cplx*,
-                        cudaStream_t, FilterStats*) {
-  return CHASE_BSE_UNSUPPORTED;
+// Scheme: pieces of A (NPA) and B (NPW), product list, tile width BN.
+template <int NP>
+struct Scheme;
+template <>
+struct Scheme<3> {  // BF16x3
+  static constexpr int NPA = 2, NPW = 2, BN = 256, NPROD = 3;
+  __device__ static constexpr int pa(int i) { return i == 2 ? 1 : 0; }
+  __device__ static constexpr int pb(int i) { return i == 1 ? 1 : 0; }
+};
+template <>
+struct Scheme<6> {  // BF16x6
+  static constexpr int NPA = 3, NPW = 3, BN = 128, NPROD = 6;
+  // (0,0) (0,1) (1,0) (0,2) (1,1) (2,0)
+  __device__ static constexpr int pa(int i) { return i == 2 ? 1 : (i == 4 ? 1 : (i == 5 ? 2 : 0)); }
+  __device__ static constexpr int pb(int i) { return i == 1 ? 1 : (i == 3 ? 2 : (i == 4 ? 1 : 0)); }
+};
+template <int NP>
+struct Geo {
+  static constexpr int BN = Scheme<NP>::BN;
+  static constexpr int B_BYTES = BN * BK * 2;
+  static constexpr int STAGE_BYTES = Scheme<NP>::NPA * A_BYTES + Scheme<NP>::NPW * B_BYTES;  // 96 KB
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+  static constexpr uint32_t TMEM_COLS = BN;
+  // instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, 128 x BN
+  static constexpr uint32_t IDESC =
+      (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+};
+constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;
+
+struct Epi {
+  int mode;           // 0: operand planes, 1: recurrence, 2: H X + gamma X
+  int64_t n, k;       // rows of P, active vectors
+  int64_t kpad;       // elements per plane row
+  __nv_bfloat16* out[3];  // output operand pieces (NPW used)
+  float2* Znext;
+  const float2* Zcur;
+  const float2* Zprev;
+  const float2* src;
+  const float* gamma;  // per column
+  float alpha, beta, c;
+  int* err;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait.  honour_abort: give up as soon as another role has aborted.
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_sh, int* err, bool honour_abort) {
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = gtimer();
+  while (true) {
+    if (mbar_try(bar, parity)) return true;
+    if (honour_abort && *abort_sh) return false;
+    if (gtimer() - t0 > WAIT_LIMIT_NS) {
+      *abort_sh = 1;
+      atomicExch(err, 1);
+      return false;
+    }
+    __nanosleep(32);
+  }
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* tm, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major tile written by TMA with 128-byte
+// swizzle; rows of 128 bytes, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
+  d |= (uint64_t)1 << 16;                    // leading byte offset (unused for this layout)
+  d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset
+  d |= (uint64_t)1 << 46;                    // descriptor version
+  d |= (uint64_t)2 << 61;                    // 128-byte swizzle
+  return d;
+}
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accum)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// (a, b) -> NPC BF16 pieces each (round to nearest even at every step)
+template <int NPC>
+__device__ __forceinline__ void put(__nv_bfloat16* const* pc, int64_t off, float a, float b) {
+#pragma unroll
+  for (int q = 0; q < NPC; ++q) {
+    const __nv_bfloat16 ha = __float2bfloat16_rn(a), hb = __float2bfloat16_rn(b);
+    *reinterpret_cast<__nv_bfloat162*>(pc[q] + off) = __halves2bfloat162(ha, hb);
+    a -= __bfloat162float(ha);
+    b -= __bfloat162float(hb);
+  }
+}
+// The four B-operand rows of vector v at K positions 2i (top entry t = w(i))
+// and 2(n+i) (bottom entry b = w(n+i)).
+template <int NPC>
+__device__ __forceinline__ void store_operand(__nv_bfloat16* const* pc, int64_t kpad, int64_t n, int64_t v, int64_t i,
+                                              float2 t, float2 b) {
+  const int64_t r0 = (4 * v) * kpad, r1 = r0 + kpad, r2 = r1 + kpad, r3 = r2 + kpad;
+  const int64_t pt = 2 * i, pb = 2 * (n + i);
+  put<NPC>(pc, r0 + pt, t.x, -t.y);
+  put<NPC>(pc, r0 + pb, b.x, -b.y);
+  put<NPC>(pc, r1 + pt, t.y, t.x);
+  put<NPC>(pc, r1 + pb, b.y, b.x);
+  put<NPC>(pc, r2 + pt, b.x, b.y);   // u(i) = conj(b)
+  put<NPC>(pc, r2 + pb, t.x, t.y);   // u(n+i) = conj(t)
+  put<NPC>(pc, r3 + pt, -b.y, b.x);
+  put<NPC>(pc, r3 + pb, -t.y, t.x);
+}
+
+struct Maps {
+  CUtensorMap a[3];
+  CUtensorMap b[3];
+};
+
+template <int NP>
+__global__ void __launch_bounds__(THREADS, 1)
+    tc_hop_kernel(const __grid_constant__ Maps maps, Epi ep, int num_kb, int num_m, int num_n) {
+  using SC = Scheme<NP>;
+  using G = Geo<NP>;
+  constexpr int BN = G::BN;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * G::STAGE_BYTES);
+  uint32_t full[STAGES], empty[STAGES];
+#pragma unroll
+  for (int s = 0; s < STAGES; ++s) {
+    full[s] = smem_u32(bars + s);
+    empty[s] = smem_u32(bars + STAGES + s);
+  }
+  const uint32_t tfull = smem_u32(bars + 2 * STAGES);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
+  volatile int* abort_sh = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  int* issued_sh = reinterpret_cast<int*>(tmem_slot + 2);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  // grouped raster over (m, n) tiles
+  const int bid = blockIdx.x;
+  const int per_group = GROUP_M * num_n;
+  const int g = bid / per_group;
+  const int first_m = g * GROUP_M;
+  const int gm = min(GROUP_M, num_m - first_m);
+  const int rem = bid - g * per_group;
+  const int mt = first_m + rem % gm;
+  const int nt = rem / gm;
+  const int m0 = mt * BM, n0 = nt * BN;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full[s], 1);
+      mbar_init(empty[s], 1);
+    }
+    mbar_init(tfull, 1);
+    *abort_sh = 0;
+    *issued_sh = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(G::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t sbase = smem_u32(smem);
+
+  if (warp == 0 && lane == 0) {
+    int issued = 0;
+    for (int kb = 0; kb < num_kb; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+      if (kb >= STAGES && !mbar_wait(empty[s], ph ^ 1u, abort_sh, ep.err, true)) break;
+      const uint32_t st = sbase + s * G::STAGE_BYTES;
+      mbar_expect_tx(full[s], G::STAGE_BYTES);
+#pragma unroll
+      for (int q = 0; q < SC::NPA; ++q) tma_load_2d(st + q * A_BYTES, &maps.a[q], kb * BK, m0, full[s]);
+#pragma unroll
+      for (int q = 0; q < SC::NPW; ++q)
+        tma_load_2d(st + SC::NPA * A_BYTES + q * G::B_BYTES, &maps.b[q], kb * BK, n0, full[s]);
+      issued = kb + 1;
+    }
+    *issued_sh = issued;
+  } else if (warp == 1 && lane == 0) {
+    for (int kb = 0; kb < num_kb; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+      if (!mbar_wait(full[s], ph, abort_sh, ep.err, true)) break;
+      tc_fence_after();
+      const uint32_t st = sbase + s * G::STAGE_BYTES;
+#pragma unroll
+      for (int kk = 0; kk < BK / 16; ++kk) {
+#pragma unroll
+        for (int pr = 0; pr < SC::NPROD; ++pr) {
+          const uint64_t ad = sdesc(st + SC::pa(pr) * A_BYTES + kk * 32);
+          const uint64_t bd = sdesc(st + SC::NPA * A_BYTES + SC::pb(pr) * G::B_BYTES + kk * 32);
+          mma_bf16(tmem, ad, bd, G::IDESC, (kb | kk | pr) != 0 ? 1u : 0u);
+        }
+      }
+      mma_commit(empty[s]);
+    }
+    mma_commit(tfull);  // completes once every MMA issued above has finished
+  } else if (warp >= 4) {
+    const int q = warp - 4;
+    const bool ok = mbar_wait(tfull, 0, abort_sh, ep.err, false);
+    // tcgen05.ld is .sync.aligned: make the decision warp-uniform and reconverge
+    const bool go = __all_sync(0xffffffffu, ok && !*abort_sh);
+    tc_fence_after();
+    const int64_t row = (int64_t)m0 + q * 32 + lane;
+    if (go) {
+      const int64_t n = ep.n, n2 = 2 * ep.n;
+      for (int c = 0; c < BN / 32; ++c) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(c * 32), v);
+        if (row >= n) continue;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const int64_t vg = (int64_t)(n0 >> 2) + c * 8 + t;
+          if (vg >= ep.k) continue;
+          const float2 ht = make_float2(v[4 * t], v[4 * t + 1]);        // (H x)_top(row)
+          const float2 hb = make_float2(-v[4 * t + 2], v[4 * t + 3]);   // (H x)_bot(row)
+          const int64_t ot = vg * n2 + row, ob = ot + n;
+          if (ep.mode == 0) {
+            store_operand<SC::NPW>(ep.out, ep.kpad, n, vg, row, ht, hb);
+          } else if (ep.mode == 1) {
+            const float2 ct = ep.Zcur[ot], cbv = ep.Zcur[ob];
+            float2 zt = make_float2(ep.alpha * (ht.x - ep.c * ct.x), ep.alpha * (ht.y - ep.c * ct.y));
+            float2 zb = make_float2(ep.alpha * (hb.x - ep.c * cbv.x), ep.alpha * (hb.y - ep.c * cbv.y));
+            if (ep.beta != 0.0f) {
+              const float2 pt = ep.Zprev[ot], pb = ep.Zprev[ob];
+              zt.x += ep.beta * pt.x; zt.y += ep.beta * pt.y;
+              zb.x += ep.beta * pb.x; zb.y += ep.beta * pb.y;
+            }
+            if (ep.src) {
+              const float gmm = ep.gamma[vg];
+              const float2 st = ep.src[ot], sb = ep.src[ob];
+              zt.x += gmm * st.x; zt.y += gmm * st.y;
+              zb.x += gmm * sb.x; zb.y += gmm * sb.y;
+            }
+            ep.Znext[ot] = zt;
+            ep.Znext[ob] = zb;
+            store_operand<SC::NPW>(ep.out, ep.kpad, n, vg, row, zt, zb);
+          } else {
+            const float gmm = ep.gamma[vg];
+            const float2 ct = ep.Zcur[ot], cbv = ep.Zcur[ob];
+            ep.Znext[ot] = make_float2(ht.x + gmm * ct.x, ht.y + gmm * ct.y);
+            ep.Znext[ob] = make_float2(hb.x + gmm * cbv.x, hb.y + gmm * cbv.y);
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (*abort_sh && threadIdx.x == 0) {
+    // drain copies still in flight into this CTA's shared memory (bounded)
+    const int issued = *issued_sh;
+    for (int kb = max(0, issued - STAGES); kb < issued; ++kb)
+      mbar_wait(full[kb % STAGES], (uint32_t)(kb / STAGES) & 1u, abort_sh, ep.err, false);
+  }
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(G::TMEM_COLS) : "memory");
+  }
+}
+
+// ---------------------------------------------------------------- helpers
+struct Pieces {
+  __nv_bfloat16* p[3];
+};
+
+// P = [A | B] (row-major complex128) -> NPC BF16 pieces, row i, K = (re, im) pairs.
+template <int NPC>
+__global__ void split_p_kernel(const cplx* A, const cplx* B, int64_t n, int64_t kpad, Pieces out) {
+  const int64_t total = n * 2 * n;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx / (2 * n), l = idx % (2 * n);
+    const cplx p = (l < n) ? A[i * n + l] : B[i * n + (l - n)];
+    put<NPC>(out.p, i * kpad + 2 * l, (float)p.x, (float)p.y);
+  }
+}
+// complex128 block (2n x k) -> FP32 master and, optionally, operand pieces
+template <int NPC>
+__global__ void pack_kernel(const cplx* W, int64_t n, int64_t k, float2* Z, Pieces out, int with_pieces,
+                            int64_t kpad) {
+  const int64_t total = n * k;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx % n, v = idx / n;
+    const cplx wt = W[v * 2 * n + i], wb = W[v * 2 * n + n + i];
+    const float2 t = make_float2((float)wt.x, (float)wt.y);
+    const float2 b = make_float2((float)wb.x, (float)wb.y);
+    if (Z) {
+      Z[v * 2 * n + i] = t;
+      Z[v * 2 * n + n + i] = b;
+    }
+    if (with_pieces) store_operand<NPC>(out.p, kpad, n, v, i, t, b);
+  }
+}
+// Z = scale * X (FP32 master) and its operand pieces
+template <int NPC>
+__global__ void scale_pack_kernel(const float2* X, int64_t n, int64_t k, float scale, float2* Z, Pieces out,
+                                  int64_t kpad) {
+  const int64_t total = n * k;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx % n, v = idx / n;
+    const float2 xt = X[v * 2 * n + i], xb = X[v * 2 * n + n + i];
+    const float2 t = make_float2(scale * xt.x, scale * xt.y), b = make_float2(scale * xb.x, scale * xb.y);
+    Z[v * 2 * n + i] = t;
+    Z[v * 2 * n + n + i] = b;
+    store_operand<NPC>(out.p, kpad, n, v, i, t, b);
+  }
+}
+// out[:, v] = (double) Zsel[:, v] + coef[v] * base[:, v]   (coef/base optional)
+__global__ void combine_kernel(cplx* out, const float2* Z0, const float2* Z1, const float2* Z2, const int* sel,
+                               const double* coef, const cplx* base, int64_t n2, int64_t k) {
+  const int64_t total = n2 * k;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = idx / n2;
+    const int q = sel[v];
+    const float2 z = (q == 0 ? Z0 : (q == 1 ? Z1 : Z2))[idx];
+    cplx r = mk((double)z.x, (double)z.y);
+    if (coef) r = cadd(r, cscale(base[idx], coef[v]));
+    out[idx] = r;
+  }
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+static int make_map(CUtensorMap* m, const void* base, int64_t kpad, int64_t rows, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return CHASE_BSE_UNSUPPORTED;
+  const cuuint64_t dims[2] = {(cuuint64_t)kpad, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)kpad * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? CHASE_BSE_OK : CHASE_BSE_CUDA_ERROR;
+}
+
+static inline unsigned gsz(int64_t total) {
+  const int64_t b = (total + 255) / 256;
+  return (unsigned)std::min<int64_t>(std::max<int64_t>(b, 1), 16384);
+}
+
+// The operand of P = [A | B] in NPA BF16 pieces, with its tensor maps.
+struct POperand {
+  int64_t n = 0, kpad = 0;
+  Pieces pc{};
+  CUtensorMap map[3];
+};
+
+template <int NP>
+static int prepare_p(const cplx* A, const cplx* B, int64_t n, Workspace& ws, POperand& P, cudaStream_t s) {
+  constexpr int NPA = Scheme<NP>::NPA;
+  P.n = n;
+  P.kpad = ((4 * n + BK - 1) / BK) * BK;
+  const int64_t rows = ((n + BM - 1) / BM) * BM;  // whole tiles: every TMA box lies inside the tensor
+  for (int q = 0; q < NPA; ++q) {
+    CB_TRY(ws.alloc(&P.pc.p[q], rows * P.kpad));
+    CB_CUDA(cudaMemsetAsync(P.pc.p[q], 0, sizeof(__nv_bfloat16) * rows * P.kpad, s));
+  }
+  split_p_kernel<NPA><<<gsz(2 * n * n), 256, 0, s>>>(A, B, n, P.kpad, P.pc);
+  count_launch();
+  CB_LAUNCH();
+  for (int q = 0; q < NPA; ++q) CB_TRY(make_map(&P.map[q], P.pc.p[q], P.kpad, rows, BM));
+  return CHASE_BSE_OK;
+}
+
+// One tensor-core application of H to the vectors held in the operand pieces
+// described by bmap, with epilogue `ep`.
+template <int NP>
+static int apply(const POperand& P, const CUtensorMap* bmap, Epi ep, cudaStream_t s) {
+  using G = Geo<NP>;
+  if (ep.k <= 0) return CHASE_BSE_OK;
+  static bool attr = false;
+  if (!attr) {
+    CB_CUDA(cudaFuncSetAttribute(tc_hop_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM_BYTES));
+    attr = true;
+  }
+  Maps maps;
+  for (int q = 0; q < Scheme<NP>::NPA; ++q) maps.a[q] = P.map[q];
+  for (int q = 0; q < Scheme<NP>::NPW; ++q) maps.b[q] = bmap[q];
+  const int num_m = (int)cdiv(P.n, BM);
+  const int num_n = (int)cdiv(4 * ep.k, G::BN);
+  const int num_kb = (int)(P.kpad / BK);
+  tc_hop_kernel<NP><<<num_m * num_n, THREADS, G::SMEM_BYTES, s>>>(maps, ep, num_kb, num_m, num_n);
+  count_launch();
+  CB_LAUNCH();
+  return CHASE_BSE_OK;
+}
+
+// Mixed-precision filter on columns sorted by descending degree.  If `ritz` and
+// `R` are given, the filter runs in correction form: with m_i = ritz_i^2 and
+// r2_i = (H^2 - m_i) v_i = (H + ritz_i)(H v_i - ritz_i v_i),
+//   p(H^2) v_i = p(m_i) v_i + q(H^2) r2_i,  q(x) = (p(x) - p(m_i)) / (x - m_i),
+// and only q(H^2) r2 runs on the tensor cores; its recurrence is the filter's
+// with the source term alpha_j p_j(m_i) r2_i (divided differences of the
+// three-term recurrence).  The low-precision error then scales with the
+// residual of v_i instead of with v_i.
+template <int NP>
+static int filter_impl(const cplx* A, const cplx* B, int64_t n, const cplx* Y0, int64_t k, const int* degs,
+                       double mu1, double mu_nevex, double muN, cplx* out, const double* ritz, const cplx* R,
+                       cudaStream_t s, FilterStats* fs) {
+  constexpr int NPW = Scheme<NP>::NPW;
+  using G = Geo<NP>;
+  if (k == 0) return CHASE_BSE_OK;
+  const int64_t n2 = 2 * n;
+  Workspace ws(s);
+  POperand P;
+  CB_TRY(prepare_p<NP>(A, B, n, ws, P, s));
+  const int64_t rows = ((4 * k + G::BN - 1) / G::BN) * G::BN;  // whole tiles
+  Pieces Zp{}, Tp{};
+  CUtensorMap mZ[3], mT[3];
+  for (int q = 0; q < NPW; ++q) {
+    CB_TRY(ws.alloc(&Zp.p[q], rows * P.kpad));
+    CB_TRY(ws.alloc(&Tp.p[q], rows * P.kpad));
+    CB_CUDA(cudaMemsetAsync(Zp.p[q], 0, sizeof(__nv_bfloat16) * rows * P.kpad, s));
+    CB_CUDA(cudaMemsetAsync(Tp.p[q], 0, sizeof(__nv_bfloat16) * rows * P.kpad, s));
+    CB_TRY(make_map(&mZ[q], Zp.p[q], P.kpad, rows, G::BN));
+    CB_TRY(make_map(&mT[q], Tp.p[q], P.kpad, rows, G::BN));
+  }
+  float2 *Zb[3], *src = nullptr;
+  float* gam;
+  int* err;
+  for (int q = 0; q < 3; ++q) CB_TRY(ws.alloc(&Zb[q], n2 * k));
+  CB_TRY(ws.alloc(&gam, k));
+  CB_TRY(ws.alloc(&err, 1));
+  CB_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+
+  const double a = mu_nevex * mu_nevex, b = muN * muN;
+  const double c = 0.5 * (a + b), e = 0.5 * (b - a);
+  const double sigma1 = e / (mu1 * mu1 - c);
+  const double tau = 2.0 / sigma1;
+  const int maxdeg = degs[0];
+  std::vector<double> al(maxdeg), be(maxdeg);  // alpha_j, beta_j of the scaled recurrence
+  {
+    double sigma = sigma1;
+    al[0] = sigma1 / e;
+    be[0] = 0.0;
+    for (int j = 1; j < maxdeg; ++j) {
+      const double sn = 1.0 / (tau - sigma);
+      al[j] = 2.0 * sn / e;
+      be[j] = -sigma * sn;
+      sigma = sn;
+    }
+  }
+  const bool corr = (ritz != nullptr && R != nullptr);
+  std::vector<double> pj;  // p_j(m_i), j = 0 .. maxdeg
+  if (corr) {
+    pj.assign((size_t)(maxdeg + 1) * k, 0.0);
+    for (int64_t i = 0; i < k; ++i) {
+      const double m = ritz[i] * ritz[i];
+      double p0 = 1.0, p1 = al[0] * (m - c);
+      pj[i] = p0;
+      pj[(size_t)k + i] = p1;
+      for (int j = 1; j < maxdeg; ++j) {
+        const double p2 = al[j] * (m - c) * p1 + be[j] * p0;
+        pj[(size_t)(j + 1) * k + i] = p2;
+        p0 = p1;
+        p1 = p2;
+      }
+    }
+  }
+  std::vector<float> gh(k);
+  int j0 = 0;
+  cudaEvent_t e0, e1;
+  CB_CUDA(cudaEventCreate(&e0));
+  CB_CUDA(cudaEventCreate(&e1));
+  CB_CUDA(cudaEventRecord(e0, s));
+  if (!corr) {
+    pack_kernel<NPW><<<gsz(n * k), 256, 0, s>>>(Y0, n, k, Zb[0], Zp, 1, P.kpad);  // Z_0 = W
+    count_launch();
+    CB_LAUNCH();
+  } else {
+    // r2 = H R + ritz R on the tensor cores; Z_0 = 0; Z_1 = alpha_0 r2
+    CB_TRY(ws.alloc(&src, n2 * k));
+    pack_kernel<NPW><<<gsz(n * k), 256, 0, s>>>(R, n, k, Zb[2], Zp, 1, P.kpad);
+    count_launch();
+    for (int64_t i = 0; i < k; ++i) gh[i] = (float)ritz[i];
+    CB_CUDA(cudaMemcpyAsync(gam, gh.data(), sizeof(float) * k, cudaMemcpyHostToDevice, s));
+    Epi ep{};
+    ep.mode = 2; ep.n = n; ep.k = k; ep.kpad = P.kpad; ep.Znext = src; ep.Zcur = Zb[2]; ep.gamma = gam; ep.err = err;
+    CB_TRY(apply<NP>(P, mZ, ep, s));
+    CB_CUDA(cudaMemsetAsync(Zb[0], 0, sizeof(float2) * n2 * k, s));
+    scale_pack_kernel<NPW><<<gsz(n * k), 256, 0, s>>>(src, n, k, (float)al[0], Zb[1], Zp, P.kpad);
+    count_launch();
+    CB_LAUNCH();
+    j0 = 1;
+    if (fs) {
+      fs->flops += 32.0 * (double)n * (double)n * (double)k;
+      fs->launches += 1;
+    }
+  }
+  for (int j = j0; j < maxdeg; ++j) {
+    int64_t kj = 0;
+    while (kj < k && degs[kj] >= j + 1) ++kj;
+    Epi e1p{};
+    e1p.mode = 0; e1p.n = n; e1p.k = kj; e1p.kpad = P.kpad; e1p.err = err;
+    for (int q = 0; q < NPW; ++q) e1p.out[q] = Tp.p[q];
+    CB_TRY(apply<NP>(P, mZ, e1p, s));  // T = H Z_j
+    Epi e2p{};
+    e2p.mode = 1; e2p.n = n; e2p.k = kj; e2p.kpad = P.kpad; e2p.err = err;
+    for (int q = 0; q < NPW; ++q) e2p.out[q] = Zp.p[q];
+    e2p.Znext = Zb[(j + 1) % 3]; e2p.Zcur = Zb[j % 3]; e2p.Zprev = Zb[(j + 2) % 3];
+    e2p.alpha = (float)al[j]; e2p.beta = (float)be[j]; e2p.c = (float)c;
+    if (corr) {
+      for (int64_t i = 0; i < kj; ++i) gh[i] = (float)(al[j] * pj[(size_t)j * k + i]);
+      CB_CUDA(cudaMemcpyAsync(gam, gh.data(), sizeof(float) * kj, cudaMemcpyHostToDevice, s));
+      e2p.src = src;
+      e2p.gamma = gam;
+    }
+    CB_TRY(apply<NP>(P, mT, e2p, s));  // Z_{j+1} = alpha (H T - c Z_j) + beta Z_{j-1} (+ source)
+    if (fs) {
+      fs->flops += 64.0 * (double)n * (double)n * (double)kj;
+      fs->launches += 2;
+    }
+  }
+  CB_CUDA(cudaEventRecord(e1, s));
+  std::vector<int> sel(k);
+  std::vector<double> coef(k, 0.0);
+  for (int64_t i = 0; i < k; ++i) {
+    sel[i] = degs[i] % 3;
+    if (corr) coef[i] = pj[(size_t)degs[i] * k + i];
+  }
+  int* dsel;
+  double* dcoef;
+  CB_TRY(ws.alloc(&dsel, k));
+  CB_TRY(ws.alloc(&dcoef, k));
+  CB_CUDA(cudaMemcpyAsync(dsel, sel.data(), sizeof(int) * k, cudaMemcpyHostToDevice, s));
+  CB_CUDA(cudaMemcpyAsync(dcoef, coef.data(), sizeof(double) * k, cudaMemcpyHostToDevice, s));
+  combine_kernel<<<gsz(n2 * k), 256, 0, s>>>(out, Zb[0], Zb[1], Zb[2], dsel, corr ? dcoef : nullptr, Y0, n2, k);
+  count_launch();
+  CB_LAUNCH();
+  int herr = 0;
+  CB_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CB_CUDA(cudaStreamSynchronize(s));
+  if (fs) {
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    fs->ms_mixed += ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return herr ? CHASE_BSE_DEVICE_TIMEOUT : CHASE_BSE_OK;
+}
+
+}  // namespace tc
+
+bool mixed_available() {
+  int dev = 0, major = 0, minor = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  return major == 10 && minor == 3 && tc::encode_fn() != nullptr;
+}
+
+int filter_mixed_sorted(const cplx* A, const cplx* B, int64_t n, cplx* Y0, int64_t k, const int* degs_sorted,
+                        double mu1, double mu_nevex, double muN, cplx* out, int scheme, cudaStream_t s,
+                        FilterStats* fs) {
+  if (scheme == 6)
+    return tc::filter_impl<6>(A, B, n, Y0, k, degs_sorted, mu1, mu_nevex, muN, out, nullptr, nullptr, s, fs);
+  return tc::filter_impl<3>(A, B, n, Y0, k, degs_sorted, mu1, mu_nevex, muN, out, nullptr, nullptr, s, fs);
+}
+
+int filter_mixed_correction_sorted(const cplx* A, const cplx* B, int64_t n, cplx* V, int64_t k,
+                                   const int* degs_sorted, const double* ritz_sorted, const cplx* R, double mu1,
+                                   double mu_nevex, double muN, cplx* out, int scheme, cudaStream_t s,
+                                   FilterStats* fs) {
+  if (scheme == 6)
+    return tc::filter_impl<6>(A, B, n, V, k, degs_sorted, mu1, mu_nevex, muN, out, ritz_sorted, R, s, fs);
+  return tc::filter_impl<3>(A, B, n, V, k, degs_sorted, mu1, mu_nevex, muN, out, ritz_sorted, R, s, fs);
 }
 
 }  // namespace cb

@@ -1,0 +1,77 @@
+"""Parity of the tensor-core (tcgen05) filter and the mixed-precision solve with the oracle."""
+import numpy as np
+import pytest
+import torch
+
+import bse_inputs as bi
+from oracle import chebyshev, dense
+from tests.gpu_util import problem_on_device, rel_fro, starts, to_dev
+
+pytestmark = pytest.mark.gpu
+
+# Relative Frobenius tolerances of the tensor-core filter against the FP64 oracle.
+# BF16x6 keeps 24 significant bits of each operand (FP32 class): the 1e-5 gate of
+# an FP32 filter applies.  BF16x3 keeps 16 bits of each operand: the representation
+# error is 2 * 2^-17 = 1.5e-5 per product, and the recurrence adds a small factor.
+TOL = {"bf16x6": 1e-5, "bf16x3": 6e-5}
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    import paper_2601_10557_gb300 as p
+    if not p.has_mixed():
+        pytest.fail("tensor-core filter not available on this device")
+    return p
+
+
+def _mus(P):
+    lam, _ = dense.eig_cholesky(P.A, P.B)
+    pos = lam[P.n:]
+    return 0.9 * pos[0], pos[len(pos) // 6], 1.05 * pos[-1]
+
+
+@pytest.mark.parametrize("scheme", ["bf16x3", "bf16x6"])
+@pytest.mark.parametrize("n,k,maxdeg", [(128, 8, 1), (128, 8, 4), (300, 70, 8), (129, 33, 6)])
+def test_filter_tensor_core_matches_oracle(pkg, scheme, n, k, maxdeg):
+    P = bi.make_problem(n, seed=n + k)
+    A, B = problem_on_device(P)
+    W0 = bi.start_block(n, k, 3)
+    degs = np.random.default_rng(k).integers(1, maxdeg + 1, size=k)
+    mu1, mune, muN = _mus(P)
+    W = to_dev(W0)
+    pkg.filter(A, B, W, degs, mu1, mune, muN, precision=scheme)
+    Y = chebyshev.chebyshev_filter(P.A, P.B, W0.T, degs, mu1, mune, muN)
+    err = rel_fro(W.cpu().numpy().T, Y)
+    assert err < TOL[scheme], err
+
+
+@pytest.mark.parametrize("scheme", ["bf16x3", "bf16x6"])
+def test_solve_mixed_matches_brute_force(pkg, scheme):
+    n, nev, nex = 64, 8, 6
+    P = bi.make_problem(n, seed=11)
+    A, B = problem_on_device(P)
+    W0, V0 = starts(n, nev + nex, 0)
+    lam, V, st = pkg.solve(A, B, nev, nex, 12, 1e-10, W0=to_dev(W0), V0=to_dev(V0), deg_min=4, deg_max=24,
+                           precision=scheme)
+    ref, _ = dense.smallest_positive(P.A, P.B, nev)
+    np.testing.assert_allclose(lam.cpu().numpy(), ref, rtol=1e-10)
+    Vg = V.cpu().numpy().T
+    H = dense.hamiltonian(P.A, P.B)
+    R = H @ Vg - Vg * lam.cpu().numpy()
+    assert np.linalg.norm(R, axis=0).max() / np.linalg.norm(H, 2) <= 1e-10
+    assert st["filter_flops_fp64"] < 0.5 * st["filter_flops"]
+
+
+def test_solve_mixed_n512_workload(pkg):
+    cfg = bi.WORKLOADS["n512"]
+    n, nev, nex = cfg["n"], cfg["nev"], cfg["nex"]
+    P = bi.make_problem(n, seed=0, spec=cfg["spec"], beta=cfg["beta"])
+    A, B = problem_on_device(P)
+    W0, V0 = starts(n, nev + nex, 0)
+    lam, V, st = pkg.solve(A, B, nev, nex, cfg["deg"], cfg["tol"], W0=to_dev(W0), V0=to_dev(V0),
+                           deg_min=cfg["deg_min"], deg_max=cfg["deg_max"], precision="bf16x3")
+    ref, _ = dense.smallest_positive(P.A, P.B, nev)
+    np.testing.assert_allclose(lam.cpu().numpy(), ref, rtol=1e-10)
+    assert st["max_residual"] <= cfg["tol"]
