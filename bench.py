@@ -218,8 +218,12 @@ def main():
     fl = fms = 0.0
     iters = []
     maxres = 0.0
+    phases = {}
     for _ in range(args.steps):
         lam, V, st, gA, gB = step(precision)
+        for key in ("ms_total", "ms_lanczos", "ms_filter", "ms_filter_mixed", "ms_filter_fp64", "ms_qr", "ms_rr",
+                    "ms_resid"):
+            phases[key] = phases.get(key, 0.0) + st[key] / args.steps
         fl += st["filter_flops"]
         fms += st["ms_filter"]
         iters.append(st["iterations"])
@@ -347,6 +351,7 @@ def main():
             "time_to_solution_s": tts_max,
             "time_to_solution_fp64_s": fp64_tts if precision != "fp64" else tts_max,
             "iterations": iters, "max_residual": maxres,
+            "phases_ms_per_step": {k2: round(v2, 2) for k2, v2 in phases.items()},
             "lambda_min_max": [float(lam_np[0]), float(lam_np[-1])],
             "e2e": {"value": e2e_val, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": e2e_ms / max(e2e_steps, 1)},
