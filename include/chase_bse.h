@@ -152,6 +152,27 @@ int chase_bse_rr(const void* A, const void* B, int64_t n, const void* Q, int64_t
 int chase_bse_residuals(const void* A, const void* B, int64_t n, const void* W,
                         const double* lambda, int64_t k, double* res, void* stream);
 
+/* chase_bse_residuals for callers that cannot let a library allocate device
+ * memory (the paper has no counterpart): for example an application whose own
+ * memory pool owns the whole device, a program with a fixed device-memory
+ * budget, or a latency-critical loop in which an allocation or a free may
+ * synchronise the device.  Same arguments and results as chase_bse_residuals;
+ * the 2n x k scratch block lives in a fixed array of
+ * CHASE_BSE_NOALLOC_MAX_ENTRIES complex128 entries (8 MiB) that every device
+ * using the library holds until the process exits, and the call performs no
+ * allocation or free.
+ *   - 2n * k > CHASE_BSE_NOALLOC_MAX_ENTRIES returns BAD_ARG; nothing runs.
+ *   - The first call on a device looks up the array's device address (once per
+ *     device, with that device current); make that first call before any stream
+ *     capture.
+ *   - All calls share the array, which keeps the last call's contents: calls
+ *     whose kernels overlap on the GPU (different streams, or different host
+ *     threads, without ordering between them) race on it and give wrong
+ *     results.  Order them on one stream or synchronise between them. */
+#define CHASE_BSE_NOALLOC_MAX_ENTRIES ((int64_t)1 << 19)
+int chase_bse_residuals_noalloc(const void* A, const void* B, int64_t n, const void* W,
+                                const double* lambda, int64_t k, double* res, void* stream);
+
 /* Eigenvalue gradient of L = sum_i w_i lambda_i (left eigenvector u = S v,
  * Theorem SH_HPD): with V = [X; Y], s_i = |x_i|^2 - |y_i|^2, c_i = w_i / s_i,
  *   gA = sum_i c_i (x_i x_i^* + conj(y_i) y_i^T)   (hermitian)

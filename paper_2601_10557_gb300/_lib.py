@@ -79,7 +79,11 @@ class Stats(ctypes.Structure):
 _lib: Optional[ctypes.CDLL] = None
 
 EXPORTS = ["chase_bse_solve", "chase_bse_filter", "chase_bse_rr", "chase_bse_residuals", "chase_bse_grad",
-           "chase_bse_strerror", "chase_bse_version", "chase_bse_has_mixed", "chase_bse_launch_count"]
+           "chase_bse_strerror", "chase_bse_version", "chase_bse_has_mixed", "chase_bse_launch_count",
+           "chase_bse_residuals_noalloc"]
+
+# 2n * k limit of chase_bse_residuals_noalloc (its fixed device scratch, complex128 entries)
+NOALLOC_MAX_ENTRIES = 1 << 19
 
 
 def lib() -> ctypes.CDLL:
@@ -97,12 +101,13 @@ def lib() -> ctypes.CDLL:
     L.chase_bse_filter.argtypes = [vp, vp, i64, vp, i64, ctypes.POINTER(ctypes.c_int32), dbl, dbl, dbl, i32, vp]
     L.chase_bse_rr.argtypes = [vp, vp, i64, vp, i64, ctypes.POINTER(ctypes.c_double), vp, vp]
     L.chase_bse_residuals.argtypes = [vp, vp, i64, vp, vp, i64, vp, vp]
+    L.chase_bse_residuals_noalloc.argtypes = [vp, vp, i64, vp, vp, i64, vp, vp]
     L.chase_bse_grad.argtypes = [vp, vp, i64, i64, vp, vp, vp]
     L.chase_bse_strerror.argtypes = [ctypes.c_int]
     L.chase_bse_strerror.restype = ctypes.c_char_p
     L.chase_bse_launch_count.restype = ctypes.c_int64
     for name in ["chase_bse_solve", "chase_bse_filter", "chase_bse_rr", "chase_bse_residuals", "chase_bse_grad",
-                 "chase_bse_version", "chase_bse_has_mixed"]:
+                 "chase_bse_version", "chase_bse_has_mixed", "chase_bse_residuals_noalloc"]:
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -228,6 +233,28 @@ def residuals(A: torch.Tensor, B: torch.Tensor, W: torch.Tensor, lam: torch.Tens
     _check(lib().chase_bse_residuals(_ptr(A), _ptr(B), n, _ptr(W), _ptr(lam), W.shape[0], _ptr(res),
                                      ctypes.c_void_p(_stream(stream))), "chase_bse_residuals")
     return res
+
+
+def residuals_noalloc(A: torch.Tensor, B: torch.Tensor, W: torch.Tensor, lam: torch.Tensor, out: torch.Tensor,
+                      stream=None) -> torch.Tensor:
+    """chase_bse_residuals_noalloc: residual norms into the caller's `out`
+    (float64, k entries) without any device allocation by the library; the
+    scratch is a fixed per-device array of NOALLOC_MAX_ENTRIES complex128
+    entries shared by all calls (see include/chase_bse.h)."""
+    A = _mat(A, "A")
+    n = A.shape[0]
+    B = _mat(B, "B", n)
+    W = _block(W, "W", 2 * n)
+    k = W.shape[0]
+    if 2 * n * k > NOALLOC_MAX_ENTRIES:
+        raise ValueError(f"2n*k = {2 * n * k} exceeds the fixed scratch of {NOALLOC_MAX_ENTRIES} entries")
+    if not (lam.is_cuda and lam.dtype == torch.float64 and lam.is_contiguous() and lam.numel() == k):
+        raise ValueError("lam must be a contiguous CUDA float64 tensor with one entry per vector")
+    if not (out.is_cuda and out.dtype == torch.float64 and out.is_contiguous() and out.numel() == k):
+        raise ValueError("out must be a contiguous CUDA float64 tensor with one entry per vector")
+    _check(lib().chase_bse_residuals_noalloc(_ptr(A), _ptr(B), n, _ptr(W), _ptr(lam), k, _ptr(out),
+                                             ctypes.c_void_p(_stream(stream))), "chase_bse_residuals_noalloc")
+    return out
 
 
 def grad(V: torch.Tensor, w: torch.Tensor, stream=None):
