@@ -48,7 +48,36 @@ def parse():
     p.add_argument("--precision", default="auto", choices=["auto", "fp64", "mixed"])
     p.add_argument("--no-fp64-compare", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=None)
+    p.add_argument("--filter-only", action="store_true",
+                   help="only the filter roofline measurement (one warm and one timed chase_bse_filter call)")
+    p.add_argument("--deg", type=int, default=None, help="filter degree for --filter-only")
     return p.parse_args()
+
+
+def filter_only(args, wl):
+    import torch
+    import paper_2601_10557_gb300 as pkg
+    P, W0n, _, _ = make_inputs(wl, 0)
+    dev = torch.device("cuda", 0)
+    A = torch.from_numpy(P.A).to(dev)
+    B = torch.from_numpy(P.B).to(dev)
+    W = torch.from_numpy(W0n).to(dev)
+    prec = args.precision if args.precision != "auto" else ("mixed" if pkg.has_mixed() else "fp64")
+    deg = args.deg or wl["deg"]
+    k = W.shape[0]
+    pkg.filter(A, B, W.clone(), [deg] * k, 1.0, 2.0, 60.0, precision=prec)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    Wt = W.clone()
+    e0.record()
+    pkg.filter(A, B, Wt, [deg] * k, 1.0, 2.0, 60.0, precision=prec)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    fl = 64.0 * wl["n"] ** 2 * k * deg
+    print(json.dumps({"filter_only": True, "precision": prec, "n": wl["n"], "k": k, "deg": deg, "ms": ms,
+                      "tflops": fl / ms / 1e9}), flush=True)
 
 
 def load_peaks():
@@ -170,6 +199,9 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, wl, rank, world)
+        return
+    if args.filter_only:
+        filter_only(args, wl)
         return
 
     import numpy as np
