@@ -16,12 +16,15 @@
 //   BF16x3: 2 pieces each, x0 y0 + x0 y1 + x1 y0          (~16 bits, ~1.5e-5)
 //   BF16x6: 3 pieces each, adds x0 y2 + x1 y1 + x2 y0      (FP32 class, ~2e-7)
 //
-// Kernel structure (one 128 x BN output tile per CTA, 256 threads):
+// Kernel structure (one 128 x 128 output tile per CTA, 256 threads):
 //   warp 0   TMA producer: the A and B pieces of 64 K-elements (128B swizzle)
-//            into a 2-stage shared-memory ring, mbarrier transaction counts
-//   warp 1   allocates BN TMEM columns; one lane issues the tcgen05.mma of a
-//            stage (4 K-steps x products) and commits the stage to the producer
-//   warps 4-7 epilogue: tcgen05.ld of their 32 TMEM lanes, then either
+//            into a 3-stage (BF16x3) or 2-stage (BF16x6) shared-memory ring
+//   warp 1   allocates all 512 TMEM columns (two accumulator buffers, each a
+//            hi*hi accumulator and one for the cross products); one lane issues
+//            the tcgen05.mma of a K block into buffer kb & 1
+//   warps 4-7 drain each K block's partial sums (tcgen05.ld) into FP32
+//            registers while the next block accumulates in the other buffer,
+//            because the tensor core's FP32 accumulation truncates; then either
 //            (mode 0) store the next GEMM's B-operand planes, or
 //            (mode 1) the fused three-term recurrence in FP32 plus the planes, or
 //            (mode 2) Z = H X + gamma_col * X (no planes).
@@ -43,39 +46,41 @@
 namespace cb {
 namespace tc {
 
-constexpr int BM = 128, BK = 64, STAGES = 2;
+constexpr int BM = 128, BK = 64, BN = 128;
 constexpr int A_BYTES = BM * BK * 2;  // 16 KB per piece
+constexpr int B_BYTES = BN * BK * 2;  // 16 KB per piece
 constexpr int THREADS = 256;
-constexpr int GROUP_M = 8;  // tile raster: GROUP_M row tiles x all column tiles per group
+constexpr int GROUP_M = 8;            // tile raster: GROUP_M row tiles x all column tiles per group
+constexpr uint32_t TMEM_COLS = 512;   // hi*hi accumulator x 2 buffers + cross products (+ spare)
+constexpr int FLUSH = 2;              // K blocks per drained hi*hi partial sum
+constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;  // bound of every mbarrier wait
+// instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, 128 x BN
+constexpr uint32_t IDESC =
+    (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 
-// Scheme: pieces of A (NPA) and B (NPW), product list, tile width BN.
+// Scheme: pieces of A (NPA) and B (NPW), product list (product 0 is x0 * y0).
 template <int NP>
 struct Scheme;
 template <>
 struct Scheme<3> {  // BF16x3
-  static constexpr int NPA = 2, NPW = 2, BN = 256, NPROD = 3;
+  static constexpr int NPA = 2, NPW = 2, NPROD = 3, STAGES = 3;
   __device__ static constexpr int pa(int i) { return i == 2 ? 1 : 0; }
   __device__ static constexpr int pb(int i) { return i == 1 ? 1 : 0; }
 };
 template <>
 struct Scheme<6> {  // BF16x6
-  static constexpr int NPA = 3, NPW = 3, BN = 128, NPROD = 6;
+  static constexpr int NPA = 3, NPW = 3, NPROD = 6, STAGES = 2;
   // (0,0) (0,1) (1,0) (0,2) (1,1) (2,0)
   __device__ static constexpr int pa(int i) { return i == 2 ? 1 : (i == 4 ? 1 : (i == 5 ? 2 : 0)); }
   __device__ static constexpr int pb(int i) { return i == 1 ? 1 : (i == 3 ? 2 : (i == 4 ? 1 : 0)); }
 };
 template <int NP>
 struct Geo {
-  static constexpr int BN = Scheme<NP>::BN;
-  static constexpr int B_BYTES = BN * BK * 2;
-  static constexpr int STAGE_BYTES = Scheme<NP>::NPA * A_BYTES + Scheme<NP>::NPW * B_BYTES;  // 96 KB
+  static constexpr int STAGES = Scheme<NP>::STAGES;
+  static constexpr int STAGE_BYTES = Scheme<NP>::NPA * A_BYTES + Scheme<NP>::NPW * B_BYTES;
+  static constexpr int NBAR = 2 * STAGES + 5;  // full, empty, acc_full[2], acc_empty[2], done
   static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
-  static constexpr uint32_t TMEM_COLS = BN;
-  // instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, 128 x BN
-  static constexpr uint32_t IDESC =
-      (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 };
-constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;
 
 struct Epi {
   int mode;           // 0: operand planes, 1: recurrence, 2: H X + gamma X
@@ -174,6 +179,34 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 }
 
 // (a, b) -> NPC BF16 pieces each (round to nearest even at every step)
+__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// sum[0..BN) += the warp's TMEM lanes at columns [col, col + BN), two loads in flight
+template <int N>
+__device__ __forceinline__ void drain_add(uint32_t col, float* sum) {
+#pragma unroll
+  for (int c = 0; c < N / 32; c += 2) {
+    uint32_t r0[32], r1[32];
+    tmem_ld32_nowait(col + (uint32_t)(c * 32), r0);
+    tmem_ld32_nowait(col + (uint32_t)((c + 1) * 32), r1);
+    tmem_wait_ld();
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      sum[c * 32 + i] += __uint_as_float(r0[i]);
+      sum[(c + 1) * 32 + i] += __uint_as_float(r1[i]);
+    }
+  }
+}
+
 template <int NPC>
 __device__ __forceinline__ void put(__nv_bfloat16* const* pc, int64_t off, float a, float b) {
 #pragma unroll
@@ -206,23 +239,36 @@ struct Maps {
   CUtensorMap b[3];
 };
 
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// One 128 x 128 output tile per CTA.  The dominant product x0*y0 accumulates
+// in one of two TMEM buffers that alternate every FLUSH K blocks; the four
+// epilogue warps drain each finished buffer into FP32 registers (round to
+// nearest) while the MMA fills the other one, so the tensor core's truncating
+// accumulator never sums more than 4 * FLUSH MMAs of the large product.  The
+// cross products, 2^-8 smaller, accumulate over the whole K in a third buffer
+// whose truncation error stays below FP32 rounding of the total.
 template <int NP>
 __global__ void __launch_bounds__(THREADS, 1)
     tc_hop_kernel(const __grid_constant__ Maps maps, Epi ep, int num_kb, int num_m, int num_n) {
   using SC = Scheme<NP>;
   using G = Geo<NP>;
-  constexpr int BN = G::BN;
+  constexpr int ST = G::STAGES;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * G::STAGE_BYTES);
-  uint32_t full[STAGES], empty[STAGES];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + ST * G::STAGE_BYTES);
+  uint32_t full[ST], empty[ST];
 #pragma unroll
-  for (int s = 0; s < STAGES; ++s) {
+  for (int s = 0; s < ST; ++s) {
     full[s] = smem_u32(bars + s);
-    empty[s] = smem_u32(bars + STAGES + s);
+    empty[s] = smem_u32(bars + ST + s);
   }
-  const uint32_t tfull = smem_u32(bars + 2 * STAGES);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
+  const uint32_t accf[2] = {smem_u32(bars + 2 * ST), smem_u32(bars + 2 * ST + 1)};
+  const uint32_t acce[2] = {smem_u32(bars + 2 * ST + 2), smem_u32(bars + 2 * ST + 3)};
+  const uint32_t done = smem_u32(bars + 2 * ST + 4);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + G::NBAR);
   volatile int* abort_sh = reinterpret_cast<volatile int*>(tmem_slot + 1);
   int* issued_sh = reinterpret_cast<int*>(tmem_slot + 2);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -239,18 +285,22 @@ __global__ void __launch_bounds__(THREADS, 1)
   const int m0 = mt * BM, n0 = nt * BN;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
+    for (int s = 0; s < ST; ++s) {
       mbar_init(full[s], 1);
       mbar_init(empty[s], 1);
     }
-    mbar_init(tfull, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(accf[b], 1);
+      mbar_init(acce[b], 4);  // one arrival per epilogue warp
+    }
+    mbar_init(done, 1);
     *abort_sh = 0;
     *issued_sh = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(G::TMEM_COLS)
+                 "r"(TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -263,55 +313,85 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (warp == 0 && lane == 0) {
     int issued = 0;
     for (int kb = 0; kb < num_kb; ++kb) {
-      const int s = kb % STAGES;
-      const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
-      if (kb >= STAGES && !mbar_wait(empty[s], ph ^ 1u, abort_sh, ep.err, true)) break;
+      const int s = kb % ST;
+      const uint32_t ph = (uint32_t)(kb / ST) & 1u;
+      if (kb >= ST && !mbar_wait(empty[s], ph ^ 1u, abort_sh, ep.err, true)) break;
       const uint32_t st = sbase + s * G::STAGE_BYTES;
       mbar_expect_tx(full[s], G::STAGE_BYTES);
 #pragma unroll
       for (int q = 0; q < SC::NPA; ++q) tma_load_2d(st + q * A_BYTES, &maps.a[q], kb * BK, m0, full[s]);
 #pragma unroll
       for (int q = 0; q < SC::NPW; ++q)
-        tma_load_2d(st + SC::NPA * A_BYTES + q * G::B_BYTES, &maps.b[q], kb * BK, n0, full[s]);
+        tma_load_2d(st + SC::NPA * A_BYTES + q * B_BYTES, &maps.b[q], kb * BK, n0, full[s]);
       issued = kb + 1;
     }
     *issued_sh = issued;
   } else if (warp == 1 && lane == 0) {
+    const uint32_t small = tmem + (uint32_t)(2 * BN);
     for (int kb = 0; kb < num_kb; ++kb) {
-      const int s = kb % STAGES;
-      const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+      const int grp = kb / FLUSH, b = grp & 1;
+      const bool first = (kb % FLUSH) == 0;
+      const bool last = (kb % FLUSH) == FLUSH - 1 || kb == num_kb - 1;
+      if (first && grp >= 2 && !mbar_wait(acce[b], (uint32_t)((grp >> 1) - 1) & 1u, abort_sh, ep.err, true)) break;
+      const int s = kb % ST;
+      const uint32_t ph = (uint32_t)(kb / ST) & 1u;
       if (!mbar_wait(full[s], ph, abort_sh, ep.err, true)) break;
       tc_fence_after();
       const uint32_t st = sbase + s * G::STAGE_BYTES;
+      const uint32_t big = tmem + (uint32_t)(b * BN);
 #pragma unroll
       for (int kk = 0; kk < BK / 16; ++kk) {
 #pragma unroll
         for (int pr = 0; pr < SC::NPROD; ++pr) {
           const uint64_t ad = sdesc(st + SC::pa(pr) * A_BYTES + kk * 32);
-          const uint64_t bd = sdesc(st + SC::NPA * A_BYTES + SC::pb(pr) * G::B_BYTES + kk * 32);
-          mma_bf16(tmem, ad, bd, G::IDESC, (kb | kk | pr) != 0 ? 1u : 0u);
+          const uint64_t bd = sdesc(st + SC::NPA * A_BYTES + SC::pb(pr) * B_BYTES + kk * 32);
+          const uint32_t acc = (pr == 0) ? ((!first || kk > 0) ? 1u : 0u) : ((kb > 0 || kk > 0 || pr > 1) ? 1u : 0u);
+          mma_bf16(pr == 0 ? big : small, ad, bd, IDESC, acc);
         }
       }
       mma_commit(empty[s]);
+      if (last) mma_commit(accf[b]);
     }
-    mma_commit(tfull);  // completes once every MMA issued above has finished
+    mma_commit(done);  // completes once every MMA issued above has finished
   } else if (warp >= 4) {
     const int q = warp - 4;
-    const bool ok = mbar_wait(tfull, 0, abort_sh, ep.err, false);
-    // tcgen05.ld is .sync.aligned: make the decision warp-uniform and reconverge
-    const bool go = __all_sync(0xffffffffu, ok && !*abort_sh);
-    tc_fence_after();
+    const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+    float sum[BN];
+#pragma unroll
+    for (int i = 0; i < BN; ++i) sum[i] = 0.0f;
+    bool ok = true;
+    const int ngrp = (num_kb + FLUSH - 1) / FLUSH;
+    for (int grp = 0; grp < ngrp; ++grp) {
+      const int b = grp & 1;
+      const bool w = mbar_wait(accf[b], (uint32_t)(grp >> 1) & 1u, abort_sh, ep.err, true);
+      if (!__all_sync(0xffffffffu, w)) {  // warp-uniform (tcgen05.ld is .sync.aligned)
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      drain_add<BN>(tmem + lane_base + (uint32_t)(b * BN), sum);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(acce[b]);
+    }
+    if (ok) {  // the cross products, once every MMA has completed
+      const bool w = mbar_wait(done, 0, abort_sh, ep.err, true);
+      ok = __all_sync(0xffffffffu, w);
+      if (ok) {
+        tc_fence_after();
+        drain_add<BN>(tmem + lane_base + (uint32_t)(2 * BN), sum);
+      }
+    }
     const int64_t row = (int64_t)m0 + q * 32 + lane;
-    if (go) {
+    if (ok && !*abort_sh && row < ep.n) {
       const int64_t n = ep.n, n2 = 2 * ep.n;
+#pragma unroll
       for (int c = 0; c < BN / 32; ++c) {
-        float v[32];
-        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(c * 32), v);
-        if (row >= n) continue;
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
           const int64_t vg = (int64_t)(n0 >> 2) + c * 8 + t;
           if (vg >= ep.k) continue;
+          const float* v = sum + c * 32;
           const float2 ht = make_float2(v[4 * t], v[4 * t + 1]);        // (H x)_top(row)
           const float2 hb = make_float2(-v[4 * t + 2], v[4 * t + 3]);   // (H x)_bot(row)
           const int64_t ot = vg * n2 + row, ob = ot + n;
@@ -347,16 +427,21 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
   tc_fence_before();
   __syncthreads();
-  if (*abort_sh && threadIdx.x == 0) {
+  if (threadIdx.x == 0 && *abort_sh) {
     // drain copies still in flight into this CTA's shared memory (bounded)
     const int issued = *issued_sh;
-    for (int kb = max(0, issued - STAGES); kb < issued; ++kb)
-      mbar_wait(full[kb % STAGES], (uint32_t)(kb / STAGES) & 1u, abort_sh, ep.err, false);
+    for (int kb = max(0, issued - ST); kb < issued; ++kb)
+      mbar_wait(full[kb % ST], (uint32_t)(kb / ST) & 1u, abort_sh, ep.err, false);
+  }
+  if (warp == 1) {
+    // every MMA has finished before the accumulator memory is released
+    if (lane == 0) mbar_wait(done, 0, abort_sh, ep.err, false);
+    __syncwarp();
   }
   __syncthreads();
   if (warp == 1) {
-    __syncwarp();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(G::TMEM_COLS) : "memory");
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
   }
 }
 
@@ -496,7 +581,7 @@ static int apply(const POperand& P, const CUtensorMap* bmap, Epi ep, cudaStream_
   for (int q = 0; q < Scheme<NP>::NPA; ++q) maps.a[q] = P.map[q];
   for (int q = 0; q < Scheme<NP>::NPW; ++q) maps.b[q] = bmap[q];
   const int num_m = (int)cdiv(P.n, BM);
-  const int num_n = (int)cdiv(4 * ep.k, G::BN);
+  const int num_n = (int)cdiv(4 * ep.k, BN);
   const int num_kb = (int)(P.kpad / BK);
   tc_hop_kernel<NP><<<num_m * num_n, THREADS, G::SMEM_BYTES, s>>>(maps, ep, num_kb, num_m, num_n);
   count_launch();
@@ -523,7 +608,7 @@ static int filter_impl(const cplx* A, const cplx* B, int64_t n, const cplx* Y0, 
   Workspace ws(s);
   POperand P;
   CB_TRY(prepare_p<NP>(A, B, n, ws, P, s));
-  const int64_t rows = ((4 * k + G::BN - 1) / G::BN) * G::BN;  // whole tiles
+  const int64_t rows = ((4 * k + BN - 1) / BN) * BN;  // whole tiles
   Pieces Zp{}, Tp{};
   CUtensorMap mZ[3], mT[3];
   for (int q = 0; q < NPW; ++q) {
@@ -531,8 +616,8 @@ static int filter_impl(const cplx* A, const cplx* B, int64_t n, const cplx* Y0, 
     CB_TRY(ws.alloc(&Tp.p[q], rows * P.kpad));
     CB_CUDA(cudaMemsetAsync(Zp.p[q], 0, sizeof(__nv_bfloat16) * rows * P.kpad, s));
     CB_CUDA(cudaMemsetAsync(Tp.p[q], 0, sizeof(__nv_bfloat16) * rows * P.kpad, s));
-    CB_TRY(make_map(&mZ[q], Zp.p[q], P.kpad, rows, G::BN));
-    CB_TRY(make_map(&mT[q], Tp.p[q], P.kpad, rows, G::BN));
+    CB_TRY(make_map(&mZ[q], Zp.p[q], P.kpad, rows, BN));
+    CB_TRY(make_map(&mT[q], Tp.p[q], P.kpad, rows, BN));
   }
   float2 *Zb[3], *src = nullptr;
   float* gam;
