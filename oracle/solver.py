@@ -22,7 +22,9 @@ Readings where the paper is silent (the same ones the CUDA driver follows):
 * after locking, mu_nevex <- largest non-locked positive Ritz value
   (Section 4.1) among those below mu_N: a Ritz value above the Lanczos upper
   bound of the spectrum is spurious (Theorem field_of_values_ritz_hermitian_variant
-  and the remark after it) and is ignored; mu_1 <- min(mu_1, lambda_1);
+  and the remark after it) and is ignored; spurious values below mu_N also
+  occur in the first iterations, so mu_nevex grows by at most a factor 2 per
+  iteration; mu_1 <- min(mu_1, lambda_1);
 * mu_1 is only the normalisation point of the filter (p(mu_1^2) = 1) and must
   stay below mu_nevex, otherwise it falls inside the damped interval where the
   scaled recurrence divides by values of T_j near zero; mu_1 <- min(mu_1,
@@ -130,7 +132,7 @@ def solve(A, B, nev, nex, deg, tol, W0raw, starts, lanczos_steps=26, deg_min=Non
             break
         cand = ritz[keep][ritz[keep] < muN]
         if len(cand):
-            mu_nevex = float(cand.max())
+            mu_nevex = min(float(cand.max()), 2.0 * mu_nevex)
         if ritz[0] > 0:
             mu1 = min(mu1, float(ritz[0]))
         mu1 = min(mu1, 0.5 * mu_nevex)

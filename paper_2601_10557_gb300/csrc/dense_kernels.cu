@@ -494,6 +494,34 @@ int normalize_cols(cplx* X, int64_t rows, int64_t m, cudaStream_t s) {
   CB_LAUNCH();
   return CHASE_BSE_OK;
 }
+__global__ void normalize_and_residual_kernel(cplx* W, const cplx* SHW, const double* ritz, int64_t n, cplx* R) {
+  __shared__ double sh[32];
+  const int64_t j = blockIdx.x, n2 = 2 * n;
+  cplx* w = W + j * n2;
+  const cplx* h = SHW + j * n2;
+  cplx* r = R + j * n2;
+  double ss = 0.0;
+  for (int64_t i = threadIdx.x; i < n2; i += blockDim.x) ss += cabs2(w[i]);
+  ss = block_sum(ss, sh);
+  const double inv = ss > 0.0 ? 1.0 / sqrt(ss) : 0.0;
+  const double lam = ritz[j];
+  for (int64_t i = threadIdx.x; i < n2; i += blockDim.x) {
+    const cplx wn = cscale(w[i], inv);
+    cplx hw = cscale(h[i], inv);
+    if (i >= n) hw = mk(-hw.x, -hw.y);  // undo S
+    w[i] = wn;
+    r[i] = csub(hw, cscale(wn, lam));
+  }
+}
+int normalize_and_residual(cplx* W, const cplx* SHW, const double* ritz, int64_t n, int64_t m, cplx* R,
+                           cudaStream_t s) {
+  if (m == 0) return CHASE_BSE_OK;
+  normalize_and_residual_kernel<<<(unsigned)m, 256, 0, s>>>(W, SHW, ritz, n, R);
+  count_launch();
+  CB_LAUNCH();
+  return CHASE_BSE_OK;
+}
+
 __global__ void set_identity_kernel(cplx* M, int64_t k) {
   GRID_STRIDE(i, k * k) { M[i] = (i % k == i / k) ? mk(1, 0) : mk(0, 0); }
 }

@@ -36,6 +36,10 @@ int collect_cols(cplx* dst, const cplx* b0, const cplx* b1, const cplx* b2, cons
 int scatter_cols(cplx* dst, const cplx* src, const int* idx, int64_t rows, int64_t m, cudaStream_t s);
 int col_norms(const cplx* X, int64_t rows, int64_t m, double* out, cudaStream_t s);
 int normalize_cols(cplx* X, int64_t rows, int64_t m, cudaStream_t s);
+// Given W (2n x m, unnormalised Ritz vectors), HZ = S H W (2n x m) and ritz (device):
+// nrm_j = ||W_j||, W_j /= nrm_j, R_j = S HZ_j / nrm_j - ritz_j W_j.
+int normalize_and_residual(cplx* W, const cplx* SHW, const double* ritz, int64_t n, int64_t m, cplx* R,
+                           cudaStream_t s);
 int set_identity(cplx* M, int64_t k, cudaStream_t s);
 int hermitize(cplx* G, int64_t k, cudaStream_t s);
 int diag_real(const cplx* G, int64_t k, double* out, cudaStream_t s);

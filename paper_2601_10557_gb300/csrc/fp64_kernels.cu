@@ -16,9 +16,38 @@ namespace cb {
 // bottom half (H W)_bot = -conj(P [conj(Y); conj(X)]).  The K loop runs over
 // the 2n columns of P = [A | B]; the second operand is built on the fly from W
 // with the half-swap and conjugation, so W_hat is never stored.
+// Epilogue of the H application for output row i (< n) of column j: C1 = (P w)_i,
+// C2 = (P u)_i, so (H w)_top(i) = C1 and (H w)_bot(i) = -conj(C2).
+__device__ __forceinline__ void hop_epilogue(const HopArgs& a, int64_t i, int64_t j, cplx c1, cplx c2) {
+  const int64_t n = a.n, n2 = 2 * a.n;
+  const cplx top = c1;
+  const cplx bot = mk(-c2.x, c2.y);  // -conj(C2)
+  const int64_t ot = j * n2 + i, ob = j * n2 + n + i;
+  if (a.mode == HOP_STORE) {
+    a.out[ot] = top;
+    a.out[ob] = a.sflip ? mk(-bot.x, -bot.y) : bot;
+  } else if (a.mode == HOP_CHEB) {
+    cplx t = csub(top, cscale(a.Wc[ot], a.c));
+    cplx b = csub(bot, cscale(a.Wc[ob], a.c));
+    t = cscale(t, a.alpha);
+    b = cscale(b, a.alpha);
+    if (a.beta != 0.0) {
+      t = cadd(t, cscale(a.Wp[ot], a.beta));
+      b = cadd(b, cscale(a.Wp[ob], a.beta));
+    }
+    a.out[ot] = t;
+    a.out[ob] = b;
+  } else {  // HOP_RESID
+    const double lam = a.lambda[j];
+    a.out[ot] = csub(top, cscale(a.W[ot], lam));
+    a.out[ob] = csub(bot, cscale(a.W[ob], lam));
+  }
+}
+
+// part != NULL: K split over blockIdx.z in chunks of kchunk columns of P.
 template <int BM, int BNW, int TM, int TNW, int BK>
 __global__ void __launch_bounds__((BM / TM) * (BNW / TNW))
-hop_kernel(HopArgs a) {
+hop_kernel(HopArgs a, cplx* part, int64_t kchunk) {
   constexpr int TY = BM / TM;
   constexpr int TX = BNW / TNW;
   constexpr int NT = TX * TY;
@@ -38,19 +67,21 @@ hop_kernel(HopArgs a) {
 #pragma unroll
     for (int c = 0; c < TNW; ++c) { acc1[r][c] = mk(0, 0); acc2[r][c] = mk(0, 0); }
 
-  for (int64_t kb = 0; kb < n2; kb += BK) {
+  const int64_t kbeg = part ? (int64_t)blockIdx.z * kchunk : 0;
+  const int64_t kend = part ? (kbeg + kchunk < n2 ? kbeg + kchunk : n2) : n2;
+  for (int64_t kb = kbeg; kb < kend; kb += BK) {
     for (int idx = tid; idx < BM * BK; idx += NT) {
       const int r = idx / BK, cc = idx % BK;
       const int64_t gi = row0 + r, gl = kb + cc;
       cplx v = mk(0, 0);
-      if (gi < n && gl < n2) v = (gl < n) ? a.A[gi * n + gl] : a.B[gi * n + (gl - n)];
+      if (gi < n && gl < kend) v = (gl < n) ? a.A[gi * n + gl] : a.B[gi * n + (gl - n)];
       Ps[cc][r] = v;
     }
     for (int idx = tid; idx < BNW * BK; idx += NT) {
       const int j = idx / BK, l = idx % BK;
       const int64_t gj = col0 + j, gl = kb + l;
       cplx v1 = mk(0, 0), v2 = mk(0, 0);
-      if (gj < a.k && gl < n2) {
+      if (gj < a.k && gl < kend) {
         const cplx* w = a.W + gj * n2;
         v1 = w[gl];
         v2 = cconj(w[gl < n ? gl + n : gl - n]);
@@ -81,45 +112,87 @@ hop_kernel(HopArgs a) {
       const int64_t i = row0 + ty + TY * r;
       const int64_t j = col0 + tx + TX * c;
       if (i >= n || j >= a.k) continue;
-      const cplx top = acc1[r][c];
-      const cplx bot = mk(-acc2[r][c].x, acc2[r][c].y);  // -conj(C2)
-      const int64_t ot = j * n2 + i, ob = j * n2 + n + i;
-      if (a.mode == HOP_STORE) {
-        a.out[ot] = top;
-        a.out[ob] = a.sflip ? mk(-bot.x, -bot.y) : bot;
-      } else if (a.mode == HOP_CHEB) {
-        cplx t = csub(top, cscale(a.Wc[ot], a.c));
-        cplx b = csub(bot, cscale(a.Wc[ob], a.c));
-        t = cscale(t, a.alpha);
-        b = cscale(b, a.alpha);
-        if (a.beta != 0.0) {
-          t = cadd(t, cscale(a.Wp[ot], a.beta));
-          b = cadd(b, cscale(a.Wp[ob], a.beta));
-        }
-        a.out[ot] = t;
-        a.out[ob] = b;
-      } else {  // HOP_RESID
-        const double lam = a.lambda[j];
-        a.out[ot] = csub(top, cscale(a.W[ot], lam));
-        a.out[ob] = csub(bot, cscale(a.W[ob], lam));
+      if (part) {  // split K: raw partial sums of P W and P U for this K chunk
+        cplx* p = part + (int64_t)blockIdx.z * (2 * n * a.k) + j * n2;
+        p[i] = acc1[r][c];
+        p[n + i] = acc2[r][c];
+      } else {
+        hop_epilogue(a, i, j, acc1[r][c], acc2[r][c]);
       }
     }
   }
 }
 
+template <int BM, int BNW>
+__global__ void hop_reduce_kernel(HopArgs a, const cplx* part, int nsplit) {
+  const int64_t n = a.n, n2 = 2 * n, total = n * a.k;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx % n, j = idx / n;
+    cplx c1 = mk(0, 0), c2 = mk(0, 0);
+    for (int z = 0; z < nsplit; ++z) {
+      const cplx* p = part + (int64_t)z * (2 * n * a.k) + j * n2;
+      c1 = cadd(c1, p[i]);
+      c2 = cadd(c2, p[n + i]);
+    }
+    hop_epilogue(a, i, j, c1, c2);
+  }
+}
+
+static int num_sms() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                 cudaSuccess || sms <= 0)
+      sms = 148;
+  }
+  return sms;
+}
+
+// Number of K chunks so that a small output grid still fills the GPU (two CTAs per
+// SM); 1 when the grid is large enough or K too short to split.
+static int64_t split_count(int64_t tiles, int64_t K, int64_t min_chunk) {
+  const int64_t want = 2 * (int64_t)num_sms();
+  if (tiles >= want || K < 2 * min_chunk) return 1;
+  int64_t s = (want + tiles - 1) / tiles;
+  if (s > K / min_chunk) s = K / min_chunk;
+  return s < 1 ? 1 : s;
+}
+
+template <int BM, int BNW, int TM, int TNW>
+static int hop_launch(const HopArgs& a, cudaStream_t s) {
+  const int64_t tiles = (int64_t)cdiv(a.n, BM) * cdiv(a.k, BNW);
+  const int64_t n2 = 2 * a.n;
+  const int64_t nsplit = split_count(tiles, n2, 256);
+  if (nsplit <= 1) {
+    dim3 grid(cdiv(a.n, BM), cdiv(a.k, BNW));
+    hop_kernel<BM, BNW, TM, TNW, 16><<<grid, (BM / TM) * (BNW / TNW), 0, s>>>(a, nullptr, 0);
+    count_launch();
+    CB_LAUNCH();
+    return CHASE_BSE_OK;
+  }
+  const int64_t kchunk = ((n2 + nsplit - 1) / nsplit + 15) / 16 * 16;
+  const int64_t ns = (n2 + kchunk - 1) / kchunk;
+  cplx* part = nullptr;
+  CB_CUDA(cudaMallocAsync(&part, sizeof(cplx) * ns * 2 * a.n * a.k, s));
+  dim3 grid(cdiv(a.n, BM), cdiv(a.k, BNW), (unsigned)ns);
+  hop_kernel<BM, BNW, TM, TNW, 16><<<grid, (BM / TM) * (BNW / TNW), 0, s>>>(a, part, kchunk);
+  count_launch();
+  const int64_t total = a.n * a.k;
+  const unsigned rb = (unsigned)((total + 255) / 256 < 8192 ? (total + 255) / 256 : 8192);
+  hop_reduce_kernel<BM, BNW><<<rb, 256, 0, s>>>(a, part, (int)ns);
+  count_launch();
+  cudaError_t e = cudaGetLastError();
+  cudaFreeAsync(part, s);
+  if (e != cudaSuccess) return CHASE_BSE_CUDA_ERROR;
+  return CHASE_BSE_OK;
+}
+
 int hop_fp64(const HopArgs& a, cudaStream_t s) {
   if (a.k <= 0 || a.n <= 0) return CHASE_BSE_OK;
-  if (a.k <= 4) {
-    dim3 grid(cdiv(a.n, 64), cdiv(a.k, 4));
-    hop_kernel<64, 4, 1, 1, 16><<<grid, 256, 0, s>>>(a);
-    count_launch();
-  } else {
-    dim3 grid(cdiv(a.n, 64), cdiv(a.k, 32));
-    hop_kernel<64, 32, 4, 2, 16><<<grid, 256, 0, s>>>(a);
-    count_launch();
-  }
-  CB_LAUNCH();
-  return CHASE_BSE_OK;
+  if (a.k <= 4) return hop_launch<64, 4, 1, 1>(a, s);
+  return hop_launch<64, 32, 4, 2>(a, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -131,10 +204,12 @@ __device__ __forceinline__ cplx load_op(const cplx* X, int64_t ld, char op, int6
   return op == 'C' ? cconj(v) : v;
 }
 
+// kchunk > 0: K split over blockIdx.z; block z writes alpha * its partial product to
+// C + z * ldc * N (beta ignored).
 template <int BM, int BN, int TM, int TN, int BK>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN))
 zgemm_kernel(char opA, char opB, int64_t M, int64_t N, int64_t K, cplx alpha, const cplx* __restrict__ A,
-             int64_t lda, const cplx* __restrict__ B, int64_t ldb, cplx beta, cplx* C, int64_t ldc) {
+             int64_t lda, const cplx* __restrict__ B, int64_t ldb, cplx beta, cplx* C, int64_t ldc, int64_t kchunk) {
   constexpr int TY = BM / TM;
   constexpr int TX = BN / TN;
   constexpr int NT = TX * TY;
@@ -151,18 +226,24 @@ zgemm_kernel(char opA, char opB, int64_t M, int64_t N, int64_t K, cplx alpha, co
 #pragma unroll
     for (int c = 0; c < TN; ++c) acc[r][c] = mk(0, 0);
 
-  for (int64_t kb = 0; kb < K; kb += BK) {
+  const int64_t kbeg = kchunk ? (int64_t)blockIdx.z * kchunk : 0;
+  const int64_t kend = kchunk ? (kbeg + kchunk < K ? kbeg + kchunk : K) : K;
+  if (kchunk) {
+    C += (int64_t)blockIdx.z * ldc * N;
+    beta = mk(0, 0);
+  }
+  for (int64_t kb = kbeg; kb < kend; kb += BK) {
     for (int idx = tid; idx < BM * BK; idx += NT) {
       int r, l;
       if (opA == 'N') { r = idx % BM; l = idx / BM; } else { l = idx % BK; r = idx / BK; }
       const int64_t gr = row0 + r, gl = kb + l;
-      As[l][r] = (gr < M && gl < K) ? load_op(A, lda, opA, gr, gl) : mk(0, 0);
+      As[l][r] = (gr < M && gl < kend) ? load_op(A, lda, opA, gr, gl) : mk(0, 0);
     }
     for (int idx = tid; idx < BN * BK; idx += NT) {
       int c, l;
       if (opB == 'N') { l = idx % BK; c = idx / BK; } else { c = idx % BN; l = idx / BN; }
       const int64_t gc = col0 + c, gl = kb + l;
-      Bs[l][c] = (gc < N && gl < K) ? load_op(B, ldb, opB, gl, gc) : mk(0, 0);
+      Bs[l][c] = (gc < N && gl < kend) ? load_op(B, ldb, opB, gl, gc) : mk(0, 0);
     }
     __syncthreads();
 #pragma unroll 4
@@ -193,24 +274,56 @@ zgemm_kernel(char opA, char opB, int64_t M, int64_t N, int64_t K, cplx alpha, co
   }
 }
 
+// C = alpha * sum_z part[z] + beta * C
+__global__ void zgemm_reduce_kernel(const cplx* part, int nsplit, int64_t M, int64_t N, cplx beta, cplx* C,
+                                    int64_t ldc) {
+  const int64_t total = M * N;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx % M, j = idx / M;
+    cplx v = mk(0, 0);
+    for (int z = 0; z < nsplit; ++z) v = cadd(v, part[(int64_t)z * M * N + idx]);
+    if (beta.x != 0.0 || beta.y != 0.0) v = cadd(v, cmul(beta, C[i + j * ldc]));
+    C[i + j * ldc] = v;
+  }
+}
+
+template <int BM, int BN, int TM, int TN>
+static int zgemm_launch(char opA, char opB, int64_t M, int64_t N, int64_t K, cplx alpha, const cplx* A, int64_t lda,
+                        const cplx* B, int64_t ldb, cplx beta, cplx* C, int64_t ldc, cudaStream_t s) {
+  const int64_t tiles = (int64_t)cdiv(M, BM) * cdiv(N, BN);
+  const int64_t nsplit = split_count(tiles, K, 512);
+  dim3 grid(cdiv(M, BM), cdiv(N, BN));
+  if (nsplit <= 1) {
+    zgemm_kernel<BM, BN, TM, TN, 8><<<grid, 256, 0, s>>>(opA, opB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, 0);
+    count_launch();
+    CB_LAUNCH();
+    return CHASE_BSE_OK;
+  }
+  const int64_t kchunk = ((K + nsplit - 1) / nsplit + 7) / 8 * 8;
+  const int64_t ns = (K + kchunk - 1) / kchunk;
+  cplx* part = nullptr;
+  CB_CUDA(cudaMallocAsync(&part, sizeof(cplx) * ns * M * N, s));
+  grid.z = (unsigned)ns;
+  zgemm_kernel<BM, BN, TM, TN, 8><<<grid, 256, 0, s>>>(opA, opB, M, N, K, alpha, A, lda, B, ldb, beta, part, M,
+                                                       kchunk);
+  count_launch();
+  const int64_t total = M * N;
+  const unsigned rb = (unsigned)((total + 255) / 256 < 8192 ? (total + 255) / 256 : 8192);
+  zgemm_reduce_kernel<<<rb, 256, 0, s>>>(part, (int)ns, M, N, beta, C, ldc);
+  count_launch();
+  cudaError_t e = cudaGetLastError();
+  cudaFreeAsync(part, s);
+  if (e != cudaSuccess) return CHASE_BSE_CUDA_ERROR;
+  return CHASE_BSE_OK;
+}
+
 int zgemm(char opA, char opB, int64_t M, int64_t N, int64_t K, cplx alpha, const cplx* A, int64_t lda,
           const cplx* B, int64_t ldb, cplx beta, cplx* C, int64_t ldc, cudaStream_t s) {
   if (M <= 0 || N <= 0) return CHASE_BSE_OK;
-  if (K <= 0) {
-    // C = beta C: run the kernel with an empty K loop
-    K = 0;
-  }
-  if (M <= 16 || N <= 16) {
-    dim3 grid(cdiv(M, 32), cdiv(N, 32));
-    zgemm_kernel<32, 32, 2, 2, 8><<<grid, 256, 0, s>>>(opA, opB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
-    count_launch();
-  } else {
-    dim3 grid(cdiv(M, 64), cdiv(N, 64));
-    zgemm_kernel<64, 64, 4, 4, 8><<<grid, 256, 0, s>>>(opA, opB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
-    count_launch();
-  }
-  CB_LAUNCH();
-  return CHASE_BSE_OK;
+  if (K < 0) K = 0;  // K = 0: C = beta C (empty K loop)
+  if (M <= 16 || N <= 16) return zgemm_launch<32, 32, 2, 2>(opA, opB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s);
+  return zgemm_launch<64, 64, 4, 4>(opA, opB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s);
 }
 
 }  // namespace cb

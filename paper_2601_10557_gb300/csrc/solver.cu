@@ -321,7 +321,7 @@ int qr(const cplx* X, int64_t n2, int64_t m, cplx* Q, int* used_hh, cudaStream_t
 
 // --------------------------------------------------------------- Rayleigh-Ritz
 int rayleigh_ritz(const cplx* A, const cplx* B, int64_t n, const cplx* Q, int64_t k, double* ritz_host,
-                  cplx* Wpos, cudaStream_t s) {
+                  cplx* Wpos, cudaStream_t s, cplx* R, double* res) {
   if (k <= 0 || (k % 2) != 0) return CHASE_BSE_BAD_ARG;
   const int64_t n2 = 2 * n, h = k / 2;
   Workspace ws(s);
@@ -362,7 +362,13 @@ int rayleigh_ritz(const cplx* A, const cplx* B, int64_t n, const cplx* Q, int64_
   CB_TRY(hermitize(G, k, s));
   // line 8: G y = theta y
   int sweeps = 0;
+  const auto tj = std::chrono::steady_clock::now();
   CB_TRY(jacobi_eigh(G, k, V, theta, rot, red, 40, &sweeps, s));
+  if (verbose()) {
+    cudaStreamSynchronize(s);
+    fprintf(stderr, "[chase_bse] rr k %ld jacobi %d sweeps %.1f ms\n", (long)k, sweeps,
+            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tj).count());
+  }
   std::vector<double> th(k);
   CB_CUDA(cudaMemcpyAsync(th.data(), theta, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
   CB_CUDA(cudaStreamSynchronize(s));
@@ -379,8 +385,20 @@ int rayleigh_ritz(const cplx* A, const cplx* B, int64_t n, const cplx* Q, int64_
   // line 9 (read as z = L^{-*} y) and the half back-transform W+ = Q Z+
   CB_TRY(zgemm('C', 'N', k, h, k, mk(1, 0), Linv, k, Ypos, k, mk(0, 0), Z, k, s));
   CB_TRY(zgemm('N', 'N', n2, h, k, mk(1, 0), Q, n2, Z, k, mk(0, 0), Wpos, n2, s));
-  CB_TRY(normalize_cols(Wpos, n2, h, s));
-  CB_CUDA(cudaStreamSynchronize(s));  // pos must outlive the copy
+  if (R && res) {
+    // Section 4.5 residuals on the positive half: H W+ = H Q Z+ = S T Z+
+    cplx* SHW;
+    CB_TRY(ws.alloc(&SHW, n2 * h));
+    CB_TRY(zgemm('N', 'N', n2, h, k, mk(1, 0), T, n2, Z, k, mk(0, 0), SHW, n2, s));
+    double* rz;
+    CB_TRY(ws.alloc(&rz, h));
+    CB_CUDA(cudaMemcpyAsync(rz, ritz_host, sizeof(double) * h, cudaMemcpyHostToDevice, s));
+    CB_TRY(normalize_and_residual(Wpos, SHW, rz, n, h, R, s));
+    CB_TRY(col_norms(R, n2, h, res, s));
+  } else {
+    CB_TRY(normalize_cols(Wpos, n2, h, s));
+  }
+  CB_CUDA(cudaStreamSynchronize(s));  // host vectors must outlive the copies
   return CHASE_BSE_OK;
 }
 
@@ -555,13 +573,14 @@ int solve(const cplx* A, const cplx* B, int64_t n, int64_t nev, int64_t nex, int
     // lines 8-10: Rayleigh-Ritz, W+ = Q Z+
     clk.start();
     std::vector<double> ritz(kf);
-    int rs = rayleigh_ritz(A, B, n, Q, 2 * kf, ritz.data(), Wpos, s);
+    cplx* Rvec = Rall;
+    Workspace rws(s);
+    if (!Rvec) CB_TRY(rws.alloc(&Rvec, n2 * kf));
+    // lines 8-11: Rayleigh-Ritz, W+ = Q Z+ and the residuals of the positive half
+    int rs = rayleigh_ritz(A, B, n, Q, 2 * kf, ritz.data(), Wpos, s, Rvec, res_d);
     st.ms_rr += clk.stop();
     if (rs != CHASE_BSE_OK) { status = rs; break; }
-    // line 11: residuals of the positive half
     clk.start();
-    CB_CUDA(cudaMemcpyAsync(lam_d, ritz.data(), sizeof(double) * kf, cudaMemcpyHostToDevice, s));
-    CB_TRY(residuals(A, B, n, Wpos, lam_d, kf, res_d, s, Rall));
     std::vector<double> res(kf);
     CB_CUDA(cudaMemcpyAsync(res.data(), res_d, sizeof(double) * kf, cudaMemcpyDeviceToHost, s));
     CB_CUDA(cudaStreamSynchronize(s));
@@ -609,11 +628,12 @@ int solve(const cplx* A, const cplx* B, int64_t n, int64_t nev, int64_t nex, int
       kprev.push_back(prev_res[i]);
       kdeg.push_back(degs[i]);
     }
-    // mu_nevex <- largest non-locked Ritz value below mu_N (larger ones are spurious)
+    // mu_nevex <- largest non-locked Ritz value below mu_N (larger ones are spurious),
+    // growing by at most a factor 2 per iteration (spurious values below mu_N occur early)
     double cand = -1.0;
     for (double r : kr)
       if (r < muN) cand = std::max(cand, r);
-    if (cand > 0.0) mu_ne = cand;
+    if (cand > 0.0) mu_ne = std::min(cand, 2.0 * mu_ne);
     if (ritz[0] > 0.0) mu1 = std::min(mu1, ritz[0]);
     mu1 = std::min(mu1, 0.5 * mu_ne);
     degrees_update(kr, kres, kprev, kdeg, tol, mu_ne, muN, o.deg_min, o.deg_max, degs);
