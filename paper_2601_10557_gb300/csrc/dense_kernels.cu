@@ -177,20 +177,27 @@ __device__ __forceinline__ void jpair(int64_t slot, int r, int64_t k, int64_t& p
   q = a < b ? b : a;
 }
 
-__global__ void jacobi_rot_kernel(const cplx* G, int64_t k, int r, cplx* rot) {
+// Rotation of pair (p, q) of round r.  Entries negligible next to their diagonal
+// (|a_pq| <= 1e-17 sqrt|a_pp a_qq|) or to the matrix (|a_pq| <= 1e-18 ||G||_F)
+// are skipped (threshold Jacobi); a sweep that applies no rotation ends the
+// iteration.  |a_pq| is formed with hypot: squaring entries that have become tiny
+// would underflow and make the rotation non-unitary.
+__global__ void jacobi_rot_kernel(const cplx* G, int64_t k, int r, cplx* rot, const double* red, int* applied) {
   const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (slot >= k / 2) return;
   int64_t p, q;
   jpair(slot, r, k, p, q);
   const double app = G[p + p * k].x, aqq = G[q + q * k].x;
   const cplx apq = G[p + q * k];
-  const double rr = sqrt(cabs2(apq));
+  const double rr = hypot(apq.x, apq.y);
+  const double normG = sqrt(red[1]);
   cplx J00 = mk(1, 0), J01 = mk(0, 0), J10 = mk(0, 0), J11 = mk(1, 0);
-  if (rr > 1e-300) {
+  if (rr > 2e-16 * sqrt(fabs(app * aqq)) && rr > 1e-16 * normG && rr > 1e-300) {
+    atomicAdd(applied, 1);
     const cplx ec = mk(apq.x / rr, -apq.y / rr);  // conj(e^{i phi})
     const double tau = (aqq - app) / (2.0 * rr);
-    const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-    const double c = 1.0 / sqrt(1.0 + t * t), sn = t * c;
+    const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + hypot(1.0, tau));
+    const double c = 1.0 / hypot(1.0, t), sn = t * c;
     J00 = mk(c, 0);
     J01 = mk(sn, 0);
     J10 = cscale(ec, -sn);
@@ -259,25 +266,33 @@ int jacobi_eigh(cplx* G, int64_t k, cplx* V, double* theta, cplx* rot, double* r
   const int64_t half = k / 2;
   const int64_t items = half * half + k * half;
   const unsigned gapply = (unsigned)((items + 255) / 256 < 2048 ? (items + 255) / 256 : 2048);
-  double hred[2];
+  double hred[2] = {0, 0};
+  int* applied = nullptr;
+  CB_CUDA(cudaMallocAsync(&applied, sizeof(int), s));
+  offdiag_norm_kernel<<<1, 1024, 0, s>>>(G, k, red);  // red[1] = ||G||_F^2 (invariant)
+  count_launch();
+  int happ = 1;
   for (; sweeps < max_sweeps; ++sweeps) {
-    offdiag_norm_kernel<<<1, 1024, 0, s>>>(G, k, red);
-    count_launch();
-    CB_LAUNCH();
-    CB_CUDA(cudaMemcpyAsync(hred, red, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
-    CB_CUDA(cudaStreamSynchronize(s));
-    if (!(hred[0] > 1e-30 * hred[1])) break;  // off <= 1e-15 ||G||_F (or NaN guard)
+    CB_CUDA(cudaMemsetAsync(applied, 0, sizeof(int), s));
     for (int r = 0; r < k - 1; ++r) {
-      jacobi_rot_kernel<<<cdiv(half, 128), 128, 0, s>>>(G, k, r, rot);
+      jacobi_rot_kernel<<<cdiv(half, 128), 128, 0, s>>>(G, k, r, rot, red, applied);
       count_launch();
       jacobi_apply_kernel<<<gapply, 256, 0, s>>>(G, V, k, r, rot);
       count_launch();
     }
     CB_LAUNCH();
+    CB_CUDA(cudaMemcpyAsync(&happ, applied, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CB_CUDA(cudaMemcpyAsync(hred, red, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CB_CUDA(cudaStreamSynchronize(s));
+    if (happ == 0 || hred[1] != hred[1]) {
+      ++sweeps;
+      break;
+    }
   }
+  cudaFreeAsync(applied, s);
   if (sweeps_out) *sweeps_out = sweeps;
   CB_TRY(diag_real(G, k, theta, s));
-  if (hred[0] != hred[0]) return CHASE_BSE_CUDA_ERROR;  // NaN in G
+  if (hred[1] != hred[1]) return CHASE_BSE_CUDA_ERROR;  // NaN in G
   return CHASE_BSE_OK;
 }
 
@@ -414,6 +429,58 @@ int build_qr_input(cplx* X, const cplx* Yp, int64_t L, const cplx* Wf, int64_t k
   const int64_t tot = 2 * n * (2 * L + 2 * kf);
   if (tot == 0) return CHASE_BSE_OK;
   build_qr_input_kernel<<<gs(tot), 256, 0, s>>>(X, Yp, L, Wf, kf, n);
+  count_launch();
+  CB_LAUNCH();
+  return CHASE_BSE_OK;
+}
+
+__global__ void build_jfixed_kernel(cplx* Xt, const cplx* Yp, int64_t L, const cplx* W, int64_t kf, int64_t n) {
+  const int64_t n2 = 2 * n, cols = 2 * (L + kf);
+  GRID_STRIDE(idx, n * cols) {
+    const int64_t r = idx % n, c = idx / n;
+    cplx v;
+    if (c < 2 * L) {
+      const cplx* y = Yp + (c % L) * n2;
+      const cplx yt = y[r], ybc = cconj(y[n + r]);
+      // S y = [yt; -yb], J S y = [-conj(yb); conj(yt)]
+      v = (c < L) ? csub(yt, ybc) : cmul(mk(0, 1), cadd(yt, ybc));
+    } else {
+      const int64_t a = c - 2 * L;
+      const cplx* w = W + (a % kf) * n2;
+      const cplx wt = w[r], wbc = cconj(w[n + r]);
+      // J w = [conj(wb); conj(wt)]
+      v = (a < kf) ? cadd(wt, wbc) : cmul(mk(0, 1), csub(wt, wbc));
+    }
+    Xt[c * n + r] = v;
+  }
+}
+int build_jfixed(cplx* Xt, const cplx* Yp, int64_t L, const cplx* W, int64_t kf, int64_t n, cudaStream_t s) {
+  const int64_t tot = n * 2 * (L + kf);
+  if (tot == 0) return CHASE_BSE_OK;
+  build_jfixed_kernel<<<gs(tot), 256, 0, s>>>(Xt, Yp, L, W, kf, n);
+  count_launch();
+  CB_LAUNCH();
+  return CHASE_BSE_OK;
+}
+__global__ void re_im_part_kernel(const cplx* C, cplx* out, int64_t k, int mode) {
+  GRID_STRIDE(i, k * k) { out[i] = (mode == 0) ? mk(2.0 * C[i].x, 0.0) : mk(0.0, 2.0 * C[i].y); }
+}
+int re_im_part(const cplx* C, cplx* out, int64_t k, int mode, cudaStream_t s) {
+  if (k == 0) return CHASE_BSE_OK;
+  re_im_part_kernel<<<gs(k * k), 256, 0, s>>>(C, out, k, mode);
+  count_launch();
+  CB_LAUNCH();
+  return CHASE_BSE_OK;
+}
+__global__ void conj_copy_kernel(cplx* dst, int64_t ldd, const cplx* src, int64_t lds, int64_t rows, int64_t m) {
+  GRID_STRIDE(i, rows * m) {
+    const int64_t r = i % rows, c = i / rows;
+    dst[r + c * ldd] = cconj(src[r + c * lds]);
+  }
+}
+int conj_copy(cplx* dst, int64_t ldd, const cplx* src, int64_t lds, int64_t rows, int64_t m, cudaStream_t s) {
+  if (rows * m == 0) return CHASE_BSE_OK;
+  conj_copy_kernel<<<gs(rows * m), 256, 0, s>>>(dst, ldd, src, lds, rows, m);
   count_launch();
   CB_LAUNCH();
   return CHASE_BSE_OK;

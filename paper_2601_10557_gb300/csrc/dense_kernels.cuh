@@ -30,6 +30,13 @@ int scale_lower(cplx* W, int64_t n, int64_t k, double gamma, cudaStream_t s);
 int build_qr_input(cplx* X, const cplx* Yp, int64_t L, const cplx* Wf, int64_t kf, int64_t n,
                    cudaStream_t s);
 int gather_cols(cplx* dst, const cplx* src, const int* idx, int64_t rows, int64_t m, cudaStream_t s);
+// J-fixed basis (J = K conj) of span[S Y+, S Y-, W+, W-], top halves only (n x 2(L + kf)):
+// locked: top(Sy + J Sy), top(i (Sy - J Sy)); active: top(w + J w), top(i (w - J w)).
+int build_jfixed(cplx* Xt, const cplx* Yp, int64_t L, const cplx* W, int64_t kf, int64_t n, cudaStream_t s);
+// out = 2 Re(C) (mode 0) or 2 i Im(C) (mode 1), k x k
+int re_im_part(const cplx* C, cplx* out, int64_t k, int mode, cudaStream_t s);
+// dst = conj(src), rows x m with leading dimensions lds, ldd
+int conj_copy(cplx* dst, int64_t ldd, const cplx* src, int64_t lds, int64_t rows, int64_t m, cudaStream_t s);
 // dst[:, j] = src_j[:, j] with src_j = bufs[sel[j]]  (collect filter outputs)
 int collect_cols(cplx* dst, const cplx* b0, const cplx* b1, const cplx* b2, const int* sel,
                  int64_t rows, int64_t m, cudaStream_t s);

@@ -189,6 +189,109 @@ static int hop_launch(const HopArgs& a, cudaStream_t s) {
   return CHASE_BSE_OK;
 }
 
+// y = [A | B] [x; conj(x)] for k vectors x (n x k, ld n).  part != NULL: K split.
+template <int BM, int BNW, int TM, int TNW, int BK>
+__global__ void __launch_bounds__((BM / TM) * (BNW / TNW))
+hop_top_kernel(const cplx* __restrict__ A, const cplx* __restrict__ B, int64_t n, const cplx* __restrict__ X,
+               int64_t k, cplx* Y, cplx* part, int64_t kchunk) {
+  constexpr int TY = BM / TM;
+  constexpr int TX = BNW / TNW;
+  constexpr int NT = TX * TY;
+  __shared__ cplx Ps[BK][BM];
+  __shared__ cplx Ws[BK][BNW];
+  const int tid = threadIdx.x;
+  const int ty = tid % TY;
+  const int tx = tid / TY;
+  const int64_t n2 = 2 * n;
+  const int64_t row0 = (int64_t)blockIdx.x * BM;
+  const int64_t col0 = (int64_t)blockIdx.y * BNW;
+  const int64_t kbeg = part ? (int64_t)blockIdx.z * kchunk : 0;
+  const int64_t kend = part ? (kbeg + kchunk < n2 ? kbeg + kchunk : n2) : n2;
+  cplx acc[TM][TNW];
+#pragma unroll
+  for (int r = 0; r < TM; ++r)
+#pragma unroll
+    for (int c = 0; c < TNW; ++c) acc[r][c] = mk(0, 0);
+  for (int64_t kb = kbeg; kb < kend; kb += BK) {
+    for (int idx = tid; idx < BM * BK; idx += NT) {
+      const int r = idx / BK, cc = idx % BK;
+      const int64_t gi = row0 + r, gl = kb + cc;
+      cplx v = mk(0, 0);
+      if (gi < n && gl < kend) v = (gl < n) ? A[gi * n + gl] : B[gi * n + (gl - n)];
+      Ps[cc][r] = v;
+    }
+    for (int idx = tid; idx < BNW * BK; idx += NT) {
+      const int j = idx / BK, l = idx % BK;
+      const int64_t gj = col0 + j, gl = kb + l;
+      cplx v = mk(0, 0);
+      if (gj < k && gl < kend) v = (gl < n) ? X[gj * n + gl] : cconj(X[gj * n + (gl - n)]);
+      Ws[l][j] = v;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < BK; ++kk) {
+      cplx p[TM], w[TNW];
+#pragma unroll
+      for (int r = 0; r < TM; ++r) p[r] = Ps[kk][ty + TY * r];
+#pragma unroll
+      for (int c = 0; c < TNW; ++c) w[c] = Ws[kk][tx + TX * c];
+#pragma unroll
+      for (int r = 0; r < TM; ++r)
+#pragma unroll
+        for (int c = 0; c < TNW; ++c) cfma(acc[r][c], p[r], w[c]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < TM; ++r)
+#pragma unroll
+    for (int c = 0; c < TNW; ++c) {
+      const int64_t i = row0 + ty + TY * r, j = col0 + tx + TX * c;
+      if (i >= n || j >= k) continue;
+      if (part) part[(int64_t)blockIdx.z * n * k + j * n + i] = acc[r][c];
+      else Y[j * n + i] = acc[r][c];
+    }
+}
+
+__global__ void sum_parts_kernel(const cplx* part, int nsplit, int64_t total, cplx* Y) {
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    cplx v = mk(0, 0);
+    for (int z = 0; z < nsplit; ++z) v = cadd(v, part[(int64_t)z * total + idx]);
+    Y[idx] = v;
+  }
+}
+
+int hop_top_fp64(const cplx* A, const cplx* B, int64_t n, const cplx* X, int64_t k, cplx* Y, cudaStream_t s) {
+  if (k <= 0 || n <= 0) return CHASE_BSE_OK;
+  constexpr int BM = 64, BNW = 64, TM = 4, TNW = 4;
+  const int64_t tiles = (int64_t)cdiv(n, BM) * cdiv(k, BNW);
+  const int64_t n2 = 2 * n;
+  const int64_t nsplit = split_count(tiles, n2, 256);
+  dim3 grid(cdiv(n, BM), cdiv(k, BNW));
+  if (nsplit <= 1) {
+    hop_top_kernel<BM, BNW, TM, TNW, 16><<<grid, 256, 0, s>>>(A, B, n, X, k, Y, nullptr, 0);
+    count_launch();
+    CB_LAUNCH();
+    return CHASE_BSE_OK;
+  }
+  const int64_t kchunk = ((n2 + nsplit - 1) / nsplit + 15) / 16 * 16;
+  const int64_t ns = (n2 + kchunk - 1) / kchunk;
+  cplx* part = nullptr;
+  CB_CUDA(cudaMallocAsync(&part, sizeof(cplx) * ns * n * k, s));
+  grid.z = (unsigned)ns;
+  hop_top_kernel<BM, BNW, TM, TNW, 16><<<grid, 256, 0, s>>>(A, B, n, X, k, Y, part, kchunk);
+  count_launch();
+  const int64_t total = n * k;
+  sum_parts_kernel<<<(unsigned)((total + 255) / 256 < 8192 ? (total + 255) / 256 : 8192), 256, 0, s>>>(
+      part, (int)ns, total, Y);
+  count_launch();
+  cudaError_t e = cudaGetLastError();
+  cudaFreeAsync(part, s);
+  if (e != cudaSuccess) return CHASE_BSE_CUDA_ERROR;
+  return CHASE_BSE_OK;
+}
+
 int hop_fp64(const HopArgs& a, cudaStream_t s) {
   if (a.k <= 0 || a.n <= 0) return CHASE_BSE_OK;
   if (a.k <= 4) return hop_launch<64, 4, 1, 1>(a, s);

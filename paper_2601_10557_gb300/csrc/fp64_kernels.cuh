@@ -32,6 +32,10 @@ struct HopArgs {
 
 int hop_fp64(const HopArgs& a, cudaStream_t s);
 
+// Top half of H applied to J-fixed vectors q = [x; conj(x)] (J = K conj):
+// H q = [y; -conj(y)] with y = A x + B conj(x).  X and Y are n x k (ld n).
+int hop_top_fp64(const cplx* A, const cplx* B, int64_t n, const cplx* X, int64_t k, cplx* Y, cudaStream_t s);
+
 // ---- generic complex GEMM (column-major, BLAS semantics) --------------------
 // C = alpha op(A) op(B) + beta C, op in {'N', 'T', 'C'}; beta == 0 ignores C.
 int zgemm(char opA, char opB, int64_t M, int64_t N, int64_t K, cplx alpha, const cplx* A,

@@ -402,6 +402,125 @@ int rayleigh_ritz(const cplx* A, const cplx* B, int64_t n, const cplx* Q, int64_
   return CHASE_BSE_OK;
 }
 
+// ------------------------------------------------- J-fixed QR and Rayleigh-Ritz
+// The search space [S Y+, S Y-, W+, W-] is closed under J = K conj, so it has an
+// orthonormal basis of J-fixed vectors q = [x; conj(x)].  Inner products of
+// J-fixed vectors are real (q_i^* q_j = 2 Re(x_i^* x_j)), so CholeskyQR runs on
+// the top halves with real coefficients and keeps the basis J-fixed.  For such q,
+// H q = [y; -conj(y)] with y = A x + B conj(x) (half an H application),
+// Q^* S H Q = 2 Re(X^* Y) and Q^* S Q = 2 i Im(X^* X).  The Rayleigh-Ritz step is
+// invariant to the choice of basis of the search space, so the results are
+// those of Algorithm 2 on any orthonormal basis.
+static int qr_jfixed(const cplx* X, int64_t n, int64_t m, cplx* Q, bool* ok_out, cudaStream_t s) {
+  *ok_out = false;
+  Workspace ws(s);
+  cplx *C, *G, *Linv, *T, *Q1;
+  int* info_d;
+  double* diag_d;
+  CB_TRY(ws.alloc(&C, m * m));
+  CB_TRY(ws.alloc(&G, m * m));
+  CB_TRY(ws.alloc(&Linv, m * m));
+  CB_TRY(ws.alloc(&T, m * 32));
+  CB_TRY(ws.alloc(&Q1, n * m));
+  CB_TRY(ws.alloc(&info_d, 1));
+  CB_TRY(ws.alloc(&diag_d, m));
+  std::vector<double> dg(m);
+  const cplx* src = X;
+  for (int pass = 0; pass < 2; ++pass) {
+    cplx* dst = (pass == 0) ? Q1 : Q;
+    CB_TRY(zgemm('C', 'N', m, m, n, mk(1, 0), src, n, src, n, mk(0, 0), C, m, s));
+    CB_TRY(re_im_part(C, G, m, 0, s));  // Gram of the J-fixed vectors: 2 Re(X^* X)
+    int info = 0;
+    CB_TRY(cholesky(G, m, info_d, &info, s));
+    if (info != 0) return CHASE_BSE_OK;
+    if (pass == 0) {
+      CB_TRY(diag_real(G, m, diag_d, s));
+      CB_CUDA(cudaMemcpyAsync(dg.data(), diag_d, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
+      CB_CUDA(cudaStreamSynchronize(s));
+      const double mx = *std::max_element(dg.begin(), dg.end());
+      const double mn = *std::min_element(dg.begin(), dg.end());
+      if (!(mn > 0.0) || (mx / mn) * (mx / mn) > 1e12) return CHASE_BSE_OK;
+    }
+    CB_TRY(tri_inverse(G, m, Linv, T, s));
+    CB_TRY(zgemm('N', 'C', n, m, m, mk(1, 0), src, n, Linv, m, mk(0, 0), dst, n, s));
+    src = Q1;
+  }
+  *ok_out = true;
+  return CHASE_BSE_OK;
+}
+
+static int rayleigh_ritz_jfixed(const cplx* A, const cplx* B, int64_t n, const cplx* Qt, int64_t k, double* ritz_host,
+                                cplx* Wpos, cplx* R, double* res, cudaStream_t s) {
+  if (k <= 0 || (k % 2) != 0) return CHASE_BSE_BAD_ARG;
+  const int64_t n2 = 2 * n, h = k / 2;
+  Workspace ws(s);
+  cplx *Tt, *C, *M, *Linv, *M2, *Tmp, *G, *V, *Ypos, *Z, *rot, *scratch, *Qc, *Tc, *SHW;
+  double *theta, *red, *rz;
+  int *info_d, *idx_d;
+  CB_TRY(ws.alloc(&Tt, n * k));
+  CB_TRY(ws.alloc(&C, k * k));
+  CB_TRY(ws.alloc(&M, k * k));
+  CB_TRY(ws.alloc(&Linv, k * k));
+  CB_TRY(ws.alloc(&M2, k * k));
+  CB_TRY(ws.alloc(&Tmp, k * k));
+  CB_TRY(ws.alloc(&G, k * k));
+  CB_TRY(ws.alloc(&V, k * k));
+  CB_TRY(ws.alloc(&Ypos, k * h));
+  CB_TRY(ws.alloc(&Z, k * h));
+  CB_TRY(ws.alloc(&rot, 2 * k));
+  CB_TRY(ws.alloc(&scratch, k * 32));
+  CB_TRY(ws.alloc(&Qc, n * k));
+  CB_TRY(ws.alloc(&Tc, n * k));
+  CB_TRY(ws.alloc(&SHW, n2 * h));
+  CB_TRY(ws.alloc(&theta, k));
+  CB_TRY(ws.alloc(&red, 2));
+  CB_TRY(ws.alloc(&rz, h));
+  CB_TRY(ws.alloc(&info_d, 1));
+  CB_TRY(ws.alloc(&idx_d, h));
+  // lines 1-3: T = S H Q (top halves y = A x + B conj x), M = Q^* T = 2 Re(X^* Y)
+  CB_TRY(hop_top_fp64(A, B, n, Qt, k, Tt, s));
+  CB_TRY(zgemm('C', 'N', k, k, n, mk(1, 0), Qt, n, Tt, n, mk(0, 0), C, k, s));
+  CB_TRY(re_im_part(C, M, k, 0, s));
+  int info = 0;
+  CB_TRY(cholesky(M, k, info_d, &info, s));  // line 4
+  if (info != 0) return CHASE_BSE_NOT_DEFINITE;
+  CB_TRY(tri_inverse(M, k, Linv, scratch, s));
+  // line 5: Q^* S Q = 2 i Im(X^* X)
+  CB_TRY(zgemm('C', 'N', k, k, n, mk(1, 0), Qt, n, Qt, n, mk(0, 0), C, k, s));
+  CB_TRY(re_im_part(C, M2, k, 1, s));
+  // line 7: G = L^{-1} M2 L^{-*}
+  CB_TRY(zgemm('N', 'N', k, k, k, mk(1, 0), Linv, k, M2, k, mk(0, 0), Tmp, k, s));
+  CB_TRY(zgemm('N', 'C', k, k, k, mk(1, 0), Tmp, k, Linv, k, mk(0, 0), G, k, s));
+  CB_TRY(hermitize(G, k, s));
+  int sweeps = 0;
+  CB_TRY(jacobi_eigh(G, k, V, theta, rot, red, 40, &sweeps, s));  // line 8
+  std::vector<double> th(k);
+  CB_CUDA(cudaMemcpyAsync(th.data(), theta, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+  CB_CUDA(cudaStreamSynchronize(s));
+  std::vector<int> pos(k);
+  std::iota(pos.begin(), pos.end(), 0);
+  std::stable_sort(pos.begin(), pos.end(), [&](int x, int y) { return th[x] > th[y]; });
+  pos.resize(h);
+  if (!(th[pos[h - 1]] > 0.0)) return CHASE_BSE_QR_FAILED;
+  for (int64_t i = 0; i < h; ++i) ritz_host[i] = 1.0 / th[pos[i]];
+  CB_CUDA(cudaMemcpyAsync(idx_d, pos.data(), sizeof(int) * h, cudaMemcpyHostToDevice, s));
+  CB_CUDA(cudaMemcpyAsync(rz, ritz_host, sizeof(double) * h, cudaMemcpyHostToDevice, s));
+  CB_TRY(gather_cols(Ypos, V, idx_d, k, h, s));
+  // line 9 (z = L^{-*} y); W+ = Q Z+ = [X Z; conj(X) Z]; S H W+ = [Y Z; conj(Y) Z]
+  CB_TRY(zgemm('C', 'N', k, h, k, mk(1, 0), Linv, k, Ypos, k, mk(0, 0), Z, k, s));
+  CB_TRY(conj_copy(Qc, n, Qt, n, n, k, s));
+  CB_TRY(conj_copy(Tc, n, Tt, n, n, k, s));
+  CB_TRY(zgemm('N', 'N', n, h, k, mk(1, 0), Qt, n, Z, k, mk(0, 0), Wpos, n2, s));
+  CB_TRY(zgemm('N', 'N', n, h, k, mk(1, 0), Qc, n, Z, k, mk(0, 0), Wpos + n, n2, s));
+  CB_TRY(zgemm('N', 'N', n, h, k, mk(1, 0), Tt, n, Z, k, mk(0, 0), SHW, n2, s));
+  CB_TRY(zgemm('N', 'N', n, h, k, mk(1, 0), Tc, n, Z, k, mk(0, 0), SHW + n, n2, s));
+  CB_TRY(normalize_and_residual(Wpos, SHW, rz, n, h, R, s));
+  CB_TRY(col_norms(R, n2, h, res, s));
+  CB_CUDA(cudaStreamSynchronize(s));  // host vectors must outlive the copies
+  if (verbose()) fprintf(stderr, "[chase_bse] rr(J) k %ld jacobi %d sweeps\n", (long)k, sweeps);
+  return CHASE_BSE_OK;
+}
+
 int residuals(const cplx* A, const cplx* B, int64_t n, const cplx* W, const double* lambda, int64_t k, double* res,
               cudaStream_t s, cplx* Rout) {
   if (k == 0) return CHASE_BSE_OK;
@@ -562,22 +681,27 @@ int solve(const cplx* A, const cplx* B, int64_t n, int64_t nev, int64_t nex, int
     CB_TRY(filter(A, B, n, W, kf, degs.data(), prec.data(), mu1, mu_ne, muN, scheme,
                   corr ? ritz_keep.data() : nullptr, corr ? Rkeep : nullptr, s, &fs));
     st.ms_filter += clk.stop();
-    // lines 5-7: W- = K conj(W+), Q = [S Y+, S Y-, W+, W-] R^{-1}, drop the locked part
+    // lines 5-7: W- = K conj(W+), Q = [S Y+, S Y-, W+, W-] R^{-1}, drop the locked part;
+    // J-fixed basis (top halves) unless its CholeskyQR2 breaks down
     clk.start();
-    CB_TRY(build_qr_input(X, Ylock, locked, W, kf, n, s));
+    CB_TRY(build_jfixed(X, Ylock, locked, W, kf, n, s));
+    bool jok = false;
+    CB_TRY(qr_jfixed(X, n, 2 * nevex, Qf, &jok, s));
     int hh = 0;
-    CB_TRY(qr(X, n2, 2 * nevex, Qf, &hh, s));
-    st.householder += hh;
+    if (!jok) {
+      CB_TRY(build_qr_input(X, Ylock, locked, W, kf, n, s));
+      CB_TRY(qr(X, n2, 2 * nevex, Qf, &hh, s));
+      st.householder += hh;
+    }
     st.ms_qr += clk.stop();
-    const cplx* Q = Qf + 2 * locked * n2;
-    // lines 8-10: Rayleigh-Ritz, W+ = Q Z+
     clk.start();
     std::vector<double> ritz(kf);
     cplx* Rvec = Rall;
     Workspace rws(s);
     if (!Rvec) CB_TRY(rws.alloc(&Rvec, n2 * kf));
     // lines 8-11: Rayleigh-Ritz, W+ = Q Z+ and the residuals of the positive half
-    int rs = rayleigh_ritz(A, B, n, Q, 2 * kf, ritz.data(), Wpos, s, Rvec, res_d);
+    int rs = jok ? rayleigh_ritz_jfixed(A, B, n, Qf + 2 * locked * n, 2 * kf, ritz.data(), Wpos, Rvec, res_d, s)
+                 : rayleigh_ritz(A, B, n, Qf + 2 * locked * n2, 2 * kf, ritz.data(), Wpos, s, Rvec, res_d);
     st.ms_rr += clk.stop();
     if (rs != CHASE_BSE_OK) { status = rs; break; }
     clk.start();
