@@ -1,4 +1,6 @@
 // Small dense FP64 kernels (see dense_kernels.cuh).
+#include <mutex>
+
 #include "dense_kernels.cuh"
 #include "fp64_kernels.cuh"
 
@@ -258,6 +260,18 @@ __global__ void offdiag_norm_kernel(const cplx* G, int64_t k, double* red) {
   if (threadIdx.x == 0) { red[0] = off; red[1] = tot; }
 }
 
+// A non-blocking stream per device, created on first use, for the captured sweeps.
+static cudaStream_t jacobi_stream() {
+  static std::mutex mu;
+  static cudaStream_t streams[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!streams[dev] && cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking) != cudaSuccess)
+    return nullptr;
+  return streams[dev];
+}
+
 int jacobi_eigh(cplx* G, int64_t k, cplx* V, double* theta, cplx* rot, double* red, int max_sweeps,
                 int* sweeps_out, cudaStream_t s) {
   if (k % 2 != 0) return CHASE_BSE_BAD_ARG;
@@ -271,25 +285,50 @@ int jacobi_eigh(cplx* G, int64_t k, cplx* V, double* theta, cplx* rot, double* r
   CB_CUDA(cudaMallocAsync(&applied, sizeof(int), s));
   offdiag_norm_kernel<<<1, 1024, 0, s>>>(G, k, red);  // red[1] = ||G||_F^2 (invariant)
   count_launch();
+  // One sweep (k - 1 rounds, two launches each) is captured once into a CUDA graph
+  // on a library stream and replayed per sweep: the rounds are short, so launch
+  // overhead would otherwise dominate.  The library stream is ordered after and
+  // before the caller's stream with events.
+  cudaStream_t js = jacobi_stream();
+  if (!js) return CHASE_BSE_CUDA_ERROR;
+  cudaEvent_t ev;
+  CB_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  CB_CUDA(cudaEventRecord(ev, s));
+  CB_CUDA(cudaStreamWaitEvent(js, ev, 0));
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  CB_CUDA(cudaStreamBeginCapture(js, cudaStreamCaptureModeThreadLocal));
+  cudaMemsetAsync(applied, 0, sizeof(int), js);
+  for (int r = 0; r < k - 1; ++r) {
+    jacobi_rot_kernel<<<cdiv(half, 128), 128, 0, js>>>(G, k, r, rot, red, applied);
+    jacobi_apply_kernel<<<gapply, 256, 0, js>>>(G, V, k, r, rot);
+  }
+  CB_CUDA(cudaStreamEndCapture(js, &graph));
+  CB_CUDA(cudaGraphInstantiate(&exec, graph, 0));
   int happ = 1;
+  int status = CHASE_BSE_OK;
   for (; sweeps < max_sweeps; ++sweeps) {
-    CB_CUDA(cudaMemsetAsync(applied, 0, sizeof(int), s));
-    for (int r = 0; r < k - 1; ++r) {
-      jacobi_rot_kernel<<<cdiv(half, 128), 128, 0, s>>>(G, k, r, rot, red, applied);
-      count_launch();
-      jacobi_apply_kernel<<<gapply, 256, 0, s>>>(G, V, k, r, rot);
-      count_launch();
+    if (cudaGraphLaunch(exec, js) != cudaSuccess) { status = CHASE_BSE_CUDA_ERROR; break; }
+    for (int64_t i = 0; i < 2 * (k - 1); ++i) count_launch();
+    if (cudaMemcpyAsync(&happ, applied, sizeof(int), cudaMemcpyDeviceToHost, js) != cudaSuccess ||
+        cudaStreamSynchronize(js) != cudaSuccess) {
+      status = CHASE_BSE_CUDA_ERROR;
+      break;
     }
-    CB_LAUNCH();
-    CB_CUDA(cudaMemcpyAsync(&happ, applied, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CB_CUDA(cudaMemcpyAsync(hred, red, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
-    CB_CUDA(cudaStreamSynchronize(s));
-    if (happ == 0 || hred[1] != hred[1]) {
+    if (happ == 0) {
       ++sweeps;
       break;
     }
   }
+  cudaGraphExecDestroy(exec);
+  cudaGraphDestroy(graph);
+  CB_CUDA(cudaEventRecord(ev, js));
+  CB_CUDA(cudaStreamWaitEvent(s, ev, 0));
+  cudaEventDestroy(ev);
+  CB_CUDA(cudaMemcpyAsync(hred, red, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CB_CUDA(cudaStreamSynchronize(s));
   cudaFreeAsync(applied, s);
+  if (status != CHASE_BSE_OK) return status;
   if (sweeps_out) *sweeps_out = sweeps;
   CB_TRY(diag_real(G, k, theta, s));
   if (hred[1] != hred[1]) return CHASE_BSE_CUDA_ERROR;  // NaN in G
@@ -439,17 +478,18 @@ __global__ void build_jfixed_kernel(cplx* Xt, const cplx* Yp, int64_t L, const c
   GRID_STRIDE(idx, n * cols) {
     const int64_t r = idx % n, c = idx / n;
     cplx v;
+    // columns in pairs (v1, v2) per vector, so that pair j spans {u_j, J u_j}
     if (c < 2 * L) {
-      const cplx* y = Yp + (c % L) * n2;
+      const cplx* y = Yp + (c / 2) * n2;
       const cplx yt = y[r], ybc = cconj(y[n + r]);
       // S y = [yt; -yb], J S y = [-conj(yb); conj(yt)]
-      v = (c < L) ? csub(yt, ybc) : cmul(mk(0, 1), cadd(yt, ybc));
+      v = (c % 2 == 0) ? csub(yt, ybc) : cmul(mk(0, 1), cadd(yt, ybc));
     } else {
       const int64_t a = c - 2 * L;
-      const cplx* w = W + (a % kf) * n2;
+      const cplx* w = W + (a / 2) * n2;
       const cplx wt = w[r], wbc = cconj(w[n + r]);
       // J w = [conj(wb); conj(wt)]
-      v = (a < kf) ? cadd(wt, wbc) : cmul(mk(0, 1), csub(wt, wbc));
+      v = (a % 2 == 0) ? cadd(wt, wbc) : cmul(mk(0, 1), csub(wt, wbc));
     }
     Xt[c * n + r] = v;
   }
@@ -462,6 +502,52 @@ int build_jfixed(cplx* Xt, const cplx* Yp, int64_t L, const cplx* W, int64_t kf,
   CB_LAUNCH();
   return CHASE_BSE_OK;
 }
+// Pairwise unitary U = blockdiag(u), u = [[1, 1], [-i, i]] / sqrt(2): maps a J-fixed
+// pair (w + Jw, i (w - Jw)) to directions along (w, Jw).
+__global__ void pair_transform_kernel(const cplx* M, cplx* out, int64_t k) {
+  // out = U^* M U, one thread per 2x2 block
+  const int64_t h = k / 2;
+  GRID_STRIDE(idx, h * h) {
+    const int64_t a = idx % h, b = idx / h;
+    const cplx m00 = M[2 * a + 2 * b * k], m10 = M[2 * a + 1 + 2 * b * k];
+    const cplx m01 = M[2 * a + (2 * b + 1) * k], m11 = M[2 * a + 1 + (2 * b + 1) * k];
+    // M U: columns (m_.0 - i m_.1)/sqrt2, (m_.0 + i m_.1)/sqrt2
+    const double r = 0.70710678118654752440;
+    const cplx i1 = mk(0, 1);
+    const cplx p00 = cscale(csub(m00, cmul(i1, m01)), r), p01 = cscale(cadd(m00, cmul(i1, m01)), r);
+    const cplx p10 = cscale(csub(m10, cmul(i1, m11)), r), p11 = cscale(cadd(m10, cmul(i1, m11)), r);
+    // U^* (.): rows (p_0. + i p_1.)/sqrt2, (p_0. - i p_1.)/sqrt2
+    out[2 * a + 2 * b * k] = cscale(cadd(p00, cmul(i1, p10)), r);
+    out[2 * a + (2 * b + 1) * k] = cscale(cadd(p01, cmul(i1, p11)), r);
+    out[2 * a + 1 + 2 * b * k] = cscale(csub(p00, cmul(i1, p10)), r);
+    out[2 * a + 1 + (2 * b + 1) * k] = cscale(csub(p01, cmul(i1, p11)), r);
+  }
+}
+int pair_transform(const cplx* M, cplx* out, int64_t k, cudaStream_t s) {
+  if (k == 0) return CHASE_BSE_OK;
+  pair_transform_kernel<<<gs(k * k / 4), 256, 0, s>>>(M, out, k);
+  count_launch();
+  CB_LAUNCH();
+  return CHASE_BSE_OK;
+}
+// Z = U Z' (k x h): rows 2a, 2a+1 of Z from rows of Z'
+__global__ void pair_apply_kernel(const cplx* Zp, cplx* Z, int64_t k, int64_t h) {
+  GRID_STRIDE(idx, (k / 2) * h) {
+    const int64_t a = idx % (k / 2), j = idx / (k / 2);
+    const cplx z0 = Zp[2 * a + j * k], z1 = Zp[2 * a + 1 + j * k];
+    const double r = 0.70710678118654752440;
+    Z[2 * a + j * k] = cscale(cadd(z0, z1), r);
+    Z[2 * a + 1 + j * k] = cscale(cmul(mk(0, 1), csub(z1, z0)), r);
+  }
+}
+int pair_apply(const cplx* Zp, cplx* Z, int64_t k, int64_t h, cudaStream_t s) {
+  if (k * h == 0) return CHASE_BSE_OK;
+  pair_apply_kernel<<<gs(k * h / 2), 256, 0, s>>>(Zp, Z, k, h);
+  count_launch();
+  CB_LAUNCH();
+  return CHASE_BSE_OK;
+}
+
 __global__ void re_im_part_kernel(const cplx* C, cplx* out, int64_t k, int mode) {
   GRID_STRIDE(i, k * k) { out[i] = (mode == 0) ? mk(2.0 * C[i].x, 0.0) : mk(0.0, 2.0 * C[i].y); }
 }

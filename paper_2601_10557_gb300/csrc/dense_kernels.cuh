@@ -30,9 +30,13 @@ int scale_lower(cplx* W, int64_t n, int64_t k, double gamma, cudaStream_t s);
 int build_qr_input(cplx* X, const cplx* Yp, int64_t L, const cplx* Wf, int64_t kf, int64_t n,
                    cudaStream_t s);
 int gather_cols(cplx* dst, const cplx* src, const int* idx, int64_t rows, int64_t m, cudaStream_t s);
-// J-fixed basis (J = K conj) of span[S Y+, S Y-, W+, W-], top halves only (n x 2(L + kf)):
-// locked: top(Sy + J Sy), top(i (Sy - J Sy)); active: top(w + J w), top(i (w - J w)).
+// J-fixed basis (J = K conj) of span[S Y+, S Y-, W+, W-], top halves only (n x 2(L + kf)),
+// in pairs per vector: locked top(Sy + J Sy), top(i (Sy - J Sy)); active top(w + J w),
+// top(i (w - J w)).
 int build_jfixed(cplx* Xt, const cplx* Yp, int64_t L, const cplx* W, int64_t kf, int64_t n, cudaStream_t s);
+// out = U^* M U and Z = U Z' for U = blockdiag([[1, 1], [-i, i]] / sqrt 2) (k even)
+int pair_transform(const cplx* M, cplx* out, int64_t k, cudaStream_t s);
+int pair_apply(const cplx* Zp, cplx* Z, int64_t k, int64_t h, cudaStream_t s);
 // out = 2 Re(C) (mode 0) or 2 i Im(C) (mode 1), k x k
 int re_im_part(const cplx* C, cplx* out, int64_t k, int mode, cudaStream_t s);
 // dst = conj(src), rows x m with leading dimensions lds, ldd

@@ -402,6 +402,33 @@ int rayleigh_ritz(const cplx* A, const cplx* B, int64_t n, const cplx* Q, int64_
   return CHASE_BSE_OK;
 }
 
+// Stage timing printed in verbose mode (CHASE_BSE_VERBOSE=1).
+struct StageTimer {
+  cudaStream_t s;
+  bool on;
+  std::chrono::steady_clock::time_point t;
+  char buf[512];
+  int len = 0;
+  StageTimer(cudaStream_t st, const char* name) : s(st), on(verbose()) {
+    if (on) {
+      cudaStreamSynchronize(s);
+      t = std::chrono::steady_clock::now();
+      len = snprintf(buf, sizeof(buf), "[chase_bse] %s:", name);
+    }
+  }
+  void mark(const char* what) {
+    if (!on) return;
+    cudaStreamSynchronize(s);
+    const auto now = std::chrono::steady_clock::now();
+    len += snprintf(buf + len, sizeof(buf) - len, " %s %.1f", what,
+                    std::chrono::duration<double, std::milli>(now - t).count());
+    t = now;
+  }
+  ~StageTimer() {
+    if (on) fprintf(stderr, "%s ms\n", buf);
+  }
+};
+
 // ------------------------------------------------- J-fixed QR and Rayleigh-Ritz
 // The search space [S Y+, S Y-, W+, W-] is closed under J = K conj, so it has an
 // orthonormal basis of J-fixed vectors q = [x; conj(x)].  Inner products of
@@ -426,12 +453,15 @@ static int qr_jfixed(const cplx* X, int64_t n, int64_t m, cplx* Q, bool* ok_out,
   CB_TRY(ws.alloc(&diag_d, m));
   std::vector<double> dg(m);
   const cplx* src = X;
+  StageTimer tm(s, "qr(J)");
   for (int pass = 0; pass < 2; ++pass) {
     cplx* dst = (pass == 0) ? Q1 : Q;
     CB_TRY(zgemm('C', 'N', m, m, n, mk(1, 0), src, n, src, n, mk(0, 0), C, m, s));
     CB_TRY(re_im_part(C, G, m, 0, s));  // Gram of the J-fixed vectors: 2 Re(X^* X)
+    tm.mark("gram");
     int info = 0;
     CB_TRY(cholesky(G, m, info_d, &info, s));
+    tm.mark("chol");
     if (info != 0) return CHASE_BSE_OK;
     if (pass == 0) {
       CB_TRY(diag_real(G, m, diag_d, s));
@@ -442,7 +472,9 @@ static int qr_jfixed(const cplx* X, int64_t n, int64_t m, cplx* Q, bool* ok_out,
       if (!(mn > 0.0) || (mx / mn) * (mx / mn) > 1e12) return CHASE_BSE_OK;
     }
     CB_TRY(tri_inverse(G, m, Linv, T, s));
+    tm.mark("trinv");
     CB_TRY(zgemm('N', 'C', n, m, m, mk(1, 0), src, n, Linv, m, mk(0, 0), dst, n, s));
+    tm.mark("apply");
     src = Q1;
   }
   *ok_out = true;
@@ -477,23 +509,32 @@ static int rayleigh_ritz_jfixed(const cplx* A, const cplx* B, int64_t n, const c
   CB_TRY(ws.alloc(&rz, h));
   CB_TRY(ws.alloc(&info_d, 1));
   CB_TRY(ws.alloc(&idx_d, h));
+  StageTimer tm(s, "rr(J)");
   // lines 1-3: T = S H Q (top halves y = A x + B conj x), M = Q^* T = 2 Re(X^* Y)
   CB_TRY(hop_top_fp64(A, B, n, Qt, k, Tt, s));
+  tm.mark("HQ");
+  // The J-fixed columns come in pairs spanning {u, J u}; the small problem is set up in
+  // the basis Q U (U = pairwise [[1, 1], [-i, i]] / sqrt 2), whose pairs point along
+  // (u, J u): G then starts close to diagonal, as for the general basis.
   CB_TRY(zgemm('C', 'N', k, k, n, mk(1, 0), Qt, n, Tt, n, mk(0, 0), C, k, s));
-  CB_TRY(re_im_part(C, M, k, 0, s));
+  CB_TRY(re_im_part(C, Tmp, k, 0, s));
+  CB_TRY(pair_transform(Tmp, M, k, s));
   int info = 0;
   CB_TRY(cholesky(M, k, info_d, &info, s));  // line 4
   if (info != 0) return CHASE_BSE_NOT_DEFINITE;
   CB_TRY(tri_inverse(M, k, Linv, scratch, s));
   // line 5: Q^* S Q = 2 i Im(X^* X)
   CB_TRY(zgemm('C', 'N', k, k, n, mk(1, 0), Qt, n, Qt, n, mk(0, 0), C, k, s));
-  CB_TRY(re_im_part(C, M2, k, 1, s));
+  CB_TRY(re_im_part(C, Tmp, k, 1, s));
+  CB_TRY(pair_transform(Tmp, M2, k, s));
   // line 7: G = L^{-1} M2 L^{-*}
   CB_TRY(zgemm('N', 'N', k, k, k, mk(1, 0), Linv, k, M2, k, mk(0, 0), Tmp, k, s));
   CB_TRY(zgemm('N', 'C', k, k, k, mk(1, 0), Tmp, k, Linv, k, mk(0, 0), G, k, s));
   CB_TRY(hermitize(G, k, s));
+  tm.mark("small");
   int sweeps = 0;
   CB_TRY(jacobi_eigh(G, k, V, theta, rot, red, 40, &sweeps, s));  // line 8
+  tm.mark("jacobi");
   std::vector<double> th(k);
   CB_CUDA(cudaMemcpyAsync(th.data(), theta, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
   CB_CUDA(cudaStreamSynchronize(s));
@@ -506,8 +547,10 @@ static int rayleigh_ritz_jfixed(const cplx* A, const cplx* B, int64_t n, const c
   CB_CUDA(cudaMemcpyAsync(idx_d, pos.data(), sizeof(int) * h, cudaMemcpyHostToDevice, s));
   CB_CUDA(cudaMemcpyAsync(rz, ritz_host, sizeof(double) * h, cudaMemcpyHostToDevice, s));
   CB_TRY(gather_cols(Ypos, V, idx_d, k, h, s));
-  // line 9 (z = L^{-*} y); W+ = Q Z+ = [X Z; conj(X) Z]; S H W+ = [Y Z; conj(Y) Z]
-  CB_TRY(zgemm('C', 'N', k, h, k, mk(1, 0), Linv, k, Ypos, k, mk(0, 0), Z, k, s));
+  // line 9 (z = L^{-*} y), back to the J-fixed basis (Z = U Z');
+  // W+ = Q Z+ = [X Z; conj(X) Z]; S H W+ = [Y Z; conj(Y) Z]
+  CB_TRY(zgemm('C', 'N', k, h, k, mk(1, 0), Linv, k, Ypos, k, mk(0, 0), Tmp, k, s));
+  CB_TRY(pair_apply(Tmp, Z, k, h, s));
   CB_TRY(conj_copy(Qc, n, Qt, n, n, k, s));
   CB_TRY(conj_copy(Tc, n, Tt, n, n, k, s));
   CB_TRY(zgemm('N', 'N', n, h, k, mk(1, 0), Qt, n, Z, k, mk(0, 0), Wpos, n2, s));
@@ -517,6 +560,7 @@ static int rayleigh_ritz_jfixed(const cplx* A, const cplx* B, int64_t n, const c
   CB_TRY(normalize_and_residual(Wpos, SHW, rz, n, h, R, s));
   CB_TRY(col_norms(R, n2, h, res, s));
   CB_CUDA(cudaStreamSynchronize(s));  // host vectors must outlive the copies
+  tm.mark("back");
   if (verbose()) fprintf(stderr, "[chase_bse] rr(J) k %ld jacobi %d sweeps\n", (long)k, sweeps);
   return CHASE_BSE_OK;
 }
