@@ -260,6 +260,121 @@ __global__ void offdiag_norm_kernel(const cplx* G, int64_t k, double* red) {
   if (threadIdx.x == 0) { red[0] = off; red[1] = tot; }
 }
 
+// ---- one Jacobi sweep as a single cooperative kernel ----------------------
+// All CTAs are co-resident (cooperative launch), and each round of the sweep is
+// two phases separated by a grid barrier: the k/2 rotations of the round, then
+// their application to G and V.  The barrier is a counter plus a generation word
+// in global memory; every wait is bounded (2 s of %globaltimer), after which the
+// kernel records an error, and all CTAs leave at their next barrier.
+struct GridSync {
+  unsigned count;
+  unsigned gen;
+};
+__device__ __forceinline__ unsigned long long gtimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ bool grid_barrier(GridSync* gsync, int* err) {
+  __shared__ int ok_sh;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok_sh = 1;
+    volatile unsigned* gen = &gsync->gen;
+    const unsigned my_gen = *gen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(&gsync->count, 1u);
+    if (arrived == gridDim.x - 1) {
+      atomicExch(&gsync->count, 0u);
+      __threadfence();
+      atomicAdd(&gsync->gen, 1u);
+    } else {
+      const unsigned long long t0 = gtimer_ns();
+      while (*gen == my_gen) {
+        if (*(volatile int*)err) { ok_sh = 0; break; }
+        if (gtimer_ns() - t0 > 2000000000ull) {
+          atomicExch(err, 1);
+          ok_sh = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    if (*(volatile int*)err) ok_sh = 0;
+  }
+  __syncthreads();
+  return ok_sh != 0;
+}
+
+__global__ void jacobi_sweep_kernel(cplx* G, cplx* V, int64_t k, cplx* rot, const double* red, int* applied,
+                                    GridSync* gsync, int* err) {
+  const int64_t half = k / 2;
+  const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const double normG = sqrt(red[1]);
+  const int64_t nG = half * half, nV = k * half;
+  for (int r = 0; r < k - 1; ++r) {
+    for (int64_t slot = tid; slot < half; slot += nthreads) {
+      int64_t p, q;
+      jpair(slot, r, k, p, q);
+      const double app = __ldcg(G + p + p * k).x, aqq = __ldcg(G + q + q * k).x;
+      const cplx apq = __ldcg(G + p + q * k);
+      const double rr = hypot(apq.x, apq.y);
+      cplx J00 = mk(1, 0), J01 = mk(0, 0), J10 = mk(0, 0), J11 = mk(1, 0);
+      if (rr > 2e-16 * sqrt(fabs(app * aqq)) && rr > 1e-16 * normG && rr > 1e-300) {
+        atomicAdd(applied, 1);
+        const cplx ec = mk(apq.x / rr, -apq.y / rr);
+        const double tau = (aqq - app) / (2.0 * rr);
+        const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + hypot(1.0, tau));
+        const double c = 1.0 / hypot(1.0, t), sn = t * c;
+        J00 = mk(c, 0);
+        J01 = mk(sn, 0);
+        J10 = cscale(ec, -sn);
+        J11 = cscale(ec, c);
+      }
+      rot[4 * slot + 0] = J00;
+      rot[4 * slot + 1] = J01;
+      rot[4 * slot + 2] = J10;
+      rot[4 * slot + 3] = J11;
+    }
+    if (!grid_barrier(gsync, err)) return;
+    for (int64_t item = tid; item < nG + nV; item += nthreads) {
+      if (item < nG) {
+        const int64_t a = item % half, b = item / half;
+        int64_t pa, qa, pb, qb;
+        jpair(a, r, k, pa, qa);
+        jpair(b, r, k, pb, qb);
+        const cplx A00 = __ldcg(rot + 4 * a), A01 = __ldcg(rot + 4 * a + 1), A10 = __ldcg(rot + 4 * a + 2),
+                   A11 = __ldcg(rot + 4 * a + 3);
+        const cplx B00 = __ldcg(rot + 4 * b), B01 = __ldcg(rot + 4 * b + 1), B10 = __ldcg(rot + 4 * b + 2),
+                   B11 = __ldcg(rot + 4 * b + 3);
+        const cplx x00 = __ldcg(G + pa + pb * k), x01 = __ldcg(G + pa + qb * k), x10 = __ldcg(G + qa + pb * k),
+                   x11 = __ldcg(G + qa + qb * k);
+        const cplx y00 = cadd(cmul(cconj(A00), x00), cmul(cconj(A10), x10));
+        const cplx y01 = cadd(cmul(cconj(A00), x01), cmul(cconj(A10), x11));
+        const cplx y10 = cadd(cmul(cconj(A01), x00), cmul(cconj(A11), x10));
+        const cplx y11 = cadd(cmul(cconj(A01), x01), cmul(cconj(A11), x11));
+        G[pa + pb * k] = cadd(cmul(y00, B00), cmul(y01, B10));
+        G[pa + qb * k] = cadd(cmul(y00, B01), cmul(y01, B11));
+        G[qa + pb * k] = cadd(cmul(y10, B00), cmul(y11, B10));
+        G[qa + qb * k] = cadd(cmul(y10, B01), cmul(y11, B11));
+      } else {
+        const int64_t it = item - nG;
+        const int64_t i = it % k, b = it / k;
+        int64_t pb, qb;
+        jpair(b, r, k, pb, qb);
+        const cplx B00 = __ldcg(rot + 4 * b), B01 = __ldcg(rot + 4 * b + 1), B10 = __ldcg(rot + 4 * b + 2),
+                   B11 = __ldcg(rot + 4 * b + 3);
+        const cplx v0 = __ldcg(V + i + pb * k), v1 = __ldcg(V + i + qb * k);
+        V[i + pb * k] = cadd(cmul(v0, B00), cmul(v1, B10));
+        V[i + qb * k] = cadd(cmul(v0, B01), cmul(v1, B11));
+      }
+    }
+    if (!grid_barrier(gsync, err)) return;
+  }
+}
+
 // A non-blocking stream per device, created on first use, for the captured sweeps.
 static cudaStream_t jacobi_stream() {
   static std::mutex mu;
@@ -285,7 +400,60 @@ int jacobi_eigh(cplx* G, int64_t k, cplx* V, double* theta, cplx* rot, double* r
   CB_CUDA(cudaMallocAsync(&applied, sizeof(int), s));
   offdiag_norm_kernel<<<1, 1024, 0, s>>>(G, k, red);  // red[1] = ||G||_F^2 (invariant)
   count_launch();
-  // One sweep (k - 1 rounds, two launches each) is captured once into a CUDA graph
+  // Preferred: one cooperative launch per sweep.
+  {
+    int dev = 0, sms = 0, per_sm = 0, coop = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_sweep_kernel, 512, 0);
+    const int64_t want = (items + 511) / 512;
+    const int64_t cap = (int64_t)sms * (per_sm < 1 ? per_sm : 1);  // one CTA per SM: fewer barrier arrivals
+    const unsigned grid = (unsigned)(want < cap ? want : cap);
+    if (coop && grid >= 1 && per_sm >= 1) {
+      GridSync* gsync = nullptr;
+      int* err = nullptr;
+      CB_CUDA(cudaMallocAsync(&gsync, sizeof(GridSync), s));
+      CB_CUDA(cudaMallocAsync(&err, sizeof(int), s));
+      CB_CUDA(cudaMemsetAsync(gsync, 0, sizeof(GridSync), s));
+      CB_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+      int happ = 1, herr = 0, status = CHASE_BSE_OK;
+      int64_t kk = k;
+      void* args[] = {&G, &V, &kk, &rot, &red, &applied, &gsync, &err};
+      for (; sweeps < max_sweeps; ++sweeps) {
+        CB_CUDA(cudaMemsetAsync(applied, 0, sizeof(int), s));
+        if (cudaLaunchCooperativeKernel((const void*)jacobi_sweep_kernel, dim3(grid), dim3(512), args, 0, s) !=
+            cudaSuccess) {
+          cudaGetLastError();
+          status = CHASE_BSE_CUDA_ERROR;
+          break;
+        }
+        count_launch();
+        CB_CUDA(cudaMemcpyAsync(&happ, applied, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CB_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CB_CUDA(cudaStreamSynchronize(s));
+        if (herr) {
+          status = CHASE_BSE_DEVICE_TIMEOUT;
+          break;
+        }
+        if (happ == 0) {
+          ++sweeps;
+          break;
+        }
+      }
+      cudaFreeAsync(gsync, s);
+      cudaFreeAsync(err, s);
+      cudaFreeAsync(applied, s);
+      if (status != CHASE_BSE_OK) return status;
+      if (sweeps_out) *sweeps_out = sweeps;
+      CB_TRY(diag_real(G, k, theta, s));
+      CB_CUDA(cudaMemcpyAsync(hred, red, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CB_CUDA(cudaStreamSynchronize(s));
+      if (hred[1] != hred[1]) return CHASE_BSE_CUDA_ERROR;  // NaN in G
+      return CHASE_BSE_OK;
+    }
+  }
+  // Otherwise one sweep (k - 1 rounds, two launches each) is captured once into a CUDA graph
   // on a library stream and replayed per sweep: the rounds are short, so launch
   // overhead would otherwise dominate.  The library stream is ordered after and
   // before the caller's stream with events.
