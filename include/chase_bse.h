@@ -73,7 +73,9 @@ typedef struct chase_bse_opts {
   int32_t deg_max;         /* (default: deg)                                          */
   int32_t lanczos_steps;   /* even number of Lanczos steps (default 26, Section 4.1)  */
   int32_t lanczos_vecs;    /* start vectors of the bound estimate (default 4, <= 64)  */
-  int32_t reserved0;
+  int32_t fp64_products;   /* mixed mode: 0 = the FP64 products of QR and Rayleigh-Ritz
+                              on the tensor cores, FP64-accurate (see
+                              chase_bse_dgemm_sliced; default), 1 = on the FP64 pipe */
   double gamma;            /* lower-half scale of the start block (default 1e-3,
                               Section 4.6)                                            */
   double switch_tol;       /* mixed mode: a column below this residual whose residual
@@ -183,6 +185,23 @@ int chase_bse_residuals_noalloc(const void* A, const void* B, int64_t n, const v
  *   gA, gB device, n x n complex128, written ROW-MAJOR like A and B. */
 int chase_bse_grad(const void* V, const double* w, int64_t n, int64_t nev, void* gA,
                    void* gB, void* stream);
+
+/* FP64-accurate real GEMM on the BF16 tensor cores, the building block of the
+ * mixed solve's QR and Rayleigh-Ritz products (the paper has no counterpart: it
+ * serves the GB300, whose FP64 pipe runs at 1/64 of its FP32 rate).
+ *   C[r + c * ldc] = alpha * sum_k A[r * lda + k] * B[c * ldb + k]
+ * for r < M, c < N: A is M x K and B is N x K, both row-major (K contiguous), C is
+ * column-major.  A, B, C device pointers (FP64); K even; lda, ldb >= K; ldc >= M.
+ * Each row of A and of B is scaled by a power of two and cut into 7 signed 8-bit
+ * digits; digit products of equal weight are summed exactly in the tensor cores'
+ * FP32 accumulators over 128-long K chunks and folded into 64-bit integers, so
+ * that the error is about 2^-56 K max|A_r.| max|B_c.| (FP64 class) plus the
+ * final rounding.  M = 0 or N = 0 is a no-op.  Returns UNSUPPORTED on a device
+ * other than compute capability 10.3, DEVICE_TIMEOUT if a bounded device-side
+ * wait gave up.  Synchronises `stream`. */
+int chase_bse_dgemm_sliced(const double* A, int64_t lda, const double* B, int64_t ldb,
+                           int64_t M, int64_t N, int64_t K, double alpha, double* C,
+                           int64_t ldc, void* stream);
 
 /* Static description of a status code. */
 const char* chase_bse_strerror(int status);

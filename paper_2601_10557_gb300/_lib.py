@@ -38,7 +38,7 @@ class Opts(ctypes.Structure):
         ("deg_max", ctypes.c_int32),
         ("lanczos_steps", ctypes.c_int32),
         ("lanczos_vecs", ctypes.c_int32),
-        ("reserved0", ctypes.c_int32),
+        ("fp64_products", ctypes.c_int32),
         ("gamma", ctypes.c_double),
         ("switch_tol", ctypes.c_double),
         ("seed", ctypes.c_uint64),
@@ -80,7 +80,7 @@ _lib: Optional[ctypes.CDLL] = None
 
 EXPORTS = ["chase_bse_solve", "chase_bse_filter", "chase_bse_rr", "chase_bse_residuals", "chase_bse_grad",
            "chase_bse_strerror", "chase_bse_version", "chase_bse_has_mixed", "chase_bse_launch_count",
-           "chase_bse_residuals_noalloc"]
+           "chase_bse_residuals_noalloc", "chase_bse_dgemm_sliced"]
 
 # 2n * k limit of chase_bse_residuals_noalloc (its fixed device scratch, complex128 entries)
 NOALLOC_MAX_ENTRIES = 1 << 19
@@ -103,11 +103,13 @@ def lib() -> ctypes.CDLL:
     L.chase_bse_residuals.argtypes = [vp, vp, i64, vp, vp, i64, vp, vp]
     L.chase_bse_residuals_noalloc.argtypes = [vp, vp, i64, vp, vp, i64, vp, vp]
     L.chase_bse_grad.argtypes = [vp, vp, i64, i64, vp, vp, vp]
+    L.chase_bse_dgemm_sliced.argtypes = [vp, i64, vp, i64, i64, i64, i64, dbl, vp, i64, vp]
     L.chase_bse_strerror.argtypes = [ctypes.c_int]
     L.chase_bse_strerror.restype = ctypes.c_char_p
     L.chase_bse_launch_count.restype = ctypes.c_int64
     for name in ["chase_bse_solve", "chase_bse_filter", "chase_bse_rr", "chase_bse_residuals", "chase_bse_grad",
-                 "chase_bse_version", "chase_bse_has_mixed", "chase_bse_residuals_noalloc"]:
+                 "chase_bse_version", "chase_bse_has_mixed", "chase_bse_residuals_noalloc",
+                 "chase_bse_dgemm_sliced"]:
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -164,8 +166,13 @@ def solve(A: torch.Tensor, B: torch.Tensor, nev: int, nex: int, deg: int = 20, t
           precision: str = "fp64", W0: Optional[torch.Tensor] = None, V0: Optional[torch.Tensor] = None,
           maxiter: int = 25, deg_min: Optional[int] = None, deg_max: Optional[int] = None,
           lanczos_steps: int = 26, lanczos_vecs: int = 4, gamma: float = 1e-3, switch_tol: float = 1e-8,
-          seed: int = 0, stream=None, allow_partial: bool = False):
-    """chase_bse_solve: returns (evals (nev,) float64, evecs (nev, 2n) complex128, stats dict)."""
+          seed: int = 0, stream=None, allow_partial: bool = False, fp64_products: str = "tensor"):
+    """chase_bse_solve: returns (evals (nev,) float64, evecs (nev, 2n) complex128, stats dict).
+
+    fp64_products ("tensor" or "fp64"): in mixed precision, where the FP64-accurate
+    products of QR and Rayleigh-Ritz run (sliced tensor-core GEMM or FP64 pipe)."""
+    if fp64_products not in ("tensor", "fp64"):
+        raise ValueError("fp64_products must be 'tensor' or 'fp64'")
     A = _mat(A, "A")
     n = A.shape[0]
     B = _mat(B, "B", n)
@@ -180,7 +187,8 @@ def solve(A: torch.Tensor, B: torch.Tensor, nev: int, nex: int, deg: int = 20, t
     o = Opts(size=ctypes.sizeof(Opts), precision=_PREC[precision], maxiter=maxiter,
              deg_min=deg if deg_min is None else deg_min, deg_max=deg if deg_max is None else deg_max,
              lanczos_steps=lanczos_steps, lanczos_vecs=lanczos_vecs, gamma=gamma, switch_tol=switch_tol,
-             seed=seed, W0=_ptr(W0), V0=_ptr(V0), stream=ctypes.c_void_p(_stream(stream)))
+             seed=seed, W0=_ptr(W0), V0=_ptr(V0), stream=ctypes.c_void_p(_stream(stream)),
+             fp64_products=0 if fp64_products == "tensor" else 1)
     evals = torch.zeros(nev, dtype=torch.float64, device=A.device)
     evecs = torch.zeros((nev, 2 * n), dtype=torch.complex128, device=A.device)
     st = Stats(size=ctypes.sizeof(Stats))
@@ -255,6 +263,22 @@ def residuals_noalloc(A: torch.Tensor, B: torch.Tensor, W: torch.Tensor, lam: to
     _check(lib().chase_bse_residuals_noalloc(_ptr(A), _ptr(B), n, _ptr(W), _ptr(lam), k, _ptr(out),
                                              ctypes.c_void_p(_stream(stream))), "chase_bse_residuals_noalloc")
     return out
+
+
+def dgemm_sliced(A: torch.Tensor, B: torch.Tensor, alpha: float = 1.0, stream=None) -> torch.Tensor:
+    """chase_bse_dgemm_sliced: alpha * A @ B.T for float64 CUDA matrices A (M, K), B (N, K)."""
+    for t, nm in ((A, "A"), (B, "B")):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.dim() == 2
+                and t.is_contiguous()):
+            raise ValueError(f"{nm} must be a contiguous CUDA float64 matrix")
+    M, K = A.shape
+    N = B.shape[0]
+    if B.shape[1] != K:
+        raise ValueError("A and B must have the same number of columns")
+    C = torch.empty((N, M), dtype=torch.float64, device=A.device)  # column-major M x N
+    _check(lib().chase_bse_dgemm_sliced(_ptr(A), K, _ptr(B), K, M, N, K, float(alpha), _ptr(C), M,
+                                        ctypes.c_void_p(_stream(stream))), "chase_bse_dgemm_sliced")
+    return C.T
 
 
 def grad(V: torch.Tensor, w: torch.Tensor, stream=None):

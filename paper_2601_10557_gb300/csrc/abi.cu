@@ -3,6 +3,7 @@
 #include <vector>
 
 #include "solver.cuh"
+#include "tc_dgemm.cuh"
 
 using cb::cplx;
 
@@ -78,6 +79,25 @@ int chase_bse_residuals(const void* A, const void* B, int64_t n, const void* W, 
 int chase_bse_grad(const void* V, const double* w, int64_t n, int64_t nev, void* gA, void* gB, void* stream) {
   if (!V || !w || !gA || !gB || n < 1 || nev < 1) return CHASE_BSE_BAD_ARG;
   CB_GUARD(return cb::gradient((const cplx*)V, w, n, nev, (cplx*)gA, (cplx*)gB, (cudaStream_t)stream);)
+}
+
+int chase_bse_dgemm_sliced(const double* A, int64_t lda, const double* B, int64_t ldb, int64_t M, int64_t N,
+                           int64_t K, double alpha, double* C, int64_t ldc, void* stream) {
+  if (M == 0 || N == 0) return CHASE_BSE_OK;
+  if (!A || !B || !C || M < 0 || N < 0 || K < 2 || (K % 2) != 0 || lda < K || ldb < K || ldc < M)
+    return CHASE_BSE_BAD_ARG;
+  if (!cb::mixed_available()) return CHASE_BSE_UNSUPPORTED;
+  CB_GUARD({
+    cudaStream_t s = (cudaStream_t)stream;
+    cb::Workspace ws(s);
+    cb::SlicedOp a;
+    cb::SlicedOp b;
+    CB_TRY(cb::sliced_alloc(ws, a, M, K, s));
+    CB_TRY(cb::sliced_alloc(ws, b, N, K, s));
+    CB_TRY(cb::slice_rows(A, lda, 0, a, s));
+    CB_TRY(cb::slice_rows(B, ldb, 0, b, s));
+    return cb::sliced_gemm(a, b, alpha, C, 1, ldc, false, s);
+  })
 }
 
 }  // extern "C"

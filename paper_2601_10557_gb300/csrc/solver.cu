@@ -11,6 +11,7 @@
 #include "dense_kernels.cuh"
 #include "fp64_kernels.cuh"
 #include "solver.cuh"
+#include "tc_dgemm.cuh"
 
 namespace cb {
 
@@ -438,7 +439,8 @@ struct StageTimer {
 // Q^* S H Q = 2 Re(X^* Y) and Q^* S Q = 2 i Im(X^* X).  The Rayleigh-Ritz step is
 // invariant to the choice of basis of the search space, so the results are
 // those of Algorithm 2 on any orthonormal basis.
-static int qr_jfixed(const cplx* X, int64_t n, int64_t m, cplx* Q, bool* ok_out, cudaStream_t s) {
+static int qr_jfixed(const cplx* X, int64_t n, int64_t m, cplx* Q, bool* ok_out, cudaStream_t s,
+                     bool sliced) {
   *ok_out = false;
   Workspace ws(s);
   cplx *C, *G, *Linv, *T, *Q1;
@@ -452,12 +454,28 @@ static int qr_jfixed(const cplx* X, int64_t n, int64_t m, cplx* Q, bool* ok_out,
   CB_TRY(ws.alloc(&info_d, 1));
   CB_TRY(ws.alloc(&diag_d, m));
   std::vector<double> dg(m);
+  // sliced tensor-core operands: the columns (Gram), the real-form rows of the
+  // block and the conjugated rows of L^{-1} (X L^{-*})
+  SlicedOp sc, sr, sl;
+  double* tmp = nullptr;
+  if (sliced) {
+    CB_TRY(sliced_alloc(ws, sc, m, 2 * n, s));
+    CB_TRY(sliced_alloc(ws, sr, 2 * n, 2 * m, s));
+    CB_TRY(sliced_alloc(ws, sl, m, 2 * m, s));
+    CB_TRY(ws.alloc(&tmp, 4 * n * m));
+  }
   const cplx* src = X;
   StageTimer tm(s, "qr(J)");
   for (int pass = 0; pass < 2; ++pass) {
     cplx* dst = (pass == 0) ? Q1 : Q;
-    CB_TRY(zgemm('C', 'N', m, m, n, mk(1, 0), src, n, src, n, mk(0, 0), C, m, s));
-    CB_TRY(re_im_part(C, G, m, 0, s));  // Gram of the J-fixed vectors: 2 Re(X^* X)
+    if (sliced) {  // Gram of the J-fixed vectors: 2 Re(X^* X), real part of G
+      CB_TRY(slice_rows(reinterpret_cast<const double*>(src), 2 * n, 0, sc, s));
+      CB_CUDA(cudaMemsetAsync(G, 0, sizeof(cplx) * m * m, s));
+      CB_TRY(sliced_gemm(sc, sc, 2.0, reinterpret_cast<double*>(G), 2, 2 * m, false, s));
+    } else {
+      CB_TRY(zgemm('C', 'N', m, m, n, mk(1, 0), src, n, src, n, mk(0, 0), C, m, s));
+      CB_TRY(re_im_part(C, G, m, 0, s));  // Gram of the J-fixed vectors: 2 Re(X^* X)
+    }
     tm.mark("gram");
     int info = 0;
     CB_TRY(cholesky(G, m, info_d, &info, s));
@@ -473,7 +491,13 @@ static int qr_jfixed(const cplx* X, int64_t n, int64_t m, cplx* Q, bool* ok_out,
     }
     CB_TRY(tri_inverse(G, m, Linv, T, s));
     tm.mark("trinv");
-    CB_TRY(zgemm('N', 'C', n, m, m, mk(1, 0), src, n, Linv, m, mk(0, 0), dst, n, s));
+    if (sliced) {
+      CB_TRY(slice_complex_rows(src, n, n, m, tmp, sr, s));
+      CB_TRY(slice_conj_rows(Linv, m, sl, s));
+      CB_TRY(sliced_gemm(sr, sl, 1.0, reinterpret_cast<double*>(dst), 1, 2 * n, false, s));
+    } else {
+      CB_TRY(zgemm('N', 'C', n, m, m, mk(1, 0), src, n, Linv, m, mk(0, 0), dst, n, s));
+    }
     tm.mark("apply");
     src = Q1;
   }
@@ -482,7 +506,7 @@ static int qr_jfixed(const cplx* X, int64_t n, int64_t m, cplx* Q, bool* ok_out,
 }
 
 static int rayleigh_ritz_jfixed(const cplx* A, const cplx* B, int64_t n, const cplx* Qt, int64_t k, double* ritz_host,
-                                cplx* Wpos, cplx* R, double* res, cudaStream_t s) {
+                                cplx* Wpos, cplx* R, double* res, cudaStream_t s, const SlicedOp* ph) {
   if (k <= 0 || (k % 2) != 0) return CHASE_BSE_BAD_ARG;
   const int64_t n2 = 2 * n, h = k / 2;
   Workspace ws(s);
@@ -501,8 +525,22 @@ static int rayleigh_ritz_jfixed(const cplx* A, const cplx* B, int64_t n, const c
   CB_TRY(ws.alloc(&Z, k * h));
   CB_TRY(ws.alloc(&rot, 2 * k));
   CB_TRY(ws.alloc(&scratch, k * 32));
-  CB_TRY(ws.alloc(&Qc, n * k));
-  CB_TRY(ws.alloc(&Tc, n * k));
+  const bool sliced = ph != nullptr;
+  SlicedOp sq, sqr, st, sqa, sta, sz, szc;
+  double* tmp = nullptr;
+  if (sliced) {
+    CB_TRY(sliced_alloc(ws, sq, k, 2 * n, s));       // columns of Q (J-fixed top halves)
+    CB_TRY(sliced_alloc(ws, sqr, k, 2 * n, s));      // the same, pairs (a, b) -> (b, -a)
+    CB_TRY(sliced_alloc(ws, st, k, 2 * n, s));       // columns of T
+    CB_TRY(sliced_alloc(ws, sqa, 2 * n, 2 * k, s));  // real-form rows of Q
+    CB_TRY(sliced_alloc(ws, sta, 2 * n, 2 * k, s));  // real-form rows of T
+    CB_TRY(sliced_alloc(ws, sz, h, 2 * k, s));       // columns of Z
+    CB_TRY(sliced_alloc(ws, szc, h, 2 * k, s));      // columns of conj(Z)
+    CB_TRY(ws.alloc(&tmp, 4 * n * k));
+  } else {
+    CB_TRY(ws.alloc(&Qc, n * k));
+    CB_TRY(ws.alloc(&Tc, n * k));
+  }
   CB_TRY(ws.alloc(&SHW, n2 * h));
   CB_TRY(ws.alloc(&theta, k));
   CB_TRY(ws.alloc(&red, 2));
@@ -511,21 +549,38 @@ static int rayleigh_ritz_jfixed(const cplx* A, const cplx* B, int64_t n, const c
   CB_TRY(ws.alloc(&idx_d, h));
   StageTimer tm(s, "rr(J)");
   // lines 1-3: T = S H Q (top halves y = A x + B conj x), M = Q^* T = 2 Re(X^* Y)
-  CB_TRY(hop_top_fp64(A, B, n, Qt, k, Tt, s));
+  if (sliced) {
+    CB_TRY(slice_rows(reinterpret_cast<const double*>(Qt), 2 * n, 0, sq, s));
+    CB_TRY(sliced_gemm(*ph, sq, 1.0, reinterpret_cast<double*>(Tt), 1, 2 * n, false, s));
+  } else {
+    CB_TRY(hop_top_fp64(A, B, n, Qt, k, Tt, s));
+  }
   tm.mark("HQ");
   // The J-fixed columns come in pairs spanning {u, J u}; the small problem is set up in
   // the basis Q U (U = pairwise [[1, 1], [-i, i]] / sqrt 2), whose pairs point along
   // (u, J u): G then starts close to diagonal, as for the general basis.
-  CB_TRY(zgemm('C', 'N', k, k, n, mk(1, 0), Qt, n, Tt, n, mk(0, 0), C, k, s));
-  CB_TRY(re_im_part(C, Tmp, k, 0, s));
+  if (sliced) {
+    CB_TRY(slice_rows(reinterpret_cast<const double*>(Tt), 2 * n, 0, st, s));
+    CB_CUDA(cudaMemsetAsync(Tmp, 0, sizeof(cplx) * k * k, s));
+    CB_TRY(sliced_gemm(sq, st, 2.0, reinterpret_cast<double*>(Tmp), 2, 2 * k, false, s));
+  } else {
+    CB_TRY(zgemm('C', 'N', k, k, n, mk(1, 0), Qt, n, Tt, n, mk(0, 0), C, k, s));
+    CB_TRY(re_im_part(C, Tmp, k, 0, s));
+  }
   CB_TRY(pair_transform(Tmp, M, k, s));
   int info = 0;
   CB_TRY(cholesky(M, k, info_d, &info, s));  // line 4
   if (info != 0) return CHASE_BSE_NOT_DEFINITE;
   CB_TRY(tri_inverse(M, k, Linv, scratch, s));
   // line 5: Q^* S Q = 2 i Im(X^* X)
-  CB_TRY(zgemm('C', 'N', k, k, n, mk(1, 0), Qt, n, Qt, n, mk(0, 0), C, k, s));
-  CB_TRY(re_im_part(C, Tmp, k, 1, s));
+  if (sliced) {  // Im(x_i^* x_j) = x_i . (Im x_j, -Re x_j) on (re, im) pairs
+    CB_TRY(slice_rows(reinterpret_cast<const double*>(Qt), 2 * n, 1, sqr, s));
+    CB_CUDA(cudaMemsetAsync(Tmp, 0, sizeof(cplx) * k * k, s));
+    CB_TRY(sliced_gemm(sq, sqr, 2.0, reinterpret_cast<double*>(Tmp) + 1, 2, 2 * k, false, s));
+  } else {
+    CB_TRY(zgemm('C', 'N', k, k, n, mk(1, 0), Qt, n, Qt, n, mk(0, 0), C, k, s));
+    CB_TRY(re_im_part(C, Tmp, k, 1, s));
+  }
   CB_TRY(pair_transform(Tmp, M2, k, s));
   // line 7: G = L^{-1} M2 L^{-*}
   CB_TRY(zgemm('N', 'N', k, k, k, mk(1, 0), Linv, k, M2, k, mk(0, 0), Tmp, k, s));
@@ -551,12 +606,23 @@ static int rayleigh_ritz_jfixed(const cplx* A, const cplx* B, int64_t n, const c
   // W+ = Q Z+ = [X Z; conj(X) Z]; S H W+ = [Y Z; conj(Y) Z]
   CB_TRY(zgemm('C', 'N', k, h, k, mk(1, 0), Linv, k, Ypos, k, mk(0, 0), Tmp, k, s));
   CB_TRY(pair_apply(Tmp, Z, k, h, s));
-  CB_TRY(conj_copy(Qc, n, Qt, n, n, k, s));
-  CB_TRY(conj_copy(Tc, n, Tt, n, n, k, s));
-  CB_TRY(zgemm('N', 'N', n, h, k, mk(1, 0), Qt, n, Z, k, mk(0, 0), Wpos, n2, s));
-  CB_TRY(zgemm('N', 'N', n, h, k, mk(1, 0), Qc, n, Z, k, mk(0, 0), Wpos + n, n2, s));
-  CB_TRY(zgemm('N', 'N', n, h, k, mk(1, 0), Tt, n, Z, k, mk(0, 0), SHW, n2, s));
-  CB_TRY(zgemm('N', 'N', n, h, k, mk(1, 0), Tc, n, Z, k, mk(0, 0), SHW + n, n2, s));
+  if (sliced) {  // conj(X) Z = conj(X conj(Z)): the conjugated halves negate the odd (imaginary) rows
+    CB_TRY(slice_rows(reinterpret_cast<const double*>(Z), 2 * k, 0, sz, s));
+    CB_TRY(slice_rows(reinterpret_cast<const double*>(Z), 2 * k, 2, szc, s));
+    CB_TRY(slice_complex_rows(Qt, n, n, k, tmp, sqa, s));
+    CB_TRY(sliced_gemm(sqa, sz, 1.0, reinterpret_cast<double*>(Wpos), 1, 2 * n2, false, s));
+    CB_TRY(sliced_gemm(sqa, szc, 1.0, reinterpret_cast<double*>(Wpos + n), 1, 2 * n2, true, s));
+    CB_TRY(slice_complex_rows(Tt, n, n, k, tmp, sta, s));
+    CB_TRY(sliced_gemm(sta, sz, 1.0, reinterpret_cast<double*>(SHW), 1, 2 * n2, false, s));
+    CB_TRY(sliced_gemm(sta, szc, 1.0, reinterpret_cast<double*>(SHW + n), 1, 2 * n2, true, s));
+  } else {
+    CB_TRY(conj_copy(Qc, n, Qt, n, n, k, s));
+    CB_TRY(conj_copy(Tc, n, Tt, n, n, k, s));
+    CB_TRY(zgemm('N', 'N', n, h, k, mk(1, 0), Qt, n, Z, k, mk(0, 0), Wpos, n2, s));
+    CB_TRY(zgemm('N', 'N', n, h, k, mk(1, 0), Qc, n, Z, k, mk(0, 0), Wpos + n, n2, s));
+    CB_TRY(zgemm('N', 'N', n, h, k, mk(1, 0), Tt, n, Z, k, mk(0, 0), SHW, n2, s));
+    CB_TRY(zgemm('N', 'N', n, h, k, mk(1, 0), Tc, n, Z, k, mk(0, 0), SHW + n, n2, s));
+  }
   CB_TRY(normalize_and_residual(Wpos, SHW, rz, n, h, R, s));
   CB_TRY(col_norms(R, n2, h, res, s));
   CB_CUDA(cudaStreamSynchronize(s));  // host vectors must outlive the copies
@@ -665,7 +731,9 @@ int solve(const cplx* A, const cplx* B, int64_t n, int64_t nev, int64_t nex, int
       (o.precision != CHASE_BSE_FP64 && o.precision != CHASE_BSE_MIXED_BF16X3 &&
        o.precision != CHASE_BSE_MIXED_BF16X6))
     return CHASE_BSE_BAD_ARG;
+  if (o.fp64_products != 0 && o.fp64_products != 1) return CHASE_BSE_BAD_ARG;
   const bool mixed = o.precision != CHASE_BSE_FP64;
+  const bool sliced = mixed && o.fp64_products == 0;
   const int scheme = o.precision == CHASE_BSE_MIXED_BF16X6 ? 6 : 3;
   if (mixed && !mixed_available()) return CHASE_BSE_UNSUPPORTED;
   cudaStream_t s = (cudaStream_t)o.stream;
@@ -691,6 +759,13 @@ int solve(const cplx* A, const cplx* B, int64_t n, int64_t nev, int64_t nex, int
   }
   std::vector<double> ritz_keep;  // Ritz values of the columns of W (mixed correction form)
   PhaseClock clk(s);
+  // mixed mode: the rows of H's top block row, y = A x + B conj(x), as sliced
+  // tensor-core operand for the Rayleigh-Ritz product H Q (cut once per solve)
+  SlicedOp ph;
+  if (sliced) {
+    CB_TRY(sliced_alloc(ws, ph, 2 * n, 2 * n, s));
+    CB_TRY(slice_hamiltonian(A, B, n, ph, s));
+  }
 
   // Algorithm 3 line 1: W+ = randn(2n, nevex), lower half scaled by gamma
   if (o.W0) CB_CUDA(cudaMemcpyAsync(W, o.W0, sizeof(cplx) * n2 * nevex, cudaMemcpyDeviceToDevice, s));
@@ -730,7 +805,7 @@ int solve(const cplx* A, const cplx* B, int64_t n, int64_t nev, int64_t nex, int
     clk.start();
     CB_TRY(build_jfixed(X, Ylock, locked, W, kf, n, s));
     bool jok = false;
-    CB_TRY(qr_jfixed(X, n, 2 * nevex, Qf, &jok, s));
+    CB_TRY(qr_jfixed(X, n, 2 * nevex, Qf, &jok, s, sliced));
     int hh = 0;
     if (!jok) {
       CB_TRY(build_qr_input(X, Ylock, locked, W, kf, n, s));
@@ -744,7 +819,8 @@ int solve(const cplx* A, const cplx* B, int64_t n, int64_t nev, int64_t nex, int
     Workspace rws(s);
     if (!Rvec) CB_TRY(rws.alloc(&Rvec, n2 * kf));
     // lines 8-11: Rayleigh-Ritz, W+ = Q Z+ and the residuals of the positive half
-    int rs = jok ? rayleigh_ritz_jfixed(A, B, n, Qf + 2 * locked * n, 2 * kf, ritz.data(), Wpos, Rvec, res_d, s)
+    int rs = jok ? rayleigh_ritz_jfixed(A, B, n, Qf + 2 * locked * n, 2 * kf, ritz.data(), Wpos, Rvec, res_d, s,
+                                        sliced ? &ph : nullptr)
                  : rayleigh_ritz(A, B, n, Qf + 2 * locked * n2, 2 * kf, ritz.data(), Wpos, s, Rvec, res_d);
     st.ms_rr += clk.stop();
     if (rs != CHASE_BSE_OK) { status = rs; break; }

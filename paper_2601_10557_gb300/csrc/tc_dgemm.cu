@@ -1,0 +1,495 @@
+// FP64-accurate sliced GEMM on tcgen05 tensor cores (see tc_dgemm.cuh).
+//
+// Kernel (one CTA per 128 x 32 output tile and K split, 384 threads):
+//   warp 0    TMA producer: per 32-long K block, all 7 digit planes of the A tile
+//             (one 3-D box of 32 x 128 x 7) and of the B tile (32 x 32 x 7), 64-byte
+//             swizzle, into a 3-stage ring (70 KB per stage)
+//   warp 1    allocates 512 TMEM columns; one lane issues, per 16-long K step and
+//             A digit t, one MMA against the B digits u = 0 .. 6 - t stacked along N
+//             (N = (7 - t) * 32), accumulating into the TMEM columns of the weight
+//             groups w = t + u = t .. 6; two buffers of 7 x 32 columns alternate
+//             every 128 K
+//   warps 4-11 drain each finished buffer (warps 4-7 columns 0-15, warps 8-11
+//             columns 16-31 of every group): the exact integer group sums of
+//             weights 2^0 .. 2^-24 into one 64-bit integer per output, those of
+//             2^-32 .. 2^-48 into a second one; at the end they write both to a
+//             per-split partial tile
+// A second kernel sums the splits in order, applies the row and column exponents
+// and writes the FP64 result with arbitrary strides.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "tc_common.cuh"
+#include "tc_dgemm.cuh"
+
+namespace cb {
+namespace tcd {
+
+using namespace cb::tc;
+
+constexpr int S = SLICES;
+constexpr int BM = 128, BNS = 32, BK = 32;
+constexpr int A_SLICE = BM * BK * 2;                    // 8 KB
+constexpr int B_SLICE = BNS * BK * 2;                   // 2 KB
+constexpr int STAGE_BYTES = S * (A_SLICE + B_SLICE);    // 70 KB
+constexpr int ST = 3;
+constexpr int CHUNK = 4;                                // K blocks per exact partial sum (128 K)
+constexpr int GCOLS = S * BNS;                          // TMEM columns per buffer
+constexpr uint32_t TMEM_COLS = 512;
+constexpr int THREADS = 384;
+constexpr int DRAIN_WARPS = 8;
+constexpr int NBAR = 2 * ST + 5;
+constexpr int SMEM_BYTES = ST * STAGE_BYTES + 1024 + 256;
+static_assert(2 * GCOLS <= (int)TMEM_COLS, "two accumulator buffers must fit in TMEM");
+// a weight group holds at most S digit products of |d| <= 128 over CHUNK * BK terms
+static_assert((double)S * 16384.0 * CHUNK * BK < 16777216.0, "group sums must stay exact in FP32");
+
+__device__ __forceinline__ uint32_t idesc_n(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+// K-major tile with 64-byte rows and 64-byte swizzle: 8-row groups 512 bytes apart.
+__device__ __forceinline__ uint64_t sdesc64(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(512 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)4 << 61;  // 64-byte swizzle
+  return d;
+}
+
+struct Args {
+  int num_m, num_n, kb_total, kb_per_split;
+  int64_t mp;          // rows of a partial tile column (A rows_pad)
+  int64_t np;          // columns per split (B rows_pad)
+  long long* hi;       // [split][col][row]
+  long long* lo;
+  int* err;
+};
+
+__global__ void __launch_bounds__(THREADS, 1)
+    sliced_gemm_kernel(const __grid_constant__ CUtensorMap ma, const __grid_constant__ CUtensorMap mb, Args g) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + ST * STAGE_BYTES);
+  uint32_t full[ST], empty[ST];
+#pragma unroll
+  for (int s = 0; s < ST; ++s) {
+    full[s] = smem_u32(bars + s);
+    empty[s] = smem_u32(bars + ST + s);
+  }
+  const uint32_t accf[2] = {smem_u32(bars + 2 * ST), smem_u32(bars + 2 * ST + 1)};
+  const uint32_t acce[2] = {smem_u32(bars + 2 * ST + 2), smem_u32(bars + 2 * ST + 3)};
+  const uint32_t done = smem_u32(bars + 2 * ST + 4);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + NBAR);
+  volatile int* abort_sh = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  int* issued_sh = reinterpret_cast<int*>(tmem_slot + 2);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  // m fastest: the CTAs sharing one B tile run together
+  const int bid = blockIdx.x;
+  const int mt = bid % g.num_m;
+  const int nt = (bid / g.num_m) % g.num_n;
+  const int sp = bid / (g.num_m * g.num_n);
+  const int kb0 = sp * g.kb_per_split;
+  const int nkb = min(g.kb_per_split, g.kb_total - kb0);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < ST; ++s) {
+      mbar_init(full[s], 1);
+      mbar_init(empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(accf[b], 1);
+      mbar_init(acce[b], DRAIN_WARPS);
+    }
+    mbar_init(done, 1);
+    *abort_sh = 0;
+    *issued_sh = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t sbase = smem_u32(smem);
+
+  if (warp == 0 && lane == 0) {
+    int issued = 0;
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % ST;
+      const uint32_t ph = (uint32_t)(kb / ST) & 1u;
+      if (kb >= ST && !mbar_wait(empty[s], ph ^ 1u, abort_sh, g.err, true)) break;
+      const uint32_t st = sbase + s * STAGE_BYTES;
+      mbar_expect_tx(full[s], STAGE_BYTES);
+      tma_load_3d(st, &ma, (kb0 + kb) * BK, mt * BM, 0, full[s]);
+      tma_load_3d(st + S * A_SLICE, &mb, (kb0 + kb) * BK, nt * BNS, 0, full[s]);
+      issued = kb + 1;
+    }
+    *issued_sh = issued;
+  } else if (warp == 1 && lane == 0) {
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int grp = kb / CHUNK, b = grp & 1;
+      const bool first = (kb % CHUNK) == 0;
+      const bool last = (kb % CHUNK) == CHUNK - 1 || kb == nkb - 1;
+      if (first && grp >= 2 && !mbar_wait(acce[b], (uint32_t)((grp >> 1) - 1) & 1u, abort_sh, g.err, true)) break;
+      const int s = kb % ST;
+      const uint32_t ph = (uint32_t)(kb / ST) & 1u;
+      if (!mbar_wait(full[s], ph, abort_sh, g.err, true)) break;
+      tc_fence_after();
+      const uint32_t st = sbase + s * STAGE_BYTES;
+      const uint32_t buf = tmem + (uint32_t)(b * GCOLS);
+#pragma unroll
+      for (int kk = 0; kk < BK / 16; ++kk) {
+        const uint64_t bd = sdesc64(st + S * A_SLICE + kk * 32);
+#pragma unroll
+        for (int t = 0; t < S; ++t) {
+          const uint64_t ad = sdesc64(st + t * A_SLICE + kk * 32);
+          const uint32_t acc = (first && kk == 0 && t == 0) ? 0u : 1u;
+          mma_bf16(buf + (uint32_t)(t * BNS), ad, bd, idesc_n((S - t) * BNS), acc);
+        }
+      }
+      mma_commit(empty[s]);
+      if (last) mma_commit(accf[b]);
+    }
+    mma_commit(done);
+  } else if (warp >= 4) {
+    // TMEM lanes 32 (warp % 4) .. +31 are the rows; half selects columns 0-15 or 16-31
+    const int q = warp & 3, half = (warp - 4) >> 2;
+    const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+    constexpr int NC = BNS / 2;
+    long long hi[NC], lo[NC];
+#pragma unroll
+    for (int i = 0; i < NC; ++i) {
+      hi[i] = 0;
+      lo[i] = 0;
+    }
+    bool ok = true;
+    const int ngrp = (nkb + CHUNK - 1) / CHUNK;
+    for (int grp = 0; grp < ngrp; ++grp) {
+      const int b = grp & 1;
+      const bool w = mbar_wait(accf[b], (uint32_t)(grp >> 1) & 1u, abort_sh, g.err, true);
+      if (!__all_sync(0xffffffffu, w)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t col = tmem + lane_base + (uint32_t)(b * GCOLS + half * NC);
+      uint32_t r0[NC], r1[NC], r2[NC];
+      // group sums g_w are integers below 2^24 (exact in FP32)
+      // hi += (g0 2^8 + g1) 2^16 + g2 2^8 + g3       (each bracket below 2^31)
+      tmem_ld16_nowait(col, r0);
+      tmem_ld16_nowait(col + 32, r1);
+      tmem_wait_ld();
+#pragma unroll
+      for (int i = 0; i < NC; ++i) {
+        const int v = __float2int_rn(__uint_as_float(r0[i])) * 256 + __float2int_rn(__uint_as_float(r1[i]));
+        hi[i] += (long long)v * 65536;
+      }
+      tmem_ld16_nowait(col + 64, r0);
+      tmem_ld16_nowait(col + 96, r1);
+      tmem_wait_ld();
+#pragma unroll
+      for (int i = 0; i < NC; ++i) {
+        const int v = __float2int_rn(__uint_as_float(r0[i])) * 256 + __float2int_rn(__uint_as_float(r1[i]));
+        hi[i] += (long long)v;
+      }
+      // lo += g4 2^16 + g5 2^8 + g6
+      tmem_ld16_nowait(col + 128, r0);
+      tmem_ld16_nowait(col + 160, r1);
+      tmem_ld16_nowait(col + 192, r2);
+      tmem_wait_ld();
+#pragma unroll
+      for (int i = 0; i < NC; ++i) {
+        lo[i] += (long long)__float2int_rn(__uint_as_float(r0[i])) * 65536 +
+                 (long long)__float2int_rn(__uint_as_float(r1[i])) * 256 +
+                 (long long)__float2int_rn(__uint_as_float(r2[i]));
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(acce[b]);
+    }
+    if (ok && !*abort_sh) {
+      const int64_t row = (int64_t)mt * BM + q * 32 + lane;  // < mp: rows are padded to whole tiles
+      const int64_t base = ((int64_t)sp * g.np + (int64_t)nt * BNS + half * NC) * g.mp + row;
+#pragma unroll
+      for (int i = 0; i < NC; ++i) {
+        g.hi[base + (int64_t)i * g.mp] = hi[i];
+        g.lo[base + (int64_t)i * g.mp] = lo[i];
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x == 0 && *abort_sh) {
+    const int issued = *issued_sh;
+    for (int kb = max(0, issued - ST); kb < issued; ++kb)
+      mbar_wait(full[kb % ST], (uint32_t)(kb / ST) & 1u, abort_sh, g.err, false);
+  }
+  if (warp == 1) {
+    if (lane == 0) mbar_wait(done, 0, abort_sh, g.err, false);
+    __syncwarp();
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+__global__ void sliced_finalize_kernel(const long long* hi, const long long* lo, int splits, int64_t mp, int64_t np,
+                                       const int* ea, const int* eb, int64_t M, int64_t N, double alpha,
+                                       double* out, int64_t rs, int64_t cs, int neg_odd) {
+  const int64_t total = M * N;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = idx % M, c = idx / M;
+    long long h = 0, l = 0;
+    for (int sp = 0; sp < splits; ++sp) {
+      const int64_t o = ((int64_t)sp * np + c) * mp + r;
+      h += hi[o];
+      l += lo[o];
+    }
+    // exact when |h|, |l| < 2^53; one rounding for the sum
+    const double v = fma((double)l, 0x1p-48, (double)h * 0x1p-24);
+    double y = alpha * ldexp(v, ea[r] + eb[c] - 14);
+    if (neg_odd && (r & 1)) y = -y;
+    out[r * rs + c * cs] = y;
+  }
+}
+
+// ---------------------------------------------------------------- slicing
+// One warp per row: exponent e with |x| < 2^e on the row, then the digits
+// d_t = rint(r_t), r_0 = x 2^(7-e), r_{t+1} = (r_t - d_t) 2^8.
+template <class Src>
+__global__ void slice_kernel(Src src, int64_t rows, int64_t K, int64_t kpad, int64_t plane, __nv_bfloat16* planes,
+                             int* exps) {
+  const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (r >= rows) return;
+  double m = 0.0;
+  for (int64_t p = lane; 2 * p < K; p += 32) {
+    const double2 v = src.pair(r, p);
+    m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  int e = 0;
+  if (m > 0.0) frexp(m, &e);
+  __nv_bfloat16* row = planes + r * kpad;
+  for (int64_t p = lane; 2 * p < kpad; p += 32) {
+    double2 v = make_double2(0.0, 0.0);
+    if (2 * p < K) v = src.pair(r, p);
+    double s0 = ldexp(v.x, 7 - e), s1 = ldexp(v.y, 7 - e);
+#pragma unroll
+    for (int t = 0; t < S; ++t) {
+      const double d0 = rint(s0), d1 = rint(s1);
+      *reinterpret_cast<__nv_bfloat162*>(row + t * plane + 2 * p) =
+          __halves2bfloat162(__float2bfloat16_rn((float)d0), __float2bfloat16_rn((float)d1));
+      s0 = (s0 - d0) * 256.0;
+      s1 = (s1 - d1) * 256.0;
+    }
+  }
+  if (lane == 0) exps[r] = e;
+}
+
+struct RowsSrc {  // row r at p + r * ld, pairs transformed by mode
+  const double* p;
+  int64_t ld;
+  int mode;
+  __device__ double2 pair(int64_t r, int64_t q) const {
+    const double2 v = *reinterpret_cast<const double2*>(p + r * ld + 2 * q);
+    if (mode == 1) return make_double2(v.y, -v.x);
+    if (mode == 2) return make_double2(v.x, -v.y);
+    return v;
+  }
+};
+struct RowsSrcUnaligned {  // same, for an odd ld or offset
+  const double* p;
+  int64_t ld;
+  int mode;
+  __device__ double2 pair(int64_t r, int64_t q) const {
+    const double a = p[r * ld + 2 * q], b = p[r * ld + 2 * q + 1];
+    if (mode == 1) return make_double2(b, -a);
+    if (mode == 2) return make_double2(a, -b);
+    return make_double2(a, b);
+  }
+};
+struct HamSrc {  // rows of P': y = A x + B conj(x) in (re, im) interleaved form
+  const cplx* A;
+  const cplx* B;
+  int64_t n;
+  __device__ double2 pair(int64_t r, int64_t l) const {
+    const int64_t i = r >> 1;
+    const cplx a = A[i * n + l], b = B[i * n + l];
+    if ((r & 1) == 0) return make_double2(a.x + b.x, b.y - a.y);  // Re y: (Re x, Im x) coefficients
+    return make_double2(a.y + b.y, a.x - b.x);                    // Im y
+  }
+};
+
+struct ConjRowsSrc {  // row r of the complex column-major M, conjugated
+  const cplx* M;
+  int64_t ld;
+  __device__ double2 pair(int64_t r, int64_t l) const {
+    const cplx v = M[r + l * ld];
+    return make_double2(v.x, -v.y);
+  }
+};
+
+// out (2n x 2m, row-major): rows 2i, 2i+1 of the real form of row i of X.
+__global__ void complex_rows_kernel(const cplx* X, int64_t ldx, int64_t n, int64_t m, double* out) {
+  __shared__ cplx t[32][33];
+  const int64_t i0 = (int64_t)blockIdx.x * 32, l0 = (int64_t)blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  for (int j = ty; j < 32; j += 8) {
+    const int64_t i = i0 + tx, l = l0 + j;
+    t[j][tx] = (i < n && l < m) ? X[i + l * ldx] : mk(0, 0);
+  }
+  __syncthreads();
+  for (int j = ty; j < 32; j += 8) {
+    const int64_t i = i0 + j, l = l0 + tx;
+    if (i < n && l < m) {
+      const cplx x = t[tx][j];
+      double* r0 = out + (2 * i) * (2 * m) + 2 * l;
+      double* r1 = r0 + 2 * m;
+      r0[0] = x.x;
+      r0[1] = -x.y;
+      r1[0] = x.y;
+      r1[1] = x.x;
+    }
+  }
+}
+
+static unsigned gsz(int64_t total) {
+  const int64_t b = (total + 255) / 256;
+  return (unsigned)std::min<int64_t>(std::max<int64_t>(b, 1), 16384);
+}
+
+static int make_map3(CUtensorMap* m, const void* base, int64_t kpad, int64_t rows_pad, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return CHASE_BSE_UNSUPPORTED;
+  const cuuint64_t dims[3] = {(cuuint64_t)kpad, (cuuint64_t)rows_pad, (cuuint64_t)S};
+  const cuuint64_t strides[2] = {(cuuint64_t)kpad * 2, (cuuint64_t)(rows_pad * kpad * 2)};
+  const cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, (cuuint32_t)S};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? CHASE_BSE_OK : CHASE_BSE_CUDA_ERROR;
+}
+
+template <class Src>
+static int run_slice(const Src& src, SlicedOp& op, cudaStream_t s) {
+  const int64_t warps = op.rows;
+  slice_kernel<Src><<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(src, op.rows, op.K, op.kpad,
+                                                                          op.rows_pad * op.kpad, op.planes, op.exps);
+  count_launch();
+  CB_LAUNCH();
+  return CHASE_BSE_OK;
+}
+
+}  // namespace tcd
+
+int sliced_alloc(Workspace& ws, SlicedOp& op, int64_t rows, int64_t K, cudaStream_t s) {
+  using namespace tcd;
+  if (rows <= 0 || K <= 0 || (K % 2) != 0) return CHASE_BSE_BAD_ARG;
+  op.rows = rows;
+  op.K = K;
+  op.rows_pad = ((rows + BM - 1) / BM) * BM;
+  op.kpad = ((K + BK - 1) / BK) * BK;
+  const int64_t elems = (int64_t)S * op.rows_pad * op.kpad;
+  CB_TRY(ws.alloc(&op.planes, elems));
+  CB_TRY(ws.alloc(&op.exps, op.rows_pad));
+  // rows beyond `rows` stay zero (and their exponent 0)
+  if (op.rows_pad > rows) {
+    for (int t = 0; t < S; ++t)
+      CB_CUDA(cudaMemsetAsync(op.planes + (int64_t)t * op.rows_pad * op.kpad + rows * op.kpad, 0,
+                              sizeof(__nv_bfloat16) * (op.rows_pad - rows) * op.kpad, s));
+    CB_CUDA(cudaMemsetAsync(op.exps + rows, 0, sizeof(int) * (op.rows_pad - rows), s));
+  }
+  CB_TRY(make_map3(&op.map_a, op.planes, op.kpad, op.rows_pad, BM));
+  CB_TRY(make_map3(&op.map_b, op.planes, op.kpad, op.rows_pad, BNS));
+  return CHASE_BSE_OK;
+}
+
+int slice_rows(const double* src, int64_t ld, int mode, SlicedOp& op, cudaStream_t s) {
+  if ((reinterpret_cast<uintptr_t>(src) % 16) == 0 && (ld % 2) == 0)
+    return tcd::run_slice(tcd::RowsSrc{src, ld, mode}, op, s);
+  return tcd::run_slice(tcd::RowsSrcUnaligned{src, ld, mode}, op, s);
+}
+
+int slice_complex_rows(const cplx* X, int64_t ldx, int64_t n, int64_t m, double* tmp, SlicedOp& op,
+                       cudaStream_t s) {
+  if (op.rows != 2 * n || op.K != 2 * m) return CHASE_BSE_BAD_ARG;
+  dim3 grid((unsigned)((n + 31) / 32), (unsigned)((m + 31) / 32));
+  tcd::complex_rows_kernel<<<grid, dim3(32, 8), 0, s>>>(X, ldx, n, m, tmp);
+  count_launch();
+  CB_LAUNCH();
+  return slice_rows(tmp, 2 * m, 0, op, s);
+}
+
+int slice_conj_rows(const cplx* M, int64_t ld, SlicedOp& op, cudaStream_t s) {
+  return tcd::run_slice(tcd::ConjRowsSrc{M, ld}, op, s);
+}
+
+int slice_hamiltonian(const cplx* A, const cplx* B, int64_t n, SlicedOp& op, cudaStream_t s) {
+  if (op.rows != 2 * n || op.K != 2 * n) return CHASE_BSE_BAD_ARG;
+  return tcd::run_slice(tcd::HamSrc{A, B, n}, op, s);
+}
+
+int sliced_gemm(const SlicedOp& a, const SlicedOp& b, double alpha, double* out, int64_t rs, int64_t cs,
+                bool neg_odd, cudaStream_t s) {
+  using namespace tcd;
+  if (a.K != b.K || a.kpad != b.kpad) return CHASE_BSE_BAD_ARG;
+  static bool attr = false;
+  if (!attr) {
+    CB_CUDA(cudaFuncSetAttribute(sliced_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    attr = true;
+  }
+  const int num_m = (int)(a.rows_pad / BM);
+  const int num_n = (int)((b.rows + BNS - 1) / BNS);
+  const int kb_total = (int)(a.kpad / BK);
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  // split K until about two CTAs per SM, keeping whole 128-long chunks per split
+  const int64_t tiles = (int64_t)num_m * num_n;
+  const int max_split = std::max(1, kb_total / CHUNK);
+  int splits = (int)std::min<int64_t>(max_split, std::max<int64_t>(1, (2 * sms + tiles - 1) / tiles));
+  int kb_per = (kb_total + splits - 1) / splits;
+  kb_per = ((kb_per + CHUNK - 1) / CHUNK) * CHUNK;
+  splits = (kb_total + kb_per - 1) / kb_per;
+  Workspace ws(s);
+  const int64_t np = (int64_t)num_n * BNS, mp = a.rows_pad;
+  Args g{};
+  g.num_m = num_m;
+  g.num_n = num_n;
+  g.kb_total = kb_total;
+  g.kb_per_split = kb_per;
+  g.mp = mp;
+  g.np = np;
+  CB_TRY(ws.alloc(&g.hi, (size_t)splits * np * mp));
+  CB_TRY(ws.alloc(&g.lo, (size_t)splits * np * mp));
+  CB_TRY(ws.alloc(&g.err, 1));
+  CB_CUDA(cudaMemsetAsync(g.err, 0, sizeof(int), s));
+  sliced_gemm_kernel<<<(unsigned)(tiles * splits), THREADS, SMEM_BYTES, s>>>(a.map_a, b.map_b, g);
+  count_launch();
+  CB_LAUNCH();
+  sliced_finalize_kernel<<<gsz(a.rows * b.rows), 256, 0, s>>>(g.hi, g.lo, splits, mp, np, a.exps, b.exps, a.rows,
+                                                              b.rows, alpha, out, rs, cs, neg_odd ? 1 : 0);
+  count_launch();
+  CB_LAUNCH();
+  int herr = 0;
+  CB_CUDA(cudaMemcpyAsync(&herr, g.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CB_CUDA(cudaStreamSynchronize(s));
+  return herr ? CHASE_BSE_DEVICE_TIMEOUT : CHASE_BSE_OK;
+}
+
+}  // namespace cb
