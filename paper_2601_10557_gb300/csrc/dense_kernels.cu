@@ -6,6 +6,11 @@
 
 namespace cb {
 
+static inline unsigned gs(int64_t total) {
+  const int64_t b = (total + 255) / 256;
+  return (unsigned)(b < 8192 ? (b > 0 ? b : 1) : 8192);
+}
+
 namespace {
 constexpr int NB = 32;  // Cholesky / triangular-inverse block size
 
@@ -27,6 +32,54 @@ __device__ double block_sum(double v, double* sh) {
   return v;
 }
 }  // namespace
+
+// ------------------------------------------------------------ grid barrier
+// For kernels launched cooperatively (all CTAs co-resident): a counter plus a
+// generation word in global memory.  Every wait is bounded (2 s of
+// %globaltimer), after which the kernel records an error, and all CTAs leave
+// at their next barrier.  Data written by other CTAs before a barrier is read
+// with __ldcg (L2) after it.
+struct GridSync {
+  unsigned count;  // arrival word: its top bit flips once per completed barrier
+  unsigned gen;    // unused (kept zero)
+};
+__device__ __forceinline__ unsigned long long gtimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// CTA 0 adds 2^31 - (gridDim.x - 1), every other CTA adds 1 (release), so the
+// top bit of the word flips exactly when the last CTA arrives; the waiters poll
+// it with acquire loads.  The wait is bounded: after 2 s, or once another CTA
+// has recorded an error, the CTA records the error and returns false.
+__device__ bool grid_barrier(GridSync* gsync, int* err) {
+  __shared__ int ok_sh;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok_sh = 1;
+    const unsigned inc = (blockIdx.x == 0) ? (0x80000000u - (gridDim.x - 1)) : 1u;
+    unsigned old, cur;
+    __threadfence();  // the CTA's writes (ordered before by __syncthreads) become visible first
+    asm volatile("atom.add.release.gpu.u32 %0, [%1], %2;" : "=r"(old) : "l"(&gsync->count), "r"(inc) : "memory");
+    const unsigned long long t0 = gtimer_ns();
+    unsigned it = 0;
+    while (true) {
+      asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(cur) : "l"(&gsync->count) : "memory");
+      if (((old ^ cur) & 0x80000000u) != 0) break;
+      if ((++it & 63) == 0) {
+        if (*(volatile int*)err) { ok_sh = 0; break; }
+        if (gtimer_ns() - t0 > 2000000000ull) {
+          atomicExch(err, 1);
+          ok_sh = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok_sh != 0;
+}
 
 // ---------------------------------------------------------------- Cholesky
 __global__ void chol_diag_kernel(cplx* G, int64_t ld, int64_t j0, int nb, int* info) {
@@ -98,8 +151,152 @@ __global__ void zero_upper_kernel(cplx* G, int64_t k) {
   }
 }
 
+// Right-looking blocked Cholesky (NB-wide block columns) in one cooperative
+// kernel: per block column, CTA 0 factors the diagonal block, then every CTA
+// takes panel rows (forward substitution against L_JJ^*, as in chol_panel_kernel)
+// and finally tiles of the trailing update A22 -= L21 L21^*, with a grid barrier
+// after each phase.
+__global__ void chol_coop_kernel(cplx* G, int64_t k, int* info, GridSync* gsync, int* err) {
+  __shared__ cplx buf[2][NB][NB + 1];
+  auto& a = buf[0];   // diagonal block (phases 1, 2)
+  auto& pi = buf[0];  // panel rows of tile row I (phase 3)
+  auto& pk = buf[1];  // panel rows of tile column K (phase 3)
+  __shared__ double dinv[NB];
+  const int t = threadIdx.x;
+  const int64_t nb = (k + NB - 1) / NB;
+  for (int64_t J = 0; J < nb; ++J) {
+    const int64_t j0 = J * NB;
+    const int jb = (int)((k - j0) < NB ? (k - j0) : NB);
+    if (blockIdx.x == 0) {
+      for (int idx = t; idx < jb * jb; idx += blockDim.x) {
+        const int r = idx % jb, c = idx / jb;
+        a[r][c] = __ldcg(G + (j0 + r) + (j0 + c) * k);
+      }
+      __syncthreads();
+      for (int c = 0; c < jb; ++c) {
+        if (t == 0) {
+          double d = a[c][c].x;
+          if (!(d > 0.0)) {
+            atomicCAS(info, 0, (int)(j0 + c + 1));
+            d = 1.0;
+          }
+          const double sd = sqrt(d);
+          a[c][c] = mk(sd, 0.0);
+          dinv[c] = 1.0 / sd;
+        }
+        __syncthreads();
+        const double inv = dinv[c];
+        for (int r = c + 1 + t; r < jb; r += blockDim.x) a[r][c] = cscale(a[r][c], inv);
+        __syncthreads();
+        const int m = jb - c - 1;
+        for (int idx = t; idx < m * m; idx += blockDim.x) {
+          const int r = c + 1 + idx % m, q = c + 1 + idx / m;
+          if (q <= r) a[r][q] = csub(a[r][q], cmul(a[r][c], cconj(a[q][c])));
+        }
+        __syncthreads();
+      }
+      for (int idx = t; idx < jb * jb; idx += blockDim.x) {
+        const int r = idx % jb, c = idx / jb;
+        G[(j0 + r) + (j0 + c) * k] = (r >= c) ? a[r][c] : mk(0, 0);
+      }
+    }
+    if (!grid_barrier(gsync, err)) return;
+    const int64_t rest = k - j0 - jb;
+    if (rest > 0) {
+      // panel: rows i >= j0 + jb solve x L_JJ^* = a_i (forward substitution)
+      for (int idx = t; idx < jb * jb; idx += blockDim.x) {
+        const int r = idx % jb, c = idx / jb;
+        a[r][c] = __ldcg(G + (j0 + r) + (j0 + c) * k);
+      }
+      __syncthreads();
+      if (t < jb) dinv[t] = 1.0 / a[t][t].x;
+      __syncthreads();
+      // consecutive rows on consecutive CTAs: the FP64 work spreads over all SMs
+      for (int64_t i = j0 + jb + blockIdx.x + (int64_t)gridDim.x * t; i < k; i += (int64_t)gridDim.x * blockDim.x) {
+        cplx x[NB];
+#pragma unroll
+        for (int c = 0; c < NB; ++c) x[c] = (c < jb) ? __ldcg(G + i + (j0 + c) * k) : mk(0, 0);
+#pragma unroll
+        for (int c = 0; c < NB; ++c) {
+          if (c < jb) {
+            cplx v = x[c];
+#pragma unroll
+            for (int q = 0; q < NB; ++q)
+              if (q < c) v = csub(v, cmul(x[q], cconj(a[c][q])));
+            x[c] = cscale(v, dinv[c]);
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < NB; ++c)
+          if (c < jb) G[i + (j0 + c) * k] = x[c];
+      }
+      if (!grid_barrier(gsync, err)) return;
+      // trailing update, NB x NB tiles (I, K) with K <= I over the lower triangle
+      const int64_t T = (rest + NB - 1) / NB;
+      for (int64_t tile = blockIdx.x; tile < T * (T + 1) / 2; tile += gridDim.x) {
+        int64_t I = (int64_t)((sqrt(8.0 * (double)tile + 1.0) - 1.0) * 0.5);
+        while (I * (I + 1) / 2 > tile) --I;
+        while ((I + 1) * (I + 2) / 2 <= tile) ++I;
+        const int64_t K = tile - I * (I + 1) / 2;
+        const int64_t i0 = j0 + jb + I * NB, c0 = j0 + jb + K * NB;
+        const int ib = (int)((k - i0) < NB ? (k - i0) : NB), cbk = (int)((k - c0) < NB ? (k - c0) : NB);
+        __syncthreads();
+        for (int idx = t; idx < NB * jb; idx += blockDim.x) {
+          const int r = idx % NB, q = idx / NB;
+          pi[r][q] = (r < ib) ? __ldcg(G + (i0 + r) + (j0 + q) * k) : mk(0, 0);
+          pk[r][q] = (r < cbk) ? __ldcg(G + (c0 + r) + (j0 + q) * k) : mk(0, 0);
+        }
+        __syncthreads();
+        for (int idx = t; idx < ib * cbk; idx += blockDim.x) {
+          const int r = idx % ib, c = idx / ib;
+          if (I == K && c > r) continue;
+          cplx acc = __ldcg(G + (i0 + r) + (c0 + c) * k);
+          for (int q = 0; q < jb; ++q) acc = csub(acc, cmul(pi[r][q], cconj(pk[c][q])));
+          G[(i0 + r) + (c0 + c) * k] = acc;
+        }
+      }
+      if (!grid_barrier(gsync, err)) return;
+    }
+  }
+}
+
+static int coop_grid(const void* kern, int threads, int* grid_out) {
+  int dev = 0, sms = 0, per_sm = 0, coop = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0);
+  if (!coop || per_sm < 1 || sms < 1) return 0;
+  *grid_out = sms;  // one CTA per SM: fewer barrier arrivals
+  return 1;
+}
+
 int cholesky(cplx* G, int64_t k, int* info_dev, int* info_host, cudaStream_t s) {
   CB_CUDA(cudaMemsetAsync(info_dev, 0, sizeof(int), s));
+  int grid = 0;
+  if (coop_grid((const void*)chol_coop_kernel, 256, &grid)) {
+    GridSync* gsync = nullptr;
+    int* err = nullptr;
+    CB_CUDA(cudaMallocAsync(&gsync, sizeof(GridSync), s));
+    CB_CUDA(cudaMallocAsync(&err, sizeof(int), s));
+    CB_CUDA(cudaMemsetAsync(gsync, 0, sizeof(GridSync), s));
+    CB_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+    int64_t kk = k;
+    void* args[] = {&G, &kk, &info_dev, &gsync, &err};
+    const cudaError_t le = cudaLaunchCooperativeKernel((const void*)chol_coop_kernel, dim3(grid), dim3(256), args, 0, s);
+    if (le != cudaSuccess) cudaGetLastError();
+    count_launch();
+    zero_upper_kernel<<<cdiv(k * k, 256) < 4096 ? cdiv(k * k, 256) : 4096, 256, 0, s>>>(G, k);
+    count_launch();
+    int herr = 0;
+    CB_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CB_CUDA(cudaMemcpyAsync(info_host, info_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
+    cudaFreeAsync(gsync, s);
+    cudaFreeAsync(err, s);
+    CB_CUDA(cudaStreamSynchronize(s));
+    if (le != cudaSuccess) return CHASE_BSE_CUDA_ERROR;
+    return herr ? CHASE_BSE_DEVICE_TIMEOUT : CHASE_BSE_OK;
+  }
   for (int64_t j0 = 0; j0 < k; j0 += NB) {
     const int nb = (int)((k - j0) < NB ? (k - j0) : NB);
     chol_diag_kernel<<<1, 256, 0, s>>>(G, k, j0, nb, info_dev);
@@ -152,12 +349,82 @@ __global__ void inv_diag_blocks_kernel(const cplx* L, int64_t k, cplx* X) {
     if (r < nb) X[(j0 + r) + (j0 + c) * k] = x[r];
 }
 
-int tri_inverse(const cplx* L, int64_t k, cplx* X, cplx* T, cudaStream_t s) {
+// X = L^{-1} by block forward substitution on TCB columns per CTA:
+// X_I = L_II^{-1} (E_I - sum_{J < I} L_IJ X_J) for the block rows I below the
+// columns' diagonal block, with the inverted diagonal blocks already in X.  The
+// CTA keeps its TCB columns of X in shared memory; 256 threads = 32 rows x TCB
+// columns x 2 halves of each dot product.  REAL: L has zero imaginary parts.
+constexpr int TCB = 4;
+template <bool REAL>
+__global__ void trinv_cols_kernel(const cplx* __restrict__ L, int64_t k, cplx* X) {
+  extern __shared__ cplx xs[];  // k x TCB, xs[l * TCB + c]
+  __shared__ cplx red[2][NB][TCB];
+  __shared__ cplx rhs[NB][TCB];
+  const int t = threadIdx.x, r = t & 31, c = (t >> 5) & (TCB - 1), h = t / (32 * TCB);
+  const int64_t c0 = (int64_t)blockIdx.x * TCB;
+  const int64_t I0 = c0 / NB, nb = (k + NB - 1) / NB;
+  const int64_t lo = I0 * NB, hi0 = ((I0 + 1) * NB < k) ? (I0 + 1) * NB : k;
+  for (int64_t idx = t; idx < hi0 * TCB; idx += blockDim.x) {
+    const int64_t l = idx / TCB;
+    const int cc = (int)(idx % TCB);
+    xs[idx] = (l >= lo && c0 + cc < k) ? X[l + (c0 + cc) * k] : mk(0, 0);
+  }
+  __syncthreads();
+  for (int64_t I = I0 + 1; I < nb; ++I) {
+    const int64_t i0 = I * NB;
+    const int ib = (int)((k - i0) < NB ? (k - i0) : NB);
+    const int64_t mid = lo + (i0 - lo) / 2;
+    const int64_t from = h ? mid : lo, to = h ? i0 : mid;
+    cplx acc = mk(0, 0);
+    if (r < ib) {
+      const cplx* Lr = L + i0 + r;
+      if (REAL) {
+        double a = 0.0;
+        for (int64_t l = from; l < to; ++l) a = fma(Lr[l * k].x, xs[l * TCB + c].x, a);
+        acc = mk(a, 0.0);
+      } else {
+        for (int64_t l = from; l < to; ++l) acc = cadd(acc, cmul(Lr[l * k], xs[l * TCB + c]));
+      }
+    }
+    red[h][r][c] = acc;
+    __syncthreads();
+    if (h == 0) rhs[r][c] = mk(-(red[0][r][c].x + red[1][r][c].x), -(red[0][r][c].y + red[1][r][c].y));
+    __syncthreads();
+    if (h == 0 && r < ib) {
+      cplx v = mk(0, 0);
+      for (int q = 0; q <= r; ++q) {
+        const cplx d = X[(i0 + r) + (i0 + q) * k];
+        if (REAL) v.x = fma(d.x, rhs[q][c].x, v.x);
+        else v = cadd(v, cmul(d, rhs[q][c]));
+      }
+      xs[(i0 + r) * TCB + c] = v;
+      if (c0 + c < k) X[(i0 + r) + (c0 + c) * k] = v;
+    }
+    __syncthreads();
+  }
+}
+
+int tri_inverse(const cplx* L, int64_t k, cplx* X, cplx* T, cudaStream_t s, bool real) {
   CB_CUDA(cudaMemsetAsync(X, 0, sizeof(cplx) * k * k, s));
   const int64_t nblk = (k + NB - 1) / NB;
   inv_diag_blocks_kernel<<<(unsigned)nblk, NB, 0, s>>>(L, k, X);
   count_launch();
   CB_LAUNCH();
+  const size_t smem = sizeof(cplx) * (size_t)k * TCB;
+  if (smem <= 200 * 1024) {
+    static bool attr = false;
+    if (!attr) {
+      CB_CUDA(cudaFuncSetAttribute(trinv_cols_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+      CB_CUDA(cudaFuncSetAttribute(trinv_cols_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+      attr = true;
+    }
+    const unsigned grid = (unsigned)((k + TCB - 1) / TCB);
+    if (real) trinv_cols_kernel<true><<<grid, 64 * TCB, smem, s>>>(L, k, X);
+    else trinv_cols_kernel<false><<<grid, 64 * TCB, smem, s>>>(L, k, X);
+    count_launch();
+    CB_LAUNCH();
+    return CHASE_BSE_OK;
+  }
   for (int64_t b = 1; b < nblk; ++b) {
     const int64_t i0 = b * NB;
     const int64_t nbi = (k - i0) < NB ? (k - i0) : NB;
@@ -260,119 +527,232 @@ __global__ void offdiag_norm_kernel(const cplx* G, int64_t k, double* red) {
   if (threadIdx.x == 0) { red[0] = off; red[1] = tot; }
 }
 
-// ---- one Jacobi sweep as a single cooperative kernel ----------------------
-// All CTAs are co-resident (cooperative launch), and each round of the sweep is
-// two phases separated by a grid barrier: the k/2 rotations of the round, then
-// their application to G and V.  The barrier is a counter plus a generation word
-// in global memory; every wait is bounded (2 s of %globaltimer), after which the
-// kernel records an error, and all CTAs leave at their next barrier.
-struct GridSync {
-  unsigned count;
-  unsigned gen;
+// ---- Jacobi sweeps with one grid barrier per round ------------------------
+// A rotation of pair (p, q), p < q, is (c, s, e) with c, s real and |e| = 1:
+// J = [[c, s], [-s e, c e]] on columns (p, q); G <- J^* G J and V <- V J.
+struct Rot {
+  double c, s, er, ei;
 };
-__device__ __forceinline__ unsigned long long gtimer_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
+
+// position of index x in round r (inverse of the pairing in jpair)
+__device__ __forceinline__ int jpos(int x, int r, int k) {
+  if (x == 0) return 0;
+  int t = (x - 1 - r) % (k - 1);
+  if (t < 0) t += k - 1;
+  return t + 1;
 }
-__device__ bool grid_barrier(GridSync* gsync, int* err) {
-  __shared__ int ok_sh;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    ok_sh = 1;
-    volatile unsigned* gen = &gsync->gen;
-    const unsigned my_gen = *gen;
-    __threadfence();
-    const unsigned arrived = atomicAdd(&gsync->count, 1u);
-    if (arrived == gridDim.x - 1) {
-      atomicExch(&gsync->count, 0u);
-      __threadfence();
-      atomicAdd(&gsync->gen, 1u);
-    } else {
-      const unsigned long long t0 = gtimer_ns();
-      while (*gen == my_gen) {
-        if (*(volatile int*)err) { ok_sh = 0; break; }
-        if (gtimer_ns() - t0 > 2000000000ull) {
-          atomicExch(err, 1);
-          ok_sh = 0;
-          break;
-        }
-        __nanosleep(64);
-      }
-    }
-    __threadfence();
-    if (*(volatile int*)err) ok_sh = 0;
-  }
-  __syncthreads();
-  return ok_sh != 0;
+__device__ __forceinline__ int jat(int pos, int r, int k) { return pos == 0 ? 0 : ((pos - 1 + r) % (k - 1)) + 1; }
+
+__device__ __forceinline__ void jpair32(int slot, int r, int k, int& p, int& q) {
+  const int a = jat(slot, r, k), b = jat(k - 1 - slot, r, k);
+  p = a < b ? a : b;
+  q = a < b ? b : a;
 }
 
-__global__ void jacobi_sweep_kernel(cplx* G, cplx* V, int64_t k, cplx* rot, const double* red, int* applied,
+// 2^-E for a normal m = f 2^E, f in [1, 2) (exact power of two, from the bits)
+__device__ __forceinline__ double pow2_inv_exp(double m) {
+  const int e = (__double2hiint(m) >> 20) & 0x7ff;
+  return __hiloint2double((2046 - e) << 20, 0);
+}
+// Thresholds of the Jacobi rotations, evaluated once per pair in FP32 on values
+// scaled by sn = 2^-E(||G||_F) (all entries are then at most 1 in magnitude):
+// rotate when |a_pq| > 2e-16 sqrt|a_pp a_qq| and |a_pq| > 1e-16 ||G||_F.  The
+// sweeps and the convergence count use this same predicate.
+__device__ __forceinline__ bool jacobi_active(double app, double aqq, cplx apq, double sn, float n2s) {
+  const float xr = (float)(apq.x * sn), xi = (float)(apq.y * sn);
+  const float a1 = (float)(app * sn), a2 = (float)(aqq * sn);
+  const float r2 = fmaf(xr, xr, xi * xi);
+  return r2 > 4e-32f * fabsf(a1 * a2) && r2 > 1e-32f * n2s && r2 > 0.0f;
+}
+
+// Rotation annihilating a_pq (identity below the thresholds).  GB300 issues an
+// FP64 warp instruction at 1/64 of the FP32 rate, so the serial chain is kept
+// short: t = tan(angle) from an FP32 estimate plus one Newton step on
+// t^2 + 2 tau t - 1 = 0 (FP64 class), and c = (1 + t^2)^(-1/2) and 1/|a_pq| from
+// FP32 reciprocal square roots refined by two FP64 Newton steps, so that
+// c^2 + s^2 = 1 and |e| = 1 hold to FP64 rounding.  a_pq is first scaled by an
+// exact power of two to magnitude in [1, 2).
+__device__ Rot jacobi_rotation(double app, double aqq, cplx apq, double sn, float n2s, int* applied) {
+  Rot R{1.0, 0.0, 1.0, 0.0};
+  if (!jacobi_active(app, aqq, apq, sn, n2s)) return R;
+  atomicAdd(applied, 1);
+  const double sc = pow2_inv_exp(fmax(fabs(apq.x), fabs(apq.y)));
+  const double xr = apq.x * sc, xi = apq.y * sc;
+  const double r2 = fma(xr, xr, xi * xi);  // in [1, 8)
+  double ri = (double)rsqrtf((float)r2);   // 1 / (sc |a_pq|)
+  ri = ri * fma(-0.5 * r2, ri * ri, 1.5);
+  ri = ri * fma(-0.5 * r2, ri * ri, 1.5);
+  R.er = xr * ri;  // e = conj(a_pq) / |a_pq|
+  R.ei = -xi * ri;
+  const double tau = 0.5 * (aqq - app) * ri * sc;  // (a_qq - a_pp) / (2 |a_pq|), below ~1e16
+  const float tf = (float)tau;
+  double t = (double)(copysignf(1.0f, tf) / (fabsf(tf) + sqrtf(fmaf(tf, tf, 1.0f))));
+  if (fabs(tau) < 1e15) {
+    const double f = fma(t, t + 2.0 * tau, -1.0);
+    t -= f * (double)(1.0f / (float)(2.0 * (t + tau)));
+  }
+  const double h = fma(t, t, 1.0);
+  double c = (double)rsqrtf((float)h);
+  c = c * fma(-0.5 * h, c * c, 1.5);
+  c = c * fma(-0.5 * h, c * c, 1.5);
+  R.c = c;
+  R.s = t * c;
+  return R;
+}
+
+// rotations written by other CTAs earlier in the same launch: read through L2
+__device__ __forceinline__ Rot ld_rot(const Rot* r) {
+  const double2 u = __ldcg(reinterpret_cast<const double2*>(r));
+  const double2 v = __ldcg(reinterpret_cast<const double2*>(r) + 1);
+  return Rot{u.x, u.y, v.x, v.y};
+}
+
+// Z = A^* X B for the 2 x 2 block X of rows (pa, qa) and columns (pb, qb).
+__device__ __forceinline__ void rot_block(const Rot& A, const Rot& B, const cplx x[4], cplx z[4]) {
+  const cplx ea = mk(A.er, -A.ei);  // conj(e_A)
+  const cplx w0 = cmul(ea, x[2]), w1 = cmul(ea, x[3]);
+  const cplx y00 = mk(A.c * x[0].x - A.s * w0.x, A.c * x[0].y - A.s * w0.y);
+  const cplx y01 = mk(A.c * x[1].x - A.s * w1.x, A.c * x[1].y - A.s * w1.y);
+  const cplx y10 = mk(A.s * x[0].x + A.c * w0.x, A.s * x[0].y + A.c * w0.y);
+  const cplx y11 = mk(A.s * x[1].x + A.c * w1.x, A.s * x[1].y + A.c * w1.y);
+  const cplx eb = mk(B.er, B.ei);
+  const cplx u0 = cmul(y01, eb), u1 = cmul(y11, eb);
+  z[0] = mk(B.c * y00.x - B.s * u0.x, B.c * y00.y - B.s * u0.y);
+  z[1] = mk(B.s * y00.x + B.c * u0.x, B.s * y00.y + B.c * u0.y);
+  z[2] = mk(B.c * y10.x - B.s * u1.x, B.c * y10.y - B.s * u1.y);
+  z[3] = mk(B.s * y10.x + B.c * u1.x, B.s * y10.y + B.c * u1.y);
+}
+// Diagonal entry i (0: p, 1: q) of J^* X J for the hermitian diagonal block X of (p, q):
+// c^2 x_pp + s^2 x_qq -+ 2 c s Re(e x_pq).
+__device__ __forceinline__ double rot_diag(const Rot& A, const cplx* G, int k, int p, int q, int i) {
+  const double xpp = __ldcg(G + p + (int64_t)p * k).x, xqq = __ldcg(G + q + (int64_t)q * k).x;
+  if (A.s == 0.0) return i == 0 ? xpp : xqq;
+  const cplx xpq = __ldcg(G + p + (int64_t)q * k);
+  const double re = A.er * xpq.x - A.ei * xpq.y;  // Re(e x_pq)
+  const double cc = A.c * A.c, ss = A.s * A.s, cs2 = 2.0 * A.c * A.s;
+  return i == 0 ? fma(cc, xpp, fma(ss, xqq, -cs2 * re)) : fma(ss, xpp, fma(cc, xqq, cs2 * re));
+}
+__device__ __forceinline__ void load_block(const cplx* G, int k, int p0, int q0, int p1, int q1, cplx x[4]) {
+  x[0] = __ldcg(G + p0 + (int64_t)p1 * k);
+  x[1] = __ldcg(G + p0 + (int64_t)q1 * k);
+  x[2] = __ldcg(G + q0 + (int64_t)p1 * k);
+  x[3] = __ldcg(G + q0 + (int64_t)q1 * k);
+}
+
+// One sweep (k - 1 rounds) on G, ping-ponging between Ga (input) and Gb; the
+// rotations of every round go to rots[r * k/2 + slot] for the V pass.  Round r
+// updates the 2 x 2 blocks (a, b), a >= b, of the pairs of slots a and b (and
+// writes the mirrored block); the thread whose block holds the pivot a_xy of a
+// pair of round r + 1 also recomputes the two new diagonal entries and writes
+// that pair's rotation, so each round needs one grid barrier.
+__global__ void jacobi_sweep_kernel(cplx* Ga, cplx* Gb, int k, Rot* rots, const double* red, int* applied,
                                     GridSync* gsync, int* err) {
-  const int64_t half = k / 2;
+  const int half = k / 2;
+  const int64_t nblk = (int64_t)half * (half + 1) / 2;
   const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const double normG = sqrt(red[1]);
-  const int64_t nG = half * half, nV = k * half;
+  const double sn = pow2_inv_exp(normG);
+  const float n2s = (float)((normG * sn) * (normG * sn));
+  // items interleaved over the CTAs: the FP64 work spreads over all SMs
+  const int64_t first = (int64_t)threadIdx.x * gridDim.x + blockIdx.x;
+  for (int64_t sl = first; sl < half; sl += nthreads) {
+    int p, q;
+    jpair32((int)sl, 0, k, p, q);
+    rots[sl] = jacobi_rotation(__ldcg(Ga + p + (int64_t)p * k).x, __ldcg(Ga + q + (int64_t)q * k).x,
+                               __ldcg(Ga + p + (int64_t)q * k), sn, n2s, applied);
+  }
+  if (!grid_barrier(gsync, err)) return;
   for (int r = 0; r < k - 1; ++r) {
-    for (int64_t slot = tid; slot < half; slot += nthreads) {
-      int64_t p, q;
-      jpair(slot, r, k, p, q);
-      const double app = __ldcg(G + p + p * k).x, aqq = __ldcg(G + q + q * k).x;
-      const cplx apq = __ldcg(G + p + q * k);
-      const double rr = hypot(apq.x, apq.y);
-      cplx J00 = mk(1, 0), J01 = mk(0, 0), J10 = mk(0, 0), J11 = mk(1, 0);
-      if (rr > 2e-16 * sqrt(fabs(app * aqq)) && rr > 1e-16 * normG && rr > 1e-300) {
-        atomicAdd(applied, 1);
-        const cplx ec = mk(apq.x / rr, -apq.y / rr);
-        const double tau = (aqq - app) / (2.0 * rr);
-        const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + hypot(1.0, tau));
-        const double c = 1.0 / hypot(1.0, t), sn = t * c;
-        J00 = mk(c, 0);
-        J01 = mk(sn, 0);
-        J10 = cscale(ec, -sn);
-        J11 = cscale(ec, c);
-      }
-      rot[4 * slot + 0] = J00;
-      rot[4 * slot + 1] = J01;
-      rot[4 * slot + 2] = J10;
-      rot[4 * slot + 3] = J11;
-    }
-    if (!grid_barrier(gsync, err)) return;
-    for (int64_t item = tid; item < nG + nV; item += nthreads) {
-      if (item < nG) {
-        const int64_t a = item % half, b = item / half;
-        int64_t pa, qa, pb, qb;
-        jpair(a, r, k, pa, qa);
-        jpair(b, r, k, pb, qb);
-        const cplx A00 = __ldcg(rot + 4 * a), A01 = __ldcg(rot + 4 * a + 1), A10 = __ldcg(rot + 4 * a + 2),
-                   A11 = __ldcg(rot + 4 * a + 3);
-        const cplx B00 = __ldcg(rot + 4 * b), B01 = __ldcg(rot + 4 * b + 1), B10 = __ldcg(rot + 4 * b + 2),
-                   B11 = __ldcg(rot + 4 * b + 3);
-        const cplx x00 = __ldcg(G + pa + pb * k), x01 = __ldcg(G + pa + qb * k), x10 = __ldcg(G + qa + pb * k),
-                   x11 = __ldcg(G + qa + qb * k);
-        const cplx y00 = cadd(cmul(cconj(A00), x00), cmul(cconj(A10), x10));
-        const cplx y01 = cadd(cmul(cconj(A00), x01), cmul(cconj(A10), x11));
-        const cplx y10 = cadd(cmul(cconj(A01), x00), cmul(cconj(A11), x10));
-        const cplx y11 = cadd(cmul(cconj(A01), x01), cmul(cconj(A11), x11));
-        G[pa + pb * k] = cadd(cmul(y00, B00), cmul(y01, B10));
-        G[pa + qb * k] = cadd(cmul(y00, B01), cmul(y01, B11));
-        G[qa + pb * k] = cadd(cmul(y10, B00), cmul(y11, B10));
-        G[qa + qb * k] = cadd(cmul(y10, B01), cmul(y11, B11));
+    const cplx* Gi = (r & 1) ? Gb : Ga;
+    cplx* Go = (r & 1) ? Ga : Gb;
+    const Rot* R = rots + (int64_t)r * half;
+    for (int64_t item = first; item < nblk; item += nthreads) {
+      int a = (int)((sqrtf(8.0f * (float)item + 1.0f) - 1.0f) * 0.5f);
+      while ((int64_t)a * (a + 1) / 2 > item) --a;
+      while ((int64_t)(a + 1) * (a + 2) / 2 <= item) ++a;
+      const int b = (int)(item - (int64_t)a * (a + 1) / 2);
+      int pa, qa, pb, qb;
+      jpair32(a, r, k, pa, qa);
+      jpair32(b, r, k, pb, qb);
+      const Rot A = ld_rot(R + a), B = ld_rot(R + b);
+      cplx x[4], z[4];
+      load_block(Gi, k, pa, qa, pb, qb, x);
+      if (A.s == 0.0 && B.s == 0.0) {
+        z[0] = x[0]; z[1] = x[1]; z[2] = x[2]; z[3] = x[3];
       } else {
-        const int64_t it = item - nG;
-        const int64_t i = it % k, b = it / k;
-        int64_t pb, qb;
-        jpair(b, r, k, pb, qb);
-        const cplx B00 = __ldcg(rot + 4 * b), B01 = __ldcg(rot + 4 * b + 1), B10 = __ldcg(rot + 4 * b + 2),
-                   B11 = __ldcg(rot + 4 * b + 3);
-        const cplx v0 = __ldcg(V + i + pb * k), v1 = __ldcg(V + i + qb * k);
-        V[i + pb * k] = cadd(cmul(v0, B00), cmul(v1, B10));
-        V[i + qb * k] = cadd(cmul(v0, B01), cmul(v1, B11));
+        rot_block(A, B, x, z);
+      }
+      Go[pa + (int64_t)pb * k] = z[0];
+      Go[pa + (int64_t)qb * k] = z[1];
+      Go[qa + (int64_t)pb * k] = z[2];
+      Go[qa + (int64_t)qb * k] = z[3];
+      if (a == b) continue;
+      Go[pb + (int64_t)pa * k] = cconj(z[0]);
+      Go[qb + (int64_t)pa * k] = cconj(z[1]);
+      Go[pb + (int64_t)qa * k] = cconj(z[2]);
+      Go[qb + (int64_t)qa * k] = cconj(z[3]);
+      if (r + 1 >= k - 1) continue;
+#pragma unroll
+      for (int ix = 0; ix < 2; ++ix) {
+        const int xi = ix == 0 ? pa : qa;
+        const int pos = jpos(xi, r + 1, k);
+        const int yi = jat(k - 1 - pos, r + 1, k);
+        if (yi != pb && yi != qb) continue;
+        const int iy = (yi == pb) ? 0 : 1;
+        const cplx zxy = z[2 * ix + iy];
+        const double dx = rot_diag(A, Gi, k, pa, qa, ix), dy = rot_diag(B, Gi, k, pb, qb, iy);
+        const int slot = pos < k - 1 - pos ? pos : k - 1 - pos;
+        rots[(int64_t)(r + 1) * half + slot] =
+            xi < yi ? jacobi_rotation(dx, dy, zxy, sn, n2s, applied) : jacobi_rotation(dy, dx, cconj(zxy), sn, n2s, applied);
       }
     }
     if (!grid_barrier(gsync, err)) return;
   }
+}
+
+// V <- V J_0 J_1 ... J_{k-2} for the stored rotations of one sweep: one warp per
+// row of V (rows are independent), the row in shared memory.
+constexpr int VROWS = 2;
+__global__ void jacobi_vpass_kernel(cplx* V, int k, const Rot* rots) {
+  extern __shared__ cplx vrow[];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * VROWS + w;
+  if (i >= k) return;  // whole warp; no block-wide synchronisation below
+  cplx* v = vrow + (int64_t)w * k;
+  for (int j = lane; j < k; j += 32) v[j] = V[i + (int64_t)j * k];
+  __syncwarp();
+  const int half = k / 2;
+  for (int r = 0; r < k - 1; ++r) {
+    const Rot* R = rots + (int64_t)r * half;
+    for (int sl = lane; sl < half; sl += 32) {
+      const Rot B = R[sl];
+      if (B.s == 0.0) continue;  // identity
+      int p, q;
+      jpair32(sl, r, k, p, q);
+      const cplx vp = v[p], u = cmul(v[q], mk(B.er, B.ei));
+      v[p] = mk(B.c * vp.x - B.s * u.x, B.c * vp.y - B.s * u.y);
+      v[q] = mk(B.s * vp.x + B.c * u.x, B.s * vp.y + B.c * u.y);
+    }
+    __syncwarp();
+  }
+  for (int j = lane; j < k; j += 32) V[i + (int64_t)j * k] = v[j];
+}
+
+// Number of pairs p < q that a sweep would rotate (the thresholds of jacobi_rotation).
+__global__ void jacobi_count_kernel(const cplx* G, int k, const double* red, int* count) {
+  const double normG = sqrt(red[1]);
+  const double sn = pow2_inv_exp(normG);
+  const float n2s = (float)((normG * sn) * (normG * sn));
+  const int64_t total = (int64_t)k * k;
+  int local = 0;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int p = (int)(idx % k), q = (int)(idx / k);
+    if (p >= q) continue;
+    if (jacobi_active(G[p + (int64_t)p * k].x, G[q + (int64_t)q * k].x, G[idx], sn, n2s)) ++local;
+  }
+  if (local) atomicAdd(count, local);
 }
 
 // A non-blocking stream per device, created on first use, for the captured sweeps.
@@ -400,28 +780,48 @@ int jacobi_eigh(cplx* G, int64_t k, cplx* V, double* theta, cplx* rot, double* r
   CB_CUDA(cudaMallocAsync(&applied, sizeof(int), s));
   offdiag_norm_kernel<<<1, 1024, 0, s>>>(G, k, red);  // red[1] = ||G||_F^2 (invariant)
   count_launch();
-  // Preferred: one cooperative launch per sweep.
+  // Preferred: one cooperative launch per sweep (one grid barrier per round),
+  // then the V pass over the stored rotations.
   {
     int dev = 0, sms = 0, per_sm = 0, coop = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_sweep_kernel, 512, 0);
-    const int64_t want = (items + 511) / 512;
-    const int64_t cap = (int64_t)sms * (per_sm < 1 ? per_sm : 1);  // one CTA per SM: fewer barrier arrivals
-    const unsigned grid = (unsigned)(want < cap ? want : cap);
-    if (coop && grid >= 1 && per_sm >= 1) {
+    // one CTA per SM: every SM's FP64 pipe takes part, one barrier arrival each
+    const unsigned grid = (unsigned)(sms > 0 ? sms : 1);
+    const size_t vsmem = sizeof(cplx) * (size_t)VROWS * (size_t)k;
+    if (coop && per_sm >= 1 && k <= (1 << 20) && vsmem <= 200 * 1024) {
+      static bool attr = false;
+      if (!attr) {
+        CB_CUDA(cudaFuncSetAttribute(jacobi_vpass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        attr = true;
+      }
       GridSync* gsync = nullptr;
-      int* err = nullptr;
+      int *err = nullptr, *cnt = nullptr;
+      cplx* G2 = nullptr;
+      Rot* rots = nullptr;
       CB_CUDA(cudaMallocAsync(&gsync, sizeof(GridSync), s));
       CB_CUDA(cudaMallocAsync(&err, sizeof(int), s));
+      CB_CUDA(cudaMallocAsync(&cnt, sizeof(int), s));
+      CB_CUDA(cudaMallocAsync(&G2, sizeof(cplx) * k * k, s));
+      CB_CUDA(cudaMallocAsync(&rots, sizeof(Rot) * (size_t)(k - 1) * half + sizeof(Rot), s));
       CB_CUDA(cudaMemsetAsync(gsync, 0, sizeof(GridSync), s));
       CB_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
-      int happ = 1, herr = 0, status = CHASE_BSE_OK;
-      int64_t kk = k;
-      void* args[] = {&G, &V, &kk, &rot, &red, &applied, &gsync, &err};
-      for (; sweeps < max_sweeps; ++sweeps) {
+      int herr = 0, status = CHASE_BSE_OK;
+      int hc[2] = {1, 1};
+      int ki = (int)k;
+      cplx *Ga = G, *Gb = G2;
+      // a matrix that is diagonal to the thresholds needs no sweep
+      CB_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int), s));
+      jacobi_count_kernel<<<gs(k * k), 256, 0, s>>>(Ga, ki, red, cnt);
+      count_launch();
+      CB_CUDA(cudaMemcpyAsync(&hc[1], cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
+      CB_CUDA(cudaStreamSynchronize(s));
+      for (; hc[1] > 0 && sweeps < max_sweeps; ++sweeps) {
         CB_CUDA(cudaMemsetAsync(applied, 0, sizeof(int), s));
+        CB_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int), s));
+        void* args[] = {&Ga, &Gb, &ki, &rots, &red, &applied, &gsync, &err};
         if (cudaLaunchCooperativeKernel((const void*)jacobi_sweep_kernel, dim3(grid), dim3(512), args, 0, s) !=
             cudaSuccess) {
           cudaGetLastError();
@@ -429,18 +829,25 @@ int jacobi_eigh(cplx* G, int64_t k, cplx* V, double* theta, cplx* rot, double* r
           break;
         }
         count_launch();
-        CB_CUDA(cudaMemcpyAsync(&happ, applied, sizeof(int), cudaMemcpyDeviceToHost, s));
+        jacobi_vpass_kernel<<<(unsigned)((k + VROWS - 1) / VROWS), 32 * VROWS, vsmem, s>>>(V, ki, rots);
+        count_launch();
+        std::swap(Ga, Gb);  // the last round (k - 2, even) wrote Gb
+        jacobi_count_kernel<<<gs(k * k), 256, 0, s>>>(Ga, ki, red, cnt);
+        count_launch();
+        CB_CUDA(cudaMemcpyAsync(&hc[0], applied, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CB_CUDA(cudaMemcpyAsync(&hc[1], cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
         CB_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
         CB_CUDA(cudaStreamSynchronize(s));
         if (herr) {
           status = CHASE_BSE_DEVICE_TIMEOUT;
           break;
         }
-        if (happ == 0) {
-          ++sweeps;
-          break;
-        }
       }
+      if (status == CHASE_BSE_OK && Ga != G)
+        CB_CUDA(cudaMemcpyAsync(G, Ga, sizeof(cplx) * k * k, cudaMemcpyDeviceToDevice, s));
+      cudaFreeAsync(rots, s);
+      cudaFreeAsync(G2, s);
+      cudaFreeAsync(cnt, s);
       cudaFreeAsync(gsync, s);
       cudaFreeAsync(err, s);
       cudaFreeAsync(applied, s);
@@ -591,10 +998,6 @@ int householder_qr(cplx* X, int64_t N, int64_t m, cplx* Q, cplx* Vs, cplx* Us, c
 }
 
 // ----------------------------------------------------------------- utilities
-static inline unsigned gs(int64_t total) {
-  const int64_t b = (total + 255) / 256;
-  return (unsigned)(b < 8192 ? (b > 0 ? b : 1) : 8192);
-}
 #define GRID_STRIDE(i, total) \
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (total); i += (int64_t)gridDim.x * blockDim.x)
 

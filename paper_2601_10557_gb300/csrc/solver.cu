@@ -489,7 +489,7 @@ static int qr_jfixed(const cplx* X, int64_t n, int64_t m, cplx* Q, bool* ok_out,
       const double mn = *std::min_element(dg.begin(), dg.end());
       if (!(mn > 0.0) || (mx / mn) * (mx / mn) > 1e12) return CHASE_BSE_OK;
     }
-    CB_TRY(tri_inverse(G, m, Linv, T, s));
+    CB_TRY(tri_inverse(G, m, Linv, T, s, true));  // the Gram is real
     tm.mark("trinv");
     if (sliced) {
       CB_TRY(slice_complex_rows(src, n, n, m, tmp, sr, s));
