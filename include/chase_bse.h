@@ -210,6 +210,14 @@ const char* chase_bse_strerror(int status);
 int chase_bse_version(void);
 int chase_bse_has_mixed(void);
 
+/* Device memory (no counterpart in the paper): the library allocates its
+ * workspaces stream-ordered from its own memory pool on each device and keeps
+ * freed memory cached for the next allocation (a solve allocates the same
+ * workspaces every iteration).  This call returns the cached memory of the
+ * current device to the driver; memory still in use by a call in flight is
+ * not affected. */
+void chase_bse_trim_memory(void);
+
 /* Diagnostics (no counterpart in the paper): the number of CUDA kernels this
  * library has launched since it was loaded, summed over all threads. */
 int64_t chase_bse_launch_count(void);

@@ -80,7 +80,7 @@ _lib: Optional[ctypes.CDLL] = None
 
 EXPORTS = ["chase_bse_solve", "chase_bse_filter", "chase_bse_rr", "chase_bse_residuals", "chase_bse_grad",
            "chase_bse_strerror", "chase_bse_version", "chase_bse_has_mixed", "chase_bse_launch_count",
-           "chase_bse_residuals_noalloc", "chase_bse_dgemm_sliced"]
+           "chase_bse_residuals_noalloc", "chase_bse_dgemm_sliced", "chase_bse_trim_memory"]
 
 # 2n * k limit of chase_bse_residuals_noalloc (its fixed device scratch, complex128 entries)
 NOALLOC_MAX_ENTRIES = 1 << 19
@@ -107,6 +107,7 @@ def lib() -> ctypes.CDLL:
     L.chase_bse_strerror.argtypes = [ctypes.c_int]
     L.chase_bse_strerror.restype = ctypes.c_char_p
     L.chase_bse_launch_count.restype = ctypes.c_int64
+    L.chase_bse_trim_memory.restype = None
     for name in ["chase_bse_solve", "chase_bse_filter", "chase_bse_rr", "chase_bse_residuals", "chase_bse_grad",
                  "chase_bse_version", "chase_bse_has_mixed", "chase_bse_residuals_noalloc",
                  "chase_bse_dgemm_sliced"]:
@@ -118,6 +119,11 @@ def lib() -> ctypes.CDLL:
 def launch_count() -> int:
     """Kernels launched by the library so far (diagnostics)."""
     return int(lib().chase_bse_launch_count())
+
+
+def trim_memory() -> None:
+    """Return the device memory the library keeps cached between calls to the driver."""
+    lib().chase_bse_trim_memory()
 
 
 def has_mixed() -> bool:

@@ -24,6 +24,8 @@ int64_t chase_bse_launch_count(void) { return cb::launch_count(); }
 
 int chase_bse_has_mixed(void) { return cb::mixed_available() ? 1 : 0; }
 
+void chase_bse_trim_memory(void) { cb::pool_trim(); }
+
 const char* chase_bse_strerror(int status) {
   switch (status) {
     case CHASE_BSE_OK: return "ok";

@@ -58,6 +58,17 @@ int64_t launch_count();
 
 inline unsigned cdiv(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
 
+// Stream-ordered device allocation from the library's memory pool (one per
+// device).  The pool keeps freed memory cached (release threshold: unlimited),
+// so the per-iteration workspaces of a solve reuse their pages instead of
+// mapping new ones; pool_trim() returns the cached memory to the driver.
+cudaError_t dalloc(void** p, size_t bytes, cudaStream_t s);
+template <class T>
+inline cudaError_t dalloc(T** p, size_t bytes, cudaStream_t s) {
+  return dalloc(reinterpret_cast<void**>(p), bytes, s);
+}
+void pool_trim();
+
 // Stream-ordered workspace: every buffer is released when the owner goes out
 // of scope (cudaFreeAsync on the same stream).
 struct Workspace {
@@ -74,7 +85,7 @@ struct Workspace {
     if (elems == 0) elems = 1;
     if (count >= 64) return CHASE_BSE_OOM;
     void* q = nullptr;
-    cudaError_t e = cudaMallocAsync(&q, elems * sizeof(T), s);
+    cudaError_t e = dalloc(&q, elems * sizeof(T), s);
     if (e != cudaSuccess) { cudaGetLastError(); return CHASE_BSE_OOM; }
     ptrs[count++] = q;
     *p = static_cast<T*>(q);

@@ -156,6 +156,18 @@ __global__ void zero_upper_kernel(cplx* G, int64_t k) {
 // takes panel rows (forward substitution against L_JJ^*, as in chol_panel_kernel)
 // and finally tiles of the trailing update A22 -= L21 L21^*, with a grid barrier
 // after each phase.
+// acc - a conj(b); REAL: the operands have zero imaginary parts (4x fewer FP64 instructions)
+template <bool REAL>
+__device__ __forceinline__ cplx msub_conj(cplx acc, cplx a, cplx b) {
+  if (REAL) return mk(fma(-a.x, b.x, acc.x), 0.0);
+  return csub(acc, cmul(a, cconj(b)));
+}
+template <bool REAL>
+__device__ __forceinline__ cplx scale_re(cplx a, double s) {
+  return REAL ? mk(a.x * s, 0.0) : cscale(a, s);
+}
+
+template <bool REAL>
 __global__ void chol_coop_kernel(cplx* G, int64_t k, int* info, GridSync* gsync, int* err) {
   __shared__ cplx buf[2][NB][NB + 1];
   auto& a = buf[0];   // diagonal block (phases 1, 2)
@@ -186,12 +198,12 @@ __global__ void chol_coop_kernel(cplx* G, int64_t k, int* info, GridSync* gsync,
         }
         __syncthreads();
         const double inv = dinv[c];
-        for (int r = c + 1 + t; r < jb; r += blockDim.x) a[r][c] = cscale(a[r][c], inv);
+        for (int r = c + 1 + t; r < jb; r += blockDim.x) a[r][c] = scale_re<REAL>(a[r][c], inv);
         __syncthreads();
         const int m = jb - c - 1;
         for (int idx = t; idx < m * m; idx += blockDim.x) {
           const int r = c + 1 + idx % m, q = c + 1 + idx / m;
-          if (q <= r) a[r][q] = csub(a[r][q], cmul(a[r][c], cconj(a[q][c])));
+          if (q <= r) a[r][q] = msub_conj<REAL>(a[r][q], a[r][c], a[q][c]);
         }
         __syncthreads();
       }
@@ -222,8 +234,8 @@ __global__ void chol_coop_kernel(cplx* G, int64_t k, int* info, GridSync* gsync,
             cplx v = x[c];
 #pragma unroll
             for (int q = 0; q < NB; ++q)
-              if (q < c) v = csub(v, cmul(x[q], cconj(a[c][q])));
-            x[c] = cscale(v, dinv[c]);
+              if (q < c) v = msub_conj<REAL>(v, x[q], a[c][q]);
+            x[c] = scale_re<REAL>(v, dinv[c]);
           }
         }
 #pragma unroll
@@ -251,7 +263,7 @@ __global__ void chol_coop_kernel(cplx* G, int64_t k, int* info, GridSync* gsync,
           const int r = idx % ib, c = idx / ib;
           if (I == K && c > r) continue;
           cplx acc = __ldcg(G + (i0 + r) + (c0 + c) * k);
-          for (int q = 0; q < jb; ++q) acc = csub(acc, cmul(pi[r][q], cconj(pk[c][q])));
+          for (int q = 0; q < jb; ++q) acc = msub_conj<REAL>(acc, pi[r][q], pk[c][q]);
           G[(i0 + r) + (c0 + c) * k] = acc;
         }
       }
@@ -271,19 +283,20 @@ static int coop_grid(const void* kern, int threads, int* grid_out) {
   return 1;
 }
 
-int cholesky(cplx* G, int64_t k, int* info_dev, int* info_host, cudaStream_t s) {
+int cholesky(cplx* G, int64_t k, int* info_dev, int* info_host, cudaStream_t s, bool real) {
   CB_CUDA(cudaMemsetAsync(info_dev, 0, sizeof(int), s));
   int grid = 0;
-  if (coop_grid((const void*)chol_coop_kernel, 256, &grid)) {
+  const void* kern = real ? (const void*)chol_coop_kernel<true> : (const void*)chol_coop_kernel<false>;
+  if (coop_grid(kern, 256, &grid)) {
     GridSync* gsync = nullptr;
     int* err = nullptr;
-    CB_CUDA(cudaMallocAsync(&gsync, sizeof(GridSync), s));
-    CB_CUDA(cudaMallocAsync(&err, sizeof(int), s));
+    CB_CUDA(dalloc(&gsync, sizeof(GridSync), s));
+    CB_CUDA(dalloc(&err, sizeof(int), s));
     CB_CUDA(cudaMemsetAsync(gsync, 0, sizeof(GridSync), s));
     CB_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
     int64_t kk = k;
     void* args[] = {&G, &kk, &info_dev, &gsync, &err};
-    const cudaError_t le = cudaLaunchCooperativeKernel((const void*)chol_coop_kernel, dim3(grid), dim3(256), args, 0, s);
+    const cudaError_t le = cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(256), args, 0, s);
     if (le != cudaSuccess) cudaGetLastError();
     count_launch();
     zero_upper_kernel<<<cdiv(k * k, 256) < 4096 ? cdiv(k * k, 256) : 4096, 256, 0, s>>>(G, k);
@@ -777,7 +790,7 @@ int jacobi_eigh(cplx* G, int64_t k, cplx* V, double* theta, cplx* rot, double* r
   const unsigned gapply = (unsigned)((items + 255) / 256 < 2048 ? (items + 255) / 256 : 2048);
   double hred[2] = {0, 0};
   int* applied = nullptr;
-  CB_CUDA(cudaMallocAsync(&applied, sizeof(int), s));
+  CB_CUDA(dalloc(&applied, sizeof(int), s));
   offdiag_norm_kernel<<<1, 1024, 0, s>>>(G, k, red);  // red[1] = ||G||_F^2 (invariant)
   count_launch();
   // Preferred: one cooperative launch per sweep (one grid barrier per round),
@@ -801,11 +814,11 @@ int jacobi_eigh(cplx* G, int64_t k, cplx* V, double* theta, cplx* rot, double* r
       int *err = nullptr, *cnt = nullptr;
       cplx* G2 = nullptr;
       Rot* rots = nullptr;
-      CB_CUDA(cudaMallocAsync(&gsync, sizeof(GridSync), s));
-      CB_CUDA(cudaMallocAsync(&err, sizeof(int), s));
-      CB_CUDA(cudaMallocAsync(&cnt, sizeof(int), s));
-      CB_CUDA(cudaMallocAsync(&G2, sizeof(cplx) * k * k, s));
-      CB_CUDA(cudaMallocAsync(&rots, sizeof(Rot) * (size_t)(k - 1) * half + sizeof(Rot), s));
+      CB_CUDA(dalloc(&gsync, sizeof(GridSync), s));
+      CB_CUDA(dalloc(&err, sizeof(int), s));
+      CB_CUDA(dalloc(&cnt, sizeof(int), s));
+      CB_CUDA(dalloc(&G2, sizeof(cplx) * k * k, s));
+      CB_CUDA(dalloc(&rots, sizeof(Rot) * (size_t)(k - 1) * half + sizeof(Rot), s));
       CB_CUDA(cudaMemsetAsync(gsync, 0, sizeof(GridSync), s));
       CB_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
       int herr = 0, status = CHASE_BSE_OK;
@@ -1119,6 +1132,27 @@ int pair_apply(const cplx* Zp, cplx* Z, int64_t k, int64_t h, cudaStream_t s) {
   return CHASE_BSE_OK;
 }
 
+// out = in^* (k x k, column-major)
+__global__ void conj_transpose_kernel(const cplx* in, int64_t k, cplx* out) {
+  __shared__ cplx tile[32][33];
+  const int64_t r0 = (int64_t)blockIdx.x * 32, c0 = (int64_t)blockIdx.y * 32;
+  for (int j = threadIdx.y; j < 32; j += 8) {
+    const int64_t r = r0 + threadIdx.x, c = c0 + j;
+    if (r < k && c < k) tile[j][threadIdx.x] = in[r + c * k];
+  }
+  __syncthreads();
+  for (int j = threadIdx.y; j < 32; j += 8) {
+    const int64_t r = c0 + threadIdx.x, c = r0 + j;  // out[r, c] = conj(in[c, r])
+    if (r < k && c < k) out[r + c * k] = cconj(tile[threadIdx.x][j]);
+  }
+}
+int conj_transpose(const cplx* in, int64_t k, cplx* out, cudaStream_t s) {
+  if (k == 0) return CHASE_BSE_OK;
+  conj_transpose_kernel<<<dim3(cdiv(k, 32), cdiv(k, 32)), dim3(32, 8), 0, s>>>(in, k, out);
+  count_launch();
+  CB_LAUNCH();
+  return CHASE_BSE_OK;
+}
 __global__ void re_im_part_kernel(const cplx* C, cplx* out, int64_t k, int mode) {
   GRID_STRIDE(i, k * k) { out[i] = (mode == 0) ? mk(2.0 * C[i].x, 0.0) : mk(0.0, 2.0 * C[i].y); }
 }

@@ -8,8 +8,9 @@ namespace cb {
 
 // Blocked Cholesky G = L L^* in place (lower triangle; strict upper zeroed).
 // *info_host = 0 on success, j+1 if the j-th pivot is not positive (or NaN).
-int cholesky(cplx* G, int64_t k, int* info_dev, int* info_host, cudaStream_t s);
+int cholesky(cplx* G, int64_t k, int* info_dev, int* info_host, cudaStream_t s, bool real = false);
 // X = L^{-1} for lower-triangular L (k x k); T is k*32 complex scratch.
+int conj_transpose(const cplx* in, int64_t k, cplx* out, cudaStream_t s);
 int tri_inverse(const cplx* L, int64_t k, cplx* X, cplx* T, cudaStream_t s, bool real = false);
 
 // Cyclic Jacobi on hermitian G (k x k, k even, overwritten by its diagonal form);

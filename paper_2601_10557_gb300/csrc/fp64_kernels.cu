@@ -175,7 +175,7 @@ static int hop_launch(const HopArgs& a, cudaStream_t s) {
   const int64_t kchunk = ((n2 + nsplit - 1) / nsplit + 15) / 16 * 16;
   const int64_t ns = (n2 + kchunk - 1) / kchunk;
   cplx* part = nullptr;
-  CB_CUDA(cudaMallocAsync(&part, sizeof(cplx) * ns * 2 * a.n * a.k, s));
+  CB_CUDA(dalloc(&part, sizeof(cplx) * ns * 2 * a.n * a.k, s));
   dim3 grid(cdiv(a.n, BM), cdiv(a.k, BNW), (unsigned)ns);
   hop_kernel<BM, BNW, TM, TNW, 16><<<grid, (BM / TM) * (BNW / TNW), 0, s>>>(a, part, kchunk);
   count_launch();
@@ -278,7 +278,7 @@ int hop_top_fp64(const cplx* A, const cplx* B, int64_t n, const cplx* X, int64_t
   const int64_t kchunk = ((n2 + nsplit - 1) / nsplit + 15) / 16 * 16;
   const int64_t ns = (n2 + kchunk - 1) / kchunk;
   cplx* part = nullptr;
-  CB_CUDA(cudaMallocAsync(&part, sizeof(cplx) * ns * n * k, s));
+  CB_CUDA(dalloc(&part, sizeof(cplx) * ns * n * k, s));
   grid.z = (unsigned)ns;
   hop_top_kernel<BM, BNW, TM, TNW, 16><<<grid, 256, 0, s>>>(A, B, n, X, k, Y, part, kchunk);
   count_launch();
@@ -406,7 +406,7 @@ static int zgemm_launch(char opA, char opB, int64_t M, int64_t N, int64_t K, cpl
   const int64_t kchunk = ((K + nsplit - 1) / nsplit + 7) / 8 * 8;
   const int64_t ns = (K + kchunk - 1) / kchunk;
   cplx* part = nullptr;
-  CB_CUDA(cudaMallocAsync(&part, sizeof(cplx) * ns * M * N, s));
+  CB_CUDA(dalloc(&part, sizeof(cplx) * ns * M * N, s));
   grid.z = (unsigned)ns;
   zgemm_kernel<BM, BN, TM, TN, 8><<<grid, 256, 0, s>>>(opA, opB, M, N, K, alpha, A, lda, B, ldb, beta, part, M,
                                                        kchunk);

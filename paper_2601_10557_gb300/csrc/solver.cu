@@ -6,6 +6,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <numeric>
+#include <mutex>
 #include <vector>
 
 #include "dense_kernels.cuh"
@@ -14,6 +15,44 @@
 #include "tc_dgemm.cuh"
 
 namespace cb {
+
+namespace {
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[64] = {};
+}  // namespace
+
+cudaError_t dalloc(void** p, size_t bytes, cudaStream_t s) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaMallocAsync(p, bytes, s);
+  cudaMemPool_t pool;
+  {
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    if (!g_pools[dev]) {
+      cudaMemPoolProps props{};
+      props.allocType = cudaMemAllocationTypePinned;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = dev;
+      e = cudaMemPoolCreate(&g_pools[dev], &props);
+      if (e != cudaSuccess) {
+        g_pools[dev] = nullptr;
+        return e;
+      }
+      uint64_t thr = UINT64_MAX;
+      cudaMemPoolSetAttribute(g_pools[dev], cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    pool = g_pools[dev];
+  }
+  return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
+
+void pool_trim() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+  std::lock_guard<std::mutex> lock(g_pool_mu);
+  if (g_pools[dev]) cudaMemPoolTrimTo(g_pools[dev], 0);
+}
 
 static std::atomic<int64_t> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
@@ -478,7 +517,7 @@ static int qr_jfixed(const cplx* X, int64_t n, int64_t m, cplx* Q, bool* ok_out,
     }
     tm.mark("gram");
     int info = 0;
-    CB_TRY(cholesky(G, m, info_d, &info, s));
+    CB_TRY(cholesky(G, m, info_d, &info, s, true));  // the Gram is real
     tm.mark("chol");
     if (info != 0) return CHASE_BSE_OK;
     if (pass == 0) {
@@ -536,7 +575,7 @@ static int rayleigh_ritz_jfixed(const cplx* A, const cplx* B, int64_t n, const c
     CB_TRY(sliced_alloc(ws, sta, 2 * n, 2 * k, s));  // real-form rows of T
     CB_TRY(sliced_alloc(ws, sz, h, 2 * k, s));       // columns of Z
     CB_TRY(sliced_alloc(ws, szc, h, 2 * k, s));      // columns of conj(Z)
-    CB_TRY(ws.alloc(&tmp, 4 * n * k));
+    CB_TRY(ws.alloc(&tmp, 4 * (n > k ? n : k) * k));  // real-form rows of an n x k or k x k block
   } else {
     CB_TRY(ws.alloc(&Qc, n * k));
     CB_TRY(ws.alloc(&Tc, n * k));
@@ -583,8 +622,20 @@ static int rayleigh_ritz_jfixed(const cplx* A, const cplx* B, int64_t n, const c
   }
   CB_TRY(pair_transform(Tmp, M2, k, s));
   // line 7: G = L^{-1} M2 L^{-*}
-  CB_TRY(zgemm('N', 'N', k, k, k, mk(1, 0), Linv, k, M2, k, mk(0, 0), Tmp, k, s));
-  CB_TRY(zgemm('N', 'C', k, k, k, mk(1, 0), Tmp, k, Linv, k, mk(0, 0), G, k, s));
+  SlicedOp sl_rows, sl_b;  // real-form rows of a k x k factor, and the right operand
+  if (sliced) {
+    CB_TRY(sliced_alloc(ws, sl_rows, 2 * k, 2 * k, s));
+    CB_TRY(sliced_alloc(ws, sl_b, k, 2 * k, s));
+    CB_TRY(slice_complex_rows(Linv, k, k, k, tmp, sl_rows, s));
+    CB_TRY(slice_rows(reinterpret_cast<const double*>(M2), 2 * k, 0, sl_b, s));
+    CB_TRY(sliced_gemm(sl_rows, sl_b, 1.0, reinterpret_cast<double*>(Tmp), 1, 2 * k, false, s));
+    CB_TRY(slice_complex_rows(Tmp, k, k, k, tmp, sl_rows, s));
+    CB_TRY(slice_conj_rows(Linv, k, sl_b, s));
+    CB_TRY(sliced_gemm(sl_rows, sl_b, 1.0, reinterpret_cast<double*>(G), 1, 2 * k, false, s));
+  } else {
+    CB_TRY(zgemm('N', 'N', k, k, k, mk(1, 0), Linv, k, M2, k, mk(0, 0), Tmp, k, s));
+    CB_TRY(zgemm('N', 'C', k, k, k, mk(1, 0), Tmp, k, Linv, k, mk(0, 0), G, k, s));
+  }
   CB_TRY(hermitize(G, k, s));
   tm.mark("small");
   int sweeps = 0;
@@ -604,7 +655,16 @@ static int rayleigh_ritz_jfixed(const cplx* A, const cplx* B, int64_t n, const c
   CB_TRY(gather_cols(Ypos, V, idx_d, k, h, s));
   // line 9 (z = L^{-*} y), back to the J-fixed basis (Z = U Z');
   // W+ = Q Z+ = [X Z; conj(X) Z]; S H W+ = [Y Z; conj(Y) Z]
-  CB_TRY(zgemm('C', 'N', k, h, k, mk(1, 0), Linv, k, Ypos, k, mk(0, 0), Tmp, k, s));
+  if (sliced) {  // Tmp = L^{-*} Y+: rows of L^{-*} are the conjugated columns of L^{-1}
+    CB_TRY(conj_transpose(Linv, k, M2, s));
+    CB_TRY(slice_complex_rows(M2, k, k, k, tmp, sl_rows, s));
+    SlicedOp sy;
+    CB_TRY(sliced_alloc(ws, sy, h, 2 * k, s));
+    CB_TRY(slice_rows(reinterpret_cast<const double*>(Ypos), 2 * k, 0, sy, s));
+    CB_TRY(sliced_gemm(sl_rows, sy, 1.0, reinterpret_cast<double*>(Tmp), 1, 2 * k, false, s));
+  } else {
+    CB_TRY(zgemm('C', 'N', k, h, k, mk(1, 0), Linv, k, Ypos, k, mk(0, 0), Tmp, k, s));
+  }
   CB_TRY(pair_apply(Tmp, Z, k, h, s));
   if (sliced) {  // conj(X) Z = conj(X conj(Z)): the conjugated halves negate the odd (imaginary) rows
     CB_TRY(slice_rows(reinterpret_cast<const double*>(Z), 2 * k, 0, sz, s));
@@ -778,6 +838,9 @@ int solve(const cplx* A, const cplx* B, int64_t n, int64_t nev, int64_t nex, int
   clk.start();
   double mu[4];
   CB_TRY(lanczos_bounds(A, B, n, V0, o.lanczos_vecs, o.lanczos_steps, nevex, mu, s));
+  if (verbose())
+    fprintf(stderr, "[chase_bse] setup wall %.2f ms\n",
+            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count());
   st.ms_lanczos = clk.stop();
   double mu1 = mu[0], mu_ne = mu[1], muN = mu[2];
   const double rhat = mu[3];
@@ -793,6 +856,8 @@ int solve(const cplx* A, const cplx* B, int64_t n, int64_t nev, int64_t nex, int
   int status = CHASE_BSE_OK;
   while (locked < nev && it < o.maxiter) {
     ++it;
+    const auto it_start = std::chrono::steady_clock::now();
+    const double ph0 = st.ms_filter + st.ms_qr + st.ms_rr + st.ms_resid;
     const int64_t kf = nevex - locked;
     // line 4: W+ <- p(H^2) W+
     clk.start();
@@ -893,6 +958,12 @@ int solve(const cplx* A, const cplx* B, int64_t n, int64_t nev, int64_t nex, int
     }
     prec = nprec;
     prev_res = kres;
+    if (verbose()) {
+      const double wall =
+          std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - it_start).count();
+      fprintf(stderr, "[chase_bse] it %d wall %.2f ms, timed phases %.2f ms\n", it, wall,
+              st.ms_filter + st.ms_qr + st.ms_rr + st.ms_resid - ph0);
+    }
   }
   st.iterations = it;
   // output: the nev smallest locked pairs in ascending order
