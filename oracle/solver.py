@@ -130,9 +130,16 @@ def solve(A, B, nev, nex, deg, tol, W0raw, starts, lanczos_steps=26, deg_min=Non
         W = Wpos[:, keep]
         if Yp.shape[1] >= nev or not keep:
             break
+        # mu_nevex: the largest kept Ritz value below mu_N (larger ones are spurious); after
+        # the first Rayleigh-Ritz (which replaces the Lanczos estimate, growing by at most 2x)
+        # it never increases: the top Ritz values of the unconverged guard vectors approach
+        # the spectrum from above, so a growing value means drift, not information
         cand = ritz[keep][ritz[keep] < muN]
         if len(cand):
-            mu_nevex = min(float(cand.max()), 2.0 * mu_nevex)
+            if it == 1:
+                mu_nevex = min(float(cand.max()), 2.0 * mu_nevex)
+            else:
+                mu_nevex = min(float(cand.max()), mu_nevex)
         if ritz[0] > 0:
             mu1 = min(mu1, float(ritz[0]))
         mu1 = min(mu1, 0.5 * mu_nevex)

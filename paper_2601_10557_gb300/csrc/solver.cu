@@ -937,12 +937,14 @@ int solve(const cplx* A, const cplx* B, int64_t n, int64_t nev, int64_t nex, int
       kprev.push_back(prev_res[i]);
       kdeg.push_back(degs[i]);
     }
-    // mu_nevex <- largest non-locked Ritz value below mu_N (larger ones are spurious),
-    // growing by at most a factor 2 per iteration (spurious values below mu_N occur early)
+    // mu_nevex <- largest non-locked Ritz value below mu_N (larger ones are spurious).
+    // The first Rayleigh-Ritz replaces the Lanczos estimate (growing by at most 2x);
+    // afterwards mu_nevex never increases: the top Ritz values of the unconverged guard
+    // vectors approach the spectrum from above, so a growing value is drift
     double cand = -1.0;
     for (double r : kr)
       if (r < muN) cand = std::max(cand, r);
-    if (cand > 0.0) mu_ne = std::min(cand, 2.0 * mu_ne);
+    if (cand > 0.0) mu_ne = (it == 1) ? std::min(cand, 2.0 * mu_ne) : std::min(cand, mu_ne);
     if (ritz[0] > 0.0) mu1 = std::min(mu1, ritz[0]);
     mu1 = std::min(mu1, 0.5 * mu_ne);
     degrees_update(kr, kres, kprev, kdeg, tol, mu_ne, muN, o.deg_min, o.deg_max, degs);

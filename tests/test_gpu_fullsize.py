@@ -1,0 +1,160 @@
+"""Parity at full size: the n = 4096 workload in the configuration the benchmark
+times (mixed precision, nev = 200, nex = 60, degrees 20-36, tol 1e-10), and the
+n = 8192 gradient workload.
+
+The dense oracle cannot solve these sizes in test time, so the checks are the
+properties that fix the answer at any size, each computed on the host from the
+GPU output with the plain FP64 formulas:
+
+* residuals ||H v - lambda v|| <= tol ||H||_2 (bound ||A||_2 + ||B||_2, exact for
+  the planted inputs) for every returned pair;
+* lambda equals the S-Rayleigh quotient v^* S H v / v^* S v of its own vector
+  (quadratically accurate in the residual);
+* completeness by Sylvester's law of inertia: for the definite pencil
+  (S H, S), the number of negative eigenvalues of S H - sigma S is the number of
+  eigenvalues of H in (0, sigma); just above lambda_nev it is nev, just below
+  lambda_1 it is 0;
+* sampled columns of the filter against the oracle filter (column by column);
+* the eigenvalue gradient against the oracle's formula on the same vectors and
+  against central finite differences of the solve.
+"""
+import numpy as np
+import pytest
+import torch
+
+import bse_inputs as bi
+from oracle import chebyshev, gradient
+from tests.gpu_util import rel_fro, to_dev
+
+pytestmark = pytest.mark.gpu
+
+TOL_FILTER = {"fp64": 1e-12, "mixed": 6e-5}
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    import paper_2601_10557_gb300 as p
+    return p
+
+
+@pytest.fixture(scope="module")
+def c2():
+    wl = bi.WORKLOADS["n4096"]
+    P = bi.make_problem(wl["n"], seed=0, spec=wl["spec"], beta=wl["beta"])
+    nevex = wl["nev"] + wl["nex"]
+    return wl, P, bi.start_block(wl["n"], nevex, 0), bi.lanczos_starts(wl["n"], 4, 0)
+
+
+def _hv(A, B, V):
+    """H V for V (2n x m), H = [[A, B], [-conj(B), -conj(A)]], without forming H."""
+    n = A.shape[0]
+    X, Y = V[:n], V[n:]
+    return np.vstack([A @ X + B @ Y, -(B.conj() @ X) - A.conj() @ Y])
+
+
+def _negative_count(M):
+    """Number of negative eigenvalues of the hermitian M (LDL^* with 1x1 / 2x2 blocks)."""
+    import scipy.linalg as sl
+    _, D, _ = sl.ldl(M, lower=True, hermitian=True)
+    count, i, m = 0, 0, D.shape[0]
+    while i < m:
+        if i + 1 < m and D[i + 1, i] != 0:
+            count += int((np.linalg.eigvalsh(D[i:i + 2, i:i + 2]) < 0).sum())
+            i += 2
+        else:
+            count += int(D[i, i].real < 0)
+            i += 1
+    return count
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_c2_filter_sampled_columns(pkg, c2, precision):
+    if precision == "mixed" and not pkg.has_mixed():
+        pytest.fail("tensor-core filter not available on this device")
+    wl, P, W0, _ = c2
+    k, deg = W0.shape[0], 20
+    mus = (1.0, 2.0, 45.0)
+    W = to_dev(W0)
+    pkg.filter(to_dev(P.A), to_dev(P.B), W, [deg] * k, *mus, precision=precision)
+    got = W.cpu().numpy()
+    cols = [0, 137, k - 1]
+    ref = chebyshev.chebyshev_filter(P.A, P.B, W0[cols].T, [deg] * len(cols), *mus)
+    for j, c in enumerate(cols):
+        assert rel_fro(got[c], ref[:, j]) < TOL_FILTER[precision], c
+
+
+def test_c2_mixed_solve_properties(pkg, c2):
+    if not pkg.has_mixed():
+        pytest.fail("tensor-core filter not available on this device")
+    wl, P, W0, V0 = c2
+    n, nev, nex, tol = wl["n"], wl["nev"], wl["nex"], wl["tol"]
+    lam, V, st = pkg.solve(to_dev(P.A), to_dev(P.B), nev, nex, wl["deg"], tol, precision="mixed",
+                           W0=to_dev(W0), V0=to_dev(V0), deg_min=wl["deg_min"], deg_max=wl["deg_max"],
+                           maxiter=40)
+    lam = lam.cpu().numpy()
+    V = V.cpu().numpy().T  # 2n x nev
+    assert st["converged"] == nev
+    assert np.all(np.diff(lam) > 0) and lam[0] > 0
+    np.testing.assert_allclose(np.linalg.norm(V, axis=0), 1.0, atol=1e-12)
+    # phase convention: largest-magnitude entry of the upper half real and positive
+    top = V[:n]
+    piv = top[np.argmax(np.abs(top), axis=0), np.arange(nev)]
+    assert np.all(np.abs(piv.imag) <= 1e-12 * np.abs(piv)) and np.all(piv.real > 0)
+    # residuals against the exact norm bound of the planted inputs
+    hnorm = P.d.max() + P.beta * P.d.min()
+    HV = _hv(P.A, P.B, V)
+    res = np.linalg.norm(HV - V * lam, axis=0)
+    assert res.max() <= tol * hnorm, res.max() / hnorm
+    # lambda is the S-Rayleigh quotient of its vector
+    SV = np.vstack([V[:n], -V[n:]])
+    rq = np.real(np.sum(SV.conj() * HV, axis=0) / np.sum(SV.conj() * V, axis=0))
+    assert np.max(np.abs(rq - lam) / lam) < 1e-12
+    # completeness: exactly nev eigenvalues of H in (0, lambda_nev (1 + 1e-9)], none below lambda_1
+    SH = np.block([[P.A, P.B], [P.B.conj(), P.A.conj()]])
+    S = np.concatenate([np.ones(n), -np.ones(n)])
+    for sigma, want in ((lam[-1] * (1 + 1e-9), nev), (lam[0] * (1 - 1e-9), 0)):
+        assert _negative_count(SH - sigma * np.diag(S)) == want
+
+
+def test_c4_gradient_fullsize(pkg):
+    """n = 8192, nev = 100, nex = 40: the adjoint kernel against the oracle's formula
+    on the same eigenvectors, and against central differences (h = 1e-6) of the solve
+    along dA = I and along a random hermitian / complex-symmetric direction."""
+    if not pkg.has_mixed():
+        pytest.fail("tensor-core filter not available on this device")
+    wl = bi.WORKLOADS["n8192grad"]
+    n, nev, nex = wl["n"], wl["nev"], wl["nex"]
+    P = bi.make_problem(n, seed=0, spec=wl["spec"], beta=wl["beta"])
+    W0, V0 = bi.start_block(n, nev + nex, 0), bi.lanczos_starts(n, 4, 0)
+    w = bi.loss_weights(nev, 0)
+    # the dense planted spectrum (spacing ~1e-3 around lambda_nev) converges slowly:
+    # adaptive degrees up to 36 and up to 100 iterations
+    kw = dict(W0=to_dev(W0), V0=to_dev(V0), deg_min=wl["deg_min"], deg_max=36, maxiter=100,
+              precision="mixed")
+    lam, Vt, st = pkg.solve(to_dev(P.A), to_dev(P.B), nev, nex, wl["deg"], wl["tol"], **kw)
+    gA, gB = pkg.grad(Vt, torch.from_numpy(w))
+    gA, gB = gA.cpu().numpy(), gB.cpu().numpy()
+    rA, rB = gradient.gradient_from_vectors(Vt.cpu().numpy().T, w)
+    assert rel_fro(gA, rA) < 1e-12
+    assert rel_fro(gB, rB) < 1e-12
+    np.testing.assert_allclose(gA, gA.conj().T, atol=1e-12 * np.abs(gA).max())
+    np.testing.assert_allclose(gB, gB.T, atol=1e-12 * np.abs(gB).max())
+    rng = np.random.default_rng(5)
+    h = 1e-6
+    E = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    F = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    # dA = I perturbs H by S, which couples eigenpairs i != j only through
+    # (S v_i)^* S v_j = v_i^* v_j = 2 y_i^* y_j (S-orthogonality: x_i^* x_j = y_i^* y_j),
+    # small because the lower halves are O(beta); the random direction is
+    # Wigner-scaled (entries ~ 1/sqrt(n), ||dA||_2 ~ 2) so that h ||dA|| stays far
+    # below the eigenvalue gaps of the planted spectrum
+    dirs = [(np.eye(n, dtype=complex), np.zeros((n, n), dtype=complex)),
+            ((E + E.conj().T) / (2 * np.sqrt(n)), (F + F.T) / (2 * np.sqrt(n)))]
+    for dA, dB in dirs:
+        lp, _, _ = pkg.solve(to_dev(P.A + h * dA), to_dev(P.B + h * dB), nev, nex, wl["deg"], wl["tol"], **kw)
+        lm, _, _ = pkg.solve(to_dev(P.A - h * dA), to_dev(P.B - h * dB), nev, nex, wl["deg"], wl["tol"], **kw)
+        fd = float(np.dot(w, (lp - lm).cpu().numpy()) / (2 * h))
+        an = float(np.real(np.sum(gA.conj() * dA) + np.sum(gB.conj() * dB)))
+        assert abs(fd - an) <= 1e-6 * abs(an), (fd, an)
