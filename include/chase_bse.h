@@ -182,7 +182,10 @@ int chase_bse_residuals_noalloc(const void* A, const void* B, int64_t n, const v
  * under the convention dL = Re sum conj(G) .* dZ.
  *   V      device, 2n x nev right eigenvectors (any normalisation)
  *   w      device, nev doubles
- *   gA, gB device, n x n complex128, written ROW-MAJOR like A and B. */
+ *   gA, gB device, n x n complex128, written ROW-MAJOR like A and B.
+ * On compute capability 10.3 the two rank-2nev products run as FP64-accurate
+ * sliced GEMMs on the tensor cores (see chase_bse_dgemm_sliced), elsewhere on
+ * the FP64 pipe. */
 int chase_bse_grad(const void* V, const double* w, int64_t n, int64_t nev, void* gA,
                    void* gB, void* stream);
 

@@ -1,4 +1,6 @@
 // Small dense FP64 kernels (see dense_kernels.cuh).
+#include <cuda_pipeline.h>
+
 #include <mutex>
 
 #include "dense_kernels.cuh"
@@ -569,13 +571,15 @@ __device__ __forceinline__ double pow2_inv_exp(double m) {
 }
 // Thresholds of the Jacobi rotations, evaluated once per pair in FP32 on values
 // scaled by sn = 2^-E(||G||_F) (all entries are then at most 1 in magnitude):
-// rotate when |a_pq| > 2e-16 sqrt|a_pp a_qq| and |a_pq| > 1e-16 ||G||_F.  The
+// rotate when |a_pq| > t sqrt|a_pp a_qq| and |a_pq| > (t/2) ||G||_F, with
+// t2a = t^2, t2b = t^2/4 (t = 2e-16 diagonalises to the rounding level).  The
 // sweeps and the convergence count use this same predicate.
-__device__ __forceinline__ bool jacobi_active(double app, double aqq, cplx apq, double sn, float n2s) {
+__device__ __forceinline__ bool jacobi_active(double app, double aqq, cplx apq, double sn, float n2s, float t2a,
+                                              float t2b) {
   const float xr = (float)(apq.x * sn), xi = (float)(apq.y * sn);
   const float a1 = (float)(app * sn), a2 = (float)(aqq * sn);
   const float r2 = fmaf(xr, xr, xi * xi);
-  return r2 > 4e-32f * fabsf(a1 * a2) && r2 > 1e-32f * n2s && r2 > 0.0f;
+  return r2 > t2a * fabsf(a1 * a2) && r2 > t2b * n2s && r2 > 0.0f;
 }
 
 // Rotation annihilating a_pq (identity below the thresholds).  GB300 issues an
@@ -585,9 +589,10 @@ __device__ __forceinline__ bool jacobi_active(double app, double aqq, cplx apq, 
 // FP32 reciprocal square roots refined by two FP64 Newton steps, so that
 // c^2 + s^2 = 1 and |e| = 1 hold to FP64 rounding.  a_pq is first scaled by an
 // exact power of two to magnitude in [1, 2).
-__device__ Rot jacobi_rotation(double app, double aqq, cplx apq, double sn, float n2s, int* applied) {
+__device__ Rot jacobi_rotation(double app, double aqq, cplx apq, double sn, float n2s, float t2a, float t2b,
+                               int* applied) {
   Rot R{1.0, 0.0, 1.0, 0.0};
-  if (!jacobi_active(app, aqq, apq, sn, n2s)) return R;
+  if (!jacobi_active(app, aqq, apq, sn, n2s, t2a, t2b)) return R;
   atomicAdd(applied, 1);
   const double sc = pow2_inv_exp(fmax(fabs(apq.x), fabs(apq.y)));
   const double xr = apq.x * sc, xi = apq.y * sc;
@@ -659,7 +664,7 @@ __device__ __forceinline__ void load_block(const cplx* G, int k, int p0, int q0,
 // pair of round r + 1 also recomputes the two new diagonal entries and writes
 // that pair's rotation, so each round needs one grid barrier.
 __global__ void jacobi_sweep_kernel(cplx* Ga, cplx* Gb, int k, Rot* rots, const double* red, int* applied,
-                                    GridSync* gsync, int* err) {
+                                    GridSync* gsync, int* err, float t2a, float t2b) {
   const int half = k / 2;
   const int64_t nblk = (int64_t)half * (half + 1) / 2;
   const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
@@ -673,7 +678,7 @@ __global__ void jacobi_sweep_kernel(cplx* Ga, cplx* Gb, int k, Rot* rots, const 
     int p, q;
     jpair32((int)sl, 0, k, p, q);
     rots[sl] = jacobi_rotation(__ldcg(Ga + p + (int64_t)p * k).x, __ldcg(Ga + q + (int64_t)q * k).x,
-                               __ldcg(Ga + p + (int64_t)q * k), sn, n2s, applied);
+                               __ldcg(Ga + p + (int64_t)q * k), sn, n2s, t2a, t2b, applied);
   }
   if (!grid_barrier(gsync, err)) return;
   for (int r = 0; r < k - 1; ++r) {
@@ -717,7 +722,8 @@ __global__ void jacobi_sweep_kernel(cplx* Ga, cplx* Gb, int k, Rot* rots, const 
         const double dx = rot_diag(A, Gi, k, pa, qa, ix), dy = rot_diag(B, Gi, k, pb, qb, iy);
         const int slot = pos < k - 1 - pos ? pos : k - 1 - pos;
         rots[(int64_t)(r + 1) * half + slot] =
-            xi < yi ? jacobi_rotation(dx, dy, zxy, sn, n2s, applied) : jacobi_rotation(dy, dx, cconj(zxy), sn, n2s, applied);
+            xi < yi ? jacobi_rotation(dx, dy, zxy, sn, n2s, t2a, t2b, applied)
+                    : jacobi_rotation(dy, dx, cconj(zxy), sn, n2s, t2a, t2b, applied);
       }
     }
     if (!grid_barrier(gsync, err)) return;
@@ -752,8 +758,54 @@ __global__ void jacobi_vpass_kernel(cplx* V, int k, const Rot* rots) {
   for (int j = lane; j < k; j += 32) V[i + (int64_t)j * k] = v[j];
 }
 
+// The same with the rotations of each round staged in shared memory by cp.async while
+// the previous round is applied (the per-round L2 latency is hidden); R rows of V
+// per CTA (one warp each) share the staged rotations.
+template <int R>
+__global__ void jacobi_vpass_staged_kernel(cplx* V, int k, const Rot* rots) {
+  extern __shared__ __align__(16) unsigned char vs_raw[];
+  const int half = k / 2;
+  Rot* rb = reinterpret_cast<Rot*>(vs_raw);                       // [2][half]
+  cplx* vrow = reinterpret_cast<cplx*>(rb + 2 * (int64_t)half);   // [R][k]
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * R + w;
+  const bool active = i < k;
+  cplx* v = vrow + (int64_t)w * k;
+  if (active)
+    for (int j = lane; j < k; j += 32) v[j] = V[i + (int64_t)j * k];
+  // a round's rotations are half * 32 bytes: 16-byte pieces over the CTA
+  auto stage = [&](int r, int buf) {
+    const char* src = reinterpret_cast<const char*>(rots + (int64_t)r * half);
+    char* dst = reinterpret_cast<char*>(rb + (int64_t)buf * half);
+    for (int c = threadIdx.x; c < 2 * half; c += blockDim.x)
+      __pipeline_memcpy_async(dst + 16 * c, src + 16 * c, 16);
+    __pipeline_commit();
+  };
+  stage(0, 0);
+  for (int r = 0; r < k - 1; ++r) {
+    __pipeline_wait_prior(0);
+    __syncthreads();  // round r staged; round r - 1 done with the other buffer
+    if (r + 1 < k - 1) stage(r + 1, (r + 1) & 1);
+    const Rot* Rr = rb + (int64_t)(r & 1) * half;
+    if (active) {
+      for (int sl = lane; sl < half; sl += 32) {
+        const Rot B = Rr[sl];
+        if (B.s == 0.0) continue;  // identity
+        int p, q;
+        jpair32(sl, r, k, p, q);
+        const cplx vp = v[p], u = cmul(v[q], mk(B.er, B.ei));
+        v[p] = mk(B.c * vp.x - B.s * u.x, B.c * vp.y - B.s * u.y);
+        v[q] = mk(B.s * vp.x + B.c * u.x, B.s * vp.y + B.c * u.y);
+      }
+    }
+    __syncwarp();
+  }
+  if (active)
+    for (int j = lane; j < k; j += 32) V[i + (int64_t)j * k] = v[j];
+}
+
 // Number of pairs p < q that a sweep would rotate (the thresholds of jacobi_rotation).
-__global__ void jacobi_count_kernel(const cplx* G, int k, const double* red, int* count) {
+__global__ void jacobi_count_kernel(const cplx* G, int k, const double* red, int* count, float t2a, float t2b) {
   const double normG = sqrt(red[1]);
   const double sn = pow2_inv_exp(normG);
   const float n2s = (float)((normG * sn) * (normG * sn));
@@ -763,7 +815,7 @@ __global__ void jacobi_count_kernel(const cplx* G, int k, const double* red, int
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int p = (int)(idx % k), q = (int)(idx / k);
     if (p >= q) continue;
-    if (jacobi_active(G[p + (int64_t)p * k].x, G[q + (int64_t)q * k].x, G[idx], sn, n2s)) ++local;
+    if (jacobi_active(G[p + (int64_t)p * k].x, G[q + (int64_t)q * k].x, G[idx], sn, n2s, t2a, t2b)) ++local;
   }
   if (local) atomicAdd(count, local);
 }
@@ -781,7 +833,9 @@ static cudaStream_t jacobi_stream() {
 }
 
 int jacobi_eigh(cplx* G, int64_t k, cplx* V, double* theta, cplx* rot, double* red, int max_sweeps,
-                int* sweeps_out, cudaStream_t s) {
+                int* sweeps_out, cudaStream_t s, double thr) {
+  if (!(thr >= 2e-16)) thr = 2e-16;
+  float t2a = (float)(thr * thr), t2b = (float)(0.25 * thr * thr);
   if (k % 2 != 0) return CHASE_BSE_BAD_ARG;
   CB_TRY(set_identity(V, k, s));
   int sweeps = 0;
@@ -804,10 +858,13 @@ int jacobi_eigh(cplx* G, int64_t k, cplx* V, double* theta, cplx* rot, double* r
     // one CTA per SM: every SM's FP64 pipe takes part, one barrier arrival each
     const unsigned grid = (unsigned)(sms > 0 ? sms : 1);
     const size_t vsmem = sizeof(cplx) * (size_t)VROWS * (size_t)k;
+    const size_t staged_smem = sizeof(Rot) * 2 * (size_t)half + sizeof(cplx) * 4 * (size_t)k;
     if (coop && per_sm >= 1 && k <= (1 << 20) && vsmem <= 200 * 1024) {
       static bool attr = false;
       if (!attr) {
         CB_CUDA(cudaFuncSetAttribute(jacobi_vpass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        CB_CUDA(cudaFuncSetAttribute(jacobi_vpass_staged_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     200 * 1024));
         attr = true;
       }
       GridSync* gsync = nullptr;
@@ -827,14 +884,14 @@ int jacobi_eigh(cplx* G, int64_t k, cplx* V, double* theta, cplx* rot, double* r
       cplx *Ga = G, *Gb = G2;
       // a matrix that is diagonal to the thresholds needs no sweep
       CB_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int), s));
-      jacobi_count_kernel<<<gs(k * k), 256, 0, s>>>(Ga, ki, red, cnt);
+      jacobi_count_kernel<<<gs(k * k), 256, 0, s>>>(Ga, ki, red, cnt, t2a, t2b);
       count_launch();
       CB_CUDA(cudaMemcpyAsync(&hc[1], cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
       CB_CUDA(cudaStreamSynchronize(s));
       for (; hc[1] > 0 && sweeps < max_sweeps; ++sweeps) {
         CB_CUDA(cudaMemsetAsync(applied, 0, sizeof(int), s));
         CB_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int), s));
-        void* args[] = {&Ga, &Gb, &ki, &rots, &red, &applied, &gsync, &err};
+        void* args[] = {&Ga, &Gb, &ki, &rots, &red, &applied, &gsync, &err, &t2a, &t2b};
         if (cudaLaunchCooperativeKernel((const void*)jacobi_sweep_kernel, dim3(grid), dim3(512), args, 0, s) !=
             cudaSuccess) {
           cudaGetLastError();
@@ -842,10 +899,13 @@ int jacobi_eigh(cplx* G, int64_t k, cplx* V, double* theta, cplx* rot, double* r
           break;
         }
         count_launch();
-        jacobi_vpass_kernel<<<(unsigned)((k + VROWS - 1) / VROWS), 32 * VROWS, vsmem, s>>>(V, ki, rots);
+        if (staged_smem <= 200 * 1024)
+          jacobi_vpass_staged_kernel<4><<<(unsigned)((k + 3) / 4), 128, staged_smem, s>>>(V, ki, rots);
+        else
+          jacobi_vpass_kernel<<<(unsigned)((k + VROWS - 1) / VROWS), 32 * VROWS, vsmem, s>>>(V, ki, rots);
         count_launch();
         std::swap(Ga, Gb);  // the last round (k - 2, even) wrote Gb
-        jacobi_count_kernel<<<gs(k * k), 256, 0, s>>>(Ga, ki, red, cnt);
+        jacobi_count_kernel<<<gs(k * k), 256, 0, s>>>(Ga, ki, red, cnt, t2a, t2b);
         count_launch();
         CB_CUDA(cudaMemcpyAsync(&hc[0], applied, sizeof(int), cudaMemcpyDeviceToHost, s));
         CB_CUDA(cudaMemcpyAsync(&hc[1], cnt, sizeof(int), cudaMemcpyDeviceToHost, s));

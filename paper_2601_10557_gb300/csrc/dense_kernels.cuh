@@ -17,7 +17,7 @@ int tri_inverse(const cplx* L, int64_t k, cplx* X, cplx* T, cudaStream_t s, bool
 // V receives the eigenvectors (columns).  theta[k] (device) gets diag(G).
 // rot is k/2 * 4 complex scratch, red 2 doubles scratch.
 int jacobi_eigh(cplx* G, int64_t k, cplx* V, double* theta, cplx* rot, double* red,
-                int max_sweeps, int* sweeps_out, cudaStream_t s);
+                int max_sweeps, int* sweeps_out, cudaStream_t s, double thr = 2e-16);
 
 // Unblocked Householder QR: Q (N x m, column-major, ld N) receives the
 // orthonormal factor of X (N x m), which is destroyed.  Vs: N*m, Us: N*m,

@@ -545,7 +545,8 @@ static int qr_jfixed(const cplx* X, int64_t n, int64_t m, cplx* Q, bool* ok_out,
 }
 
 static int rayleigh_ritz_jfixed(const cplx* A, const cplx* B, int64_t n, const cplx* Qt, int64_t k, double* ritz_host,
-                                cplx* Wpos, cplx* R, double* res, cudaStream_t s, const SlicedOp* ph) {
+                                cplx* Wpos, cplx* R, double* res, cudaStream_t s, const SlicedOp* ph,
+                                double jthr = 2e-16) {
   if (k <= 0 || (k % 2) != 0) return CHASE_BSE_BAD_ARG;
   const int64_t n2 = 2 * n, h = k / 2;
   Workspace ws(s);
@@ -639,7 +640,7 @@ static int rayleigh_ritz_jfixed(const cplx* A, const cplx* B, int64_t n, const c
   CB_TRY(hermitize(G, k, s));
   tm.mark("small");
   int sweeps = 0;
-  CB_TRY(jacobi_eigh(G, k, V, theta, rot, red, 40, &sweeps, s));  // line 8
+  CB_TRY(jacobi_eigh(G, k, V, theta, rot, red, 40, &sweeps, s, jthr));  // line 8
   tm.mark("jacobi");
   std::vector<double> th(k);
   CB_CUDA(cudaMemcpyAsync(th.data(), theta, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
@@ -716,6 +717,19 @@ int gradient(const cplx* V, const double* w, int64_t n, int64_t nev, cplx* gA, c
   CB_TRY(ws.alloc(&cbuf, nev));
   CB_TRY(grad_prepare(V, w, n, nev, cbuf, Uc, U2, Ub, U3, s));
   // row-major gA is the column-major conj(gA) = Uc U2^T; row-major gB = gB = Ub U3^T
+  if (mixed_available()) {  // FP64-accurate products on the tensor cores (sliced GEMM)
+    SlicedOp sa, sb;
+    double* tmp;
+    CB_TRY(sliced_alloc(ws, sa, 2 * n, 4 * nev, s));
+    CB_TRY(sliced_alloc(ws, sb, n, 4 * nev, s));
+    CB_TRY(ws.alloc(&tmp, 8 * n * nev));
+    CB_TRY(slice_complex_rows(Uc, n, n, 2 * nev, tmp, sa, s));
+    CB_TRY(slice_plain_rows(U2, n, sb, s));
+    CB_TRY(sliced_gemm(sa, sb, 1.0, reinterpret_cast<double*>(gA), 1, 2 * n, false, s));
+    CB_TRY(slice_complex_rows(Ub, n, n, 2 * nev, tmp, sa, s));
+    CB_TRY(slice_plain_rows(U3, n, sb, s));
+    return sliced_gemm(sa, sb, 1.0, reinterpret_cast<double*>(gB), 1, 2 * n, false, s);
+  }
   CB_TRY(zgemm('N', 'T', n, n, 2 * nev, mk(1, 0), Uc, n, U2, n, mk(0, 0), gA, n, s));
   CB_TRY(zgemm('N', 'T', n, n, 2 * nev, mk(1, 0), Ub, n, U3, n, mk(0, 0), gB, n, s));
   return CHASE_BSE_OK;
@@ -884,8 +898,14 @@ int solve(const cplx* A, const cplx* B, int64_t n, int64_t nev, int64_t nex, int
     Workspace rws(s);
     if (!Rvec) CB_TRY(rws.alloc(&Rvec, n2 * kf));
     // lines 8-11: Rayleigh-Ritz, W+ = Q Z+ and the residuals of the positive half
+    // Jacobi accuracy of the small eigenproblem: the Ritz vectors need not be more
+    // accurate than the subspace they come from; 1e-4 of the smallest residual of the
+    // previous iteration (1e-8 before the first), down to the rounding level
+    double jthr = 1e-8;
+    for (int64_t i = 0; i < kf; ++i) jthr = std::min(jthr, 1e-4 * prev_res[i]);
+    jthr = std::max(jthr, 2e-16);
     int rs = jok ? rayleigh_ritz_jfixed(A, B, n, Qf + 2 * locked * n, 2 * kf, ritz.data(), Wpos, Rvec, res_d, s,
-                                        sliced ? &ph : nullptr)
+                                        sliced ? &ph : nullptr, jthr)
                  : rayleigh_ritz(A, B, n, Qf + 2 * locked * n2, 2 * kf, ritz.data(), Wpos, s, Rvec, res_d);
     st.ms_rr += clk.stop();
     if (rs != CHASE_BSE_OK) { status = rs; break; }

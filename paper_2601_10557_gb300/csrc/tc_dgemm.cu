@@ -62,6 +62,7 @@ __device__ __forceinline__ uint64_t sdesc64(uint32_t saddr) {
 
 struct Args {
   int num_m, num_n, kb_total, kb_per_split;
+  int n_fast;          // raster: the CTAs of one A tile (1) or of one B tile (0) run together
   int64_t mp;          // rows of a partial tile column (A rows_pad)
   int64_t np;          // columns per split (B rows_pad)
   long long* hi;       // [split][col][row]
@@ -88,10 +89,11 @@ __global__ void __launch_bounds__(THREADS, 1)
   int* issued_sh = reinterpret_cast<int*>(tmem_slot + 2);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-  // m fastest: the CTAs sharing one B tile run together
+  // the CTAs sharing a tile of the larger operand run together, so that it is read
+  // from DRAM once and the other operand's tiles come from L2
   const int bid = blockIdx.x;
-  const int mt = bid % g.num_m;
-  const int nt = (bid / g.num_m) % g.num_n;
+  const int mt = g.n_fast ? (bid / g.num_n) % g.num_m : bid % g.num_m;
+  const int nt = g.n_fast ? bid % g.num_n : (bid / g.num_m) % g.num_n;
   const int sp = bid / (g.num_m * g.num_n);
   const int kb0 = sp * g.kb_per_split;
   const int nkb = min(g.kb_per_split, g.kb_total - kb0);
@@ -334,12 +336,13 @@ struct HamSrc {  // rows of P': y = A x + B conj(x) in (re, im) interleaved form
   }
 };
 
-struct ConjRowsSrc {  // row r of the complex column-major M, conjugated
+struct ComplexRowsSrc {  // row r of the complex column-major M, optionally conjugated
   const cplx* M;
   int64_t ld;
+  double sign;  // -1: conjugate
   __device__ double2 pair(int64_t r, int64_t l) const {
     const cplx v = M[r + l * ld];
-    return make_double2(v.x, -v.y);
+    return make_double2(v.x, sign * v.y);
   }
 };
 
@@ -436,7 +439,11 @@ int slice_complex_rows(const cplx* X, int64_t ldx, int64_t n, int64_t m, double*
 }
 
 int slice_conj_rows(const cplx* M, int64_t ld, SlicedOp& op, cudaStream_t s) {
-  return tcd::run_slice(tcd::ConjRowsSrc{M, ld}, op, s);
+  return tcd::run_slice(tcd::ComplexRowsSrc{M, ld, -1.0}, op, s);
+}
+
+int slice_plain_rows(const cplx* M, int64_t ld, SlicedOp& op, cudaStream_t s) {
+  return tcd::run_slice(tcd::ComplexRowsSrc{M, ld, 1.0}, op, s);
 }
 
 int slice_hamiltonian(const cplx* A, const cplx* B, int64_t n, SlicedOp& op, cudaStream_t s) {
@@ -471,6 +478,7 @@ int sliced_gemm(const SlicedOp& a, const SlicedOp& b, double alpha, double* out,
   Args g{};
   g.num_m = num_m;
   g.num_n = num_n;
+  g.n_fast = a.rows_pad >= b.rows_pad ? 1 : 0;
   g.kb_total = kb_total;
   g.kb_per_split = kb_per;
   g.mp = mp;

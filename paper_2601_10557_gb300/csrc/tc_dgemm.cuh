@@ -50,6 +50,8 @@ int slice_complex_rows(const cplx* X, int64_t ldx, int64_t n, int64_t m, double*
 // Rows of the complex matrix M (column-major, ld), conjugated, as (re, im) pairs:
 // the B operand of X M^* (op.rows = rows of M, op.K = 2 x columns of M).
 int slice_conj_rows(const cplx* M, int64_t ld, SlicedOp& op, cudaStream_t s);
+// The same rows without conjugation: the B operand of X M^T.
+int slice_plain_rows(const cplx* M, int64_t ld, SlicedOp& op, cudaStream_t s);
 
 // Rows of the real 2n x 2n matrix P' with [Re y; Im y] interleaved = P' [Re x; Im x]
 // interleaved for y = A x + B conj(x) (A, B row-major complex n x n).
