@@ -227,7 +227,7 @@ static void host_sym_eig(std::vector<double>& a, int m, std::vector<double>& w, 
 }
 
 int lanczos_bounds(const cplx* A, const cplx* B, int64_t n, const cplx* V0, int64_t nvec, int steps,
-                   int64_t nevex, double out[4], cudaStream_t s) {
+                   int64_t nevex, double out[4], cudaStream_t s, const SlicedOp* ph) {
   const int64_t n2 = 2 * n, sz = n2 * nvec;
   Workspace ws(s);
   cplx *Vp, *V, *U, *Wv, *Y;
@@ -245,7 +245,9 @@ int lanczos_bounds(const cplx* A, const cplx* B, int64_t n, const cplx* V0, int6
   HopArgs h{};
   h.A = A; h.B = B; h.n = n; h.k = nvec; h.mode = HOP_STORE;
   h.W = Wv; h.out = Y;
-  CB_TRY(hop_fp64(h, s));
+  // H applied on the FP64 pipe, or (mixed mode) by the sliced tensor-core GEMM
+  auto apply_h = [&]() { return ph ? hop_sliced(*ph, Wv, n, nvec, Y, s) : hop_fp64(h, s); };
+  CB_TRY(apply_h());
   CB_TRY(sdot_real(Wv, Y, n, nvec, nrm2, s));
   CB_TRY(lanczos_normalise(b0, nrm2, Wv, Y, V, U, n, nvec, s));
   for (int j = 0; j < steps; ++j) {
@@ -253,7 +255,7 @@ int lanczos_bounds(const cplx* A, const cplx* B, int64_t n, const cplx* V0, int6
     CB_TRY(lanczos_axpy(Wv, U, V, Vp, alpha + (size_t)j * nvec, j > 0 ? beta + (size_t)(j - 1) * nvec : nullptr, n,
                         nvec, s));
     h.W = Wv; h.out = Y;
-    CB_TRY(hop_fp64(h, s));
+    CB_TRY(apply_h());
     CB_TRY(sdot_real(Wv, Y, n, nvec, nrm2, s));
     std::swap(Vp, V);
     CB_TRY(lanczos_normalise(beta + (size_t)j * nvec, nrm2, Wv, Y, V, U, n, nvec, s));
@@ -833,13 +835,6 @@ int solve(const cplx* A, const cplx* B, int64_t n, int64_t nev, int64_t nex, int
   }
   std::vector<double> ritz_keep;  // Ritz values of the columns of W (mixed correction form)
   PhaseClock clk(s);
-  // mixed mode: the rows of H's top block row, y = A x + B conj(x), as sliced
-  // tensor-core operand for the Rayleigh-Ritz product H Q (cut once per solve)
-  SlicedOp ph;
-  if (sliced) {
-    CB_TRY(sliced_alloc(ws, ph, 2 * n, 2 * n, s));
-    CB_TRY(slice_hamiltonian(A, B, n, ph, s));
-  }
 
   // Algorithm 3 line 1: W+ = randn(2n, nevex), lower half scaled by gamma
   if (o.W0) CB_CUDA(cudaMemcpyAsync(W, o.W0, sizeof(cplx) * n2 * nevex, cudaMemcpyDeviceToDevice, s));
@@ -848,10 +843,19 @@ int solve(const cplx* A, const cplx* B, int64_t n, int64_t nev, int64_t nex, int
   if (o.V0) CB_CUDA(cudaMemcpyAsync(V0, o.V0, sizeof(cplx) * n2 * o.lanczos_vecs, cudaMemcpyDeviceToDevice, s));
   else CB_TRY(randn_complex(V0, n2 * o.lanczos_vecs, o.seed, 2, s));
 
+  // mixed mode: the rows of H's top block row, y = A x + B conj(x), as sliced
+  // tensor-core operand for the Lanczos and Rayleigh-Ritz products with H (cut
+  // once per solve)
+  SlicedOp ph;
+  if (sliced) {
+    CB_TRY(sliced_alloc(ws, ph, 2 * n, 2 * n, s));
+    CB_TRY(slice_hamiltonian(A, B, n, ph, s));
+  }
+
   // line 2: spectral bounds
   clk.start();
   double mu[4];
-  CB_TRY(lanczos_bounds(A, B, n, V0, o.lanczos_vecs, o.lanczos_steps, nevex, mu, s));
+  CB_TRY(lanczos_bounds(A, B, n, V0, o.lanczos_vecs, o.lanczos_steps, nevex, mu, s, sliced ? &ph : nullptr));
   if (verbose())
     fprintf(stderr, "[chase_bse] setup wall %.2f ms\n",
             std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count());

@@ -18,9 +18,11 @@ int filter(const cplx* A, const cplx* B, int64_t n, cplx* W, int64_t k, const in
            double mu1, double mu_nevex, double muN, int scheme, const double* ritz, const cplx* R, cudaStream_t s,
            FilterStats* fs);
 
-// Lanczos bounds: mu1, mu_nevex, muN and rho_hat (max |theta|).
+// Lanczos bounds: mu1, mu_nevex, muN and rho_hat (max |theta|); with ph (the sliced
+// operand of slice_hamiltonian) H is applied on the tensor cores, FP64-accurate.
+struct SlicedOp;
 int lanczos_bounds(const cplx* A, const cplx* B, int64_t n, const cplx* V0, int64_t nvec, int steps,
-                   int64_t nevex, double out[4], cudaStream_t s);
+                   int64_t nevex, double out[4], cudaStream_t s, const SlicedOp* ph = nullptr);
 
 // Orthonormal Q (2n x m) of X (2n x m; X is preserved).  *used_hh set to 1 if
 // the Householder fallback ran.

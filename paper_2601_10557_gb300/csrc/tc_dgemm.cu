@@ -370,6 +370,33 @@ __global__ void complex_rows_kernel(const cplx* X, int64_t ldx, int64_t n, int64
   }
 }
 
+// Z (n x 2k, column-major) from W (2n x k): the J-fixed halves of w_j = [x; y],
+// a_j = (x + conj(y))/2 and c_j = i (x - conj(y))/2, so that w = [a; conj(a)] - i [c; conj(c)].
+__global__ void jsplit_kernel(const cplx* W, int64_t n, int64_t k, cplx* Z) {
+  const int64_t total = n * k;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx % n, j = idx / n;
+    const cplx x = W[j * 2 * n + i], y = W[j * 2 * n + n + i];
+    const cplx a = mk(0.5 * (x.x + y.x), 0.5 * (x.y - y.y));
+    const cplx d = mk(0.5 * (x.x - y.x), 0.5 * (x.y + y.y));  // (x - conj(y)) / 2
+    Z[(2 * j) * n + i] = a;
+    Z[(2 * j + 1) * n + i] = mk(-d.y, d.x);                  // i d
+  }
+}
+// H w_j from T = [P'a_j, P'c_j] (y = A z + B conj(z) of the J-fixed halves):
+// top = P'a - i P'c, bottom = -conj(P'a) + i conj(P'c).
+__global__ void jcombine_kernel(const cplx* T, int64_t n, int64_t k, cplx* out) {
+  const int64_t total = n * k;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx % n, j = idx / n;
+    const cplx ta = T[(2 * j) * n + i], tc = T[(2 * j + 1) * n + i];
+    out[j * 2 * n + i] = mk(ta.x + tc.y, ta.y - tc.x);       // ta - i tc
+    out[j * 2 * n + n + i] = mk(-ta.x + tc.y, ta.y + tc.x);  // -conj(ta) + i conj(tc)
+  }
+}
+
 static unsigned gsz(int64_t total) {
   const int64_t b = (total + 255) / 256;
   return (unsigned)std::min<int64_t>(std::max<int64_t>(b, 1), 16384);
@@ -444,6 +471,26 @@ int slice_conj_rows(const cplx* M, int64_t ld, SlicedOp& op, cudaStream_t s) {
 
 int slice_plain_rows(const cplx* M, int64_t ld, SlicedOp& op, cudaStream_t s) {
   return tcd::run_slice(tcd::ComplexRowsSrc{M, ld, 1.0}, op, s);
+}
+
+int hop_sliced(const SlicedOp& ph, const cplx* W, int64_t n, int64_t k, cplx* out, cudaStream_t s) {
+  if (k == 0) return CHASE_BSE_OK;
+  if (ph.rows != 2 * n || ph.K != 2 * n) return CHASE_BSE_BAD_ARG;
+  Workspace ws(s);
+  cplx *Z, *T;
+  CB_TRY(ws.alloc(&Z, n * 2 * k));
+  CB_TRY(ws.alloc(&T, n * 2 * k));
+  tcd::jsplit_kernel<<<tcd::gsz(n * k), 256, 0, s>>>(W, n, k, Z);
+  count_launch();
+  CB_LAUNCH();
+  SlicedOp sz;
+  CB_TRY(sliced_alloc(ws, sz, 2 * k, 2 * n, s));
+  CB_TRY(slice_rows(reinterpret_cast<const double*>(Z), 2 * n, 0, sz, s));
+  CB_TRY(sliced_gemm(ph, sz, 1.0, reinterpret_cast<double*>(T), 1, 2 * n, false, s));
+  tcd::jcombine_kernel<<<tcd::gsz(n * k), 256, 0, s>>>(T, n, k, out);
+  count_launch();
+  CB_LAUNCH();
+  return CHASE_BSE_OK;
 }
 
 int slice_hamiltonian(const cplx* A, const cplx* B, int64_t n, SlicedOp& op, cudaStream_t s) {

@@ -57,6 +57,12 @@ int slice_plain_rows(const cplx* M, int64_t ld, SlicedOp& op, cudaStream_t s);
 // interleaved for y = A x + B conj(x) (A, B row-major complex n x n).
 int slice_hamiltonian(const cplx* A, const cplx* B, int64_t n, SlicedOp& op, cudaStream_t s);
 
+// out = H W for a general 2n x k block W (column-major, ld 2n), from the sliced
+// P' of slice_hamiltonian: each w = [x; y] is the sum of the J-fixed vectors
+// [a; conj(a)] and -i [c; conj(c)], a = (x + conj(y))/2, c = i (x - conj(y))/2,
+// and H [z; conj(z)] = [P'z; -conj(P'z)].
+int hop_sliced(const SlicedOp& ph, const cplx* W, int64_t n, int64_t k, cplx* out, cudaStream_t s);
+
 // C[r][c] = alpha * sum_k a[r][k] b[c][k] for r < a.rows, c < b.rows, written to
 // out[r * rs + c * cs]; with neg_odd the rows r odd are negated (complex
 // conjugate of a real-form result).

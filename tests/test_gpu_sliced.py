@@ -97,6 +97,10 @@ def test_mixed_solve_sliced_matches_fp64_products(cbx):
         assert st["max_residual"] <= 1e-10
     e_t, e_f = out["tensor"][0], out["fp64"][0]
     assert np.max(np.abs(e_t - e_f) / np.abs(e_f)) < 1e-12
+    # mu_N and rho_hat come from the Lanczos bounds alone, whose H products run on the
+    # tensor cores (J-even / J-odd split) in one mode and on the FP64 pipe in the other
+    for key in ("muN", "rho_hat"):
+        assert abs(out["tensor"][2][key] - out["fp64"][2][key]) <= 1e-9 * out["fp64"][2][key], key
     # and both match the dense eigenvalues of H
     H = np.block([[p.A, p.B], [-p.B.conj(), -p.A.conj()]])
     lam = np.sort(np.linalg.eigvals(H).real)
