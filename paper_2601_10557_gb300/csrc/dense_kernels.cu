@@ -5,6 +5,7 @@
 
 #include "dense_kernels.cuh"
 #include "fp64_kernels.cuh"
+#include "coop.cuh"
 
 namespace cb {
 
@@ -34,54 +35,6 @@ __device__ double block_sum(double v, double* sh) {
   return v;
 }
 }  // namespace
-
-// ------------------------------------------------------------ grid barrier
-// For kernels launched cooperatively (all CTAs co-resident): a counter plus a
-// generation word in global memory.  Every wait is bounded (2 s of
-// %globaltimer), after which the kernel records an error, and all CTAs leave
-// at their next barrier.  Data written by other CTAs before a barrier is read
-// with __ldcg (L2) after it.
-struct GridSync {
-  unsigned count;  // arrival word: its top bit flips once per completed barrier
-  unsigned gen;    // unused (kept zero)
-};
-__device__ __forceinline__ unsigned long long gtimer_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-// CTA 0 adds 2^31 - (gridDim.x - 1), every other CTA adds 1 (release), so the
-// top bit of the word flips exactly when the last CTA arrives; the waiters poll
-// it with acquire loads.  The wait is bounded: after 2 s, or once another CTA
-// has recorded an error, the CTA records the error and returns false.
-__device__ bool grid_barrier(GridSync* gsync, int* err) {
-  __shared__ int ok_sh;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    ok_sh = 1;
-    const unsigned inc = (blockIdx.x == 0) ? (0x80000000u - (gridDim.x - 1)) : 1u;
-    unsigned old, cur;
-    __threadfence();  // the CTA's writes (ordered before by __syncthreads) become visible first
-    asm volatile("atom.add.release.gpu.u32 %0, [%1], %2;" : "=r"(old) : "l"(&gsync->count), "r"(inc) : "memory");
-    const unsigned long long t0 = gtimer_ns();
-    unsigned it = 0;
-    while (true) {
-      asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(cur) : "l"(&gsync->count) : "memory");
-      if (((old ^ cur) & 0x80000000u) != 0) break;
-      if ((++it & 63) == 0) {
-        if (*(volatile int*)err) { ok_sh = 0; break; }
-        if (gtimer_ns() - t0 > 2000000000ull) {
-          atomicExch(err, 1);
-          ok_sh = 0;
-          break;
-        }
-      }
-    }
-    __threadfence();
-  }
-  __syncthreads();
-  return ok_sh != 0;
-}
 
 // ---------------------------------------------------------------- Cholesky
 __global__ void chol_diag_kernel(cplx* G, int64_t ld, int64_t j0, int nb, int* info) {
@@ -549,21 +502,6 @@ struct Rot {
   double c, s, er, ei;
 };
 
-// position of index x in round r (inverse of the pairing in jpair)
-__device__ __forceinline__ int jpos(int x, int r, int k) {
-  if (x == 0) return 0;
-  int t = (x - 1 - r) % (k - 1);
-  if (t < 0) t += k - 1;
-  return t + 1;
-}
-__device__ __forceinline__ int jat(int pos, int r, int k) { return pos == 0 ? 0 : ((pos - 1 + r) % (k - 1)) + 1; }
-
-__device__ __forceinline__ void jpair32(int slot, int r, int k, int& p, int& q) {
-  const int a = jat(slot, r, k), b = jat(k - 1 - slot, r, k);
-  p = a < b ? a : b;
-  q = a < b ? b : a;
-}
-
 // 2^-E for a normal m = f 2^E, f in [1, 2) (exact power of two, from the bits)
 __device__ __forceinline__ double pow2_inv_exp(double m) {
   const int e = (__double2hiint(m) >> 20) & 0x7ff;
@@ -668,7 +606,6 @@ __global__ void jacobi_sweep_kernel(cplx* Ga, cplx* Gb, int k, Rot* rots, const 
   const int half = k / 2;
   const int64_t nblk = (int64_t)half * (half + 1) / 2;
   const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
-  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const double normG = sqrt(red[1]);
   const double sn = pow2_inv_exp(normG);
   const float n2s = (float)((normG * sn) * (normG * sn));
@@ -830,6 +767,13 @@ static cudaStream_t jacobi_stream() {
   if (!streams[dev] && cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking) != cudaSuccess)
     return nullptr;
   return streams[dev];
+}
+
+int offdiag_norms(const cplx* G, int64_t k, double* red, cudaStream_t s) {
+  offdiag_norm_kernel<<<1, 1024, 0, s>>>(G, k, red);
+  count_launch();
+  CB_LAUNCH();
+  return CHASE_BSE_OK;
 }
 
 int jacobi_eigh(cplx* G, int64_t k, cplx* V, double* theta, cplx* rot, double* red, int max_sweeps,

@@ -9,15 +9,27 @@ namespace cb {
 // Blocked Cholesky G = L L^* in place (lower triangle; strict upper zeroed).
 // *info_host = 0 on success, j+1 if the j-th pivot is not positive (or NaN).
 int cholesky(cplx* G, int64_t k, int* info_dev, int* info_host, cudaStream_t s, bool real = false);
-// X = L^{-1} for lower-triangular L (k x k); T is k*32 complex scratch.
+// out = in^* (k x k)
 int conj_transpose(const cplx* in, int64_t k, cplx* out, cudaStream_t s);
+// X = L^{-1} for lower-triangular L (k x k); T is k*32 complex scratch; real: L has
+// zero imaginary parts.
 int tri_inverse(const cplx* L, int64_t k, cplx* X, cplx* T, cudaStream_t s, bool real = false);
 
+// red[0] = ||offdiag(G)||_F^2, red[1] = ||G||_F^2 (device)
+int offdiag_norms(const cplx* G, int64_t k, double* red, cudaStream_t s);
 // Cyclic Jacobi on hermitian G (k x k, k even, overwritten by its diagonal form);
 // V receives the eigenvectors (columns).  theta[k] (device) gets diag(G).
-// rot is k/2 * 4 complex scratch, red 2 doubles scratch.
+// rot is k/2 * 4 complex scratch, red 2 doubles scratch; rotations stop below the
+// relative threshold thr (>= 2e-16).
 int jacobi_eigh(cplx* G, int64_t k, cplx* V, double* theta, cplx* rot, double* red,
                 int max_sweeps, int* sweeps_out, cudaStream_t s, double thr = 2e-16);
+
+// As jacobi_eigh, for G far from diagonal: FP32 Jacobi sweeps first, then the FP32
+// eigenvectors made unitary in FP64 (Newton-Schulz on the tensor cores), G1 = V1^* G V1
+// and FP64 Jacobi on G1 (jacobi_mixed.cu).  Falls back to jacobi_eigh for small k or a
+// nearly diagonal G.  Needs the tensor cores (compute capability 10.3).
+int jacobi_eigh_mixed(cplx* G, int64_t k, cplx* V, double* theta, cplx* rot, double* red, int* sweeps32_out,
+                      int* sweeps64_out, cudaStream_t s, double thr);
 
 // Unblocked Householder QR: Q (N x m, column-major, ld N) receives the
 // orthonormal factor of X (N x m), which is destroyed.  Vs: N*m, Us: N*m,

@@ -642,7 +642,9 @@ static int rayleigh_ritz_jfixed(const cplx* A, const cplx* B, int64_t n, const c
   CB_TRY(hermitize(G, k, s));
   tm.mark("small");
   int sweeps = 0;
-  CB_TRY(jacobi_eigh(G, k, V, theta, rot, red, 40, &sweeps, s, jthr));  // line 8
+  int sweeps32 = 0;
+  if (sliced) CB_TRY(jacobi_eigh_mixed(G, k, V, theta, rot, red, &sweeps32, &sweeps, s, jthr));  // line 8
+  else CB_TRY(jacobi_eigh(G, k, V, theta, rot, red, 40, &sweeps, s, jthr));
   tm.mark("jacobi");
   std::vector<double> th(k);
   CB_CUDA(cudaMemcpyAsync(th.data(), theta, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
@@ -690,7 +692,8 @@ static int rayleigh_ritz_jfixed(const cplx* A, const cplx* B, int64_t n, const c
   CB_TRY(col_norms(R, n2, h, res, s));
   CB_CUDA(cudaStreamSynchronize(s));  // host vectors must outlive the copies
   tm.mark("back");
-  if (verbose()) fprintf(stderr, "[chase_bse] rr(J) k %ld jacobi %d sweeps\n", (long)k, sweeps);
+  if (verbose())
+    fprintf(stderr, "[chase_bse] rr(J) k %ld jacobi %d FP32 + %d FP64 sweeps\n", (long)k, sweeps32, sweeps);
   return CHASE_BSE_OK;
 }
 
