@@ -89,6 +89,9 @@ def load_peaks():
     return dict(PEAKS_FALLBACK), "fallback"
 
 
+TC_TRAFFIC_N4096_K260 = (486775552 + 42145280 + 504331776 + 48718848) / 2.0  # bytes per launch
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
@@ -348,8 +351,12 @@ def main():
     else:
         peak = peaks["bf16_tflops"] / 3.0
         peak_note = f"{peak_src} bf16 burst / 3 (three BF16 products per FP32-accurate product)"
+    # DRAM bytes per launch of the BF16x3 filter kernel (tc_hop_kernel<3, 128>) at this
+    # workload, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, mean of
+    # two launches; profiles/tc_hop_bf16x3_n4096_k260.md); other cases were not captured
+    traffic = TC_TRAFFIC_N4096_K260 if (precision in ("mixed", "bf16x3") and n == 4096 and nevex == 260) else None
     roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None, "kernel": "hop_kernel (FP64 DFMA)" if precision == "fp64" else "tc_filter_gemm",
+            "traffic": traffic, "kernel": "hop_kernel (FP64 DFMA)" if precision == "fp64" else "tc_filter_gemm",
             "peak_source": peak_note, "launches_timed": gemm_launches, "all_launches": rl,
             "flops_per_launch": flops_per_launch}
 

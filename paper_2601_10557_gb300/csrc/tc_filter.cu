@@ -47,16 +47,15 @@
 namespace cb {
 namespace tc {
 
-constexpr int BM = 128, BK = 64, BN = 128;
+constexpr int BM = 128, BK = 64;
 constexpr int A_BYTES = BM * BK * 2;  // 16 KB per piece
-constexpr int B_BYTES = BN * BK * 2;  // 16 KB per piece
-constexpr int THREADS = 256;
 constexpr int GROUP_M = 8;            // tile raster: GROUP_M row tiles x all column tiles per group
-constexpr uint32_t TMEM_COLS = 512;   // hi*hi accumulator x 2 buffers + cross products (+ spare)
-constexpr int FLUSH = 2;              // K blocks per drained hi*hi partial sum
-// instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, 128 x BN
-constexpr uint32_t IDESC =
-    (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+constexpr uint32_t TMEM_COLS = 512;   // two accumulator buffers (+ the cross products for 128-wide tiles)
+constexpr int FLUSH = 2;              // K blocks per drained partial sum
+// instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, 128 x n
+__device__ __forceinline__ uint32_t make_idesc(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
 
 // Scheme: pieces of A (NPA) and B (NPW), product list (product 0 is x0 * y0).
 template <int NP>
@@ -74,12 +73,25 @@ struct Scheme<6> {  // BF16x6
   __device__ static constexpr int pa(int i) { return i == 2 ? 1 : (i == 4 ? 1 : (i == 5 ? 2 : 0)); }
   __device__ static constexpr int pb(int i) { return i == 1 ? 1 : (i == 3 ? 2 : (i == 4 ? 1 : 0)); }
 };
-template <int NP>
+// Tile geometry for BNT-wide output tiles.  128-wide: the x0 * y0 product drains from
+// two alternating TMEM buffers and the cross products accumulate over all of K in a
+// third; 4 drain warps of 128 columns.  256-wide (BF16x3 only): all products share the
+// two alternating buffers (drained every FLUSH K blocks, so the truncating accumulator
+// sums at most FLUSH * 4 * NPROD MMAs); 16 drain warps of 64 columns keep the FP32
+// partial sums in registers; a 2-stage ring of 96 KB.
+template <int NP, int BNT>
 struct Geo {
-  static constexpr int STAGES = Scheme<NP>::STAGES;
+  static constexpr int STAGES = (BNT == 256) ? 2 : Scheme<NP>::STAGES;
+  static constexpr int B_BYTES = BNT * BK * 2;
   static constexpr int STAGE_BYTES = Scheme<NP>::NPA * A_BYTES + Scheme<NP>::NPW * B_BYTES;
   static constexpr int NBAR = 2 * STAGES + 5;  // full, empty, acc_full[2], acc_empty[2], done
   static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+  static constexpr bool CROSS = (BNT == 128);             // separate cross-product buffer
+  static constexpr int DCOLS = (BNT == 128) ? 128 : 64;    // columns per drain warp
+  static constexpr int DRAIN_WARPS = 4 * (BNT / DCOLS);
+  static constexpr int THREADS = 128 + 32 * DRAIN_WARPS;
+  static_assert(STAGE_BYTES * STAGES + 1280 <= 232448, "shared memory");
+  static_assert(CROSS ? 3 * BNT <= (int)TMEM_COLS : 2 * BNT <= (int)TMEM_COLS, "TMEM columns");
 };
 
 struct Epi {
@@ -124,6 +136,19 @@ __device__ __forceinline__ void drain_add(uint32_t col, float* sum) {
   }
 }
 
+// sum[0..N) += the warp's TMEM lanes at columns [col, col + N), 16 columns per load
+template <int N>
+__device__ __forceinline__ void drain_add16(uint32_t col, float* sum) {
+#pragma unroll
+  for (int c = 0; c < N / 16; ++c) {
+    uint32_t r[16];
+    tmem_ld16_nowait(col + (uint32_t)(c * 16), r);
+    tmem_wait_ld();
+#pragma unroll
+    for (int i = 0; i < 16; ++i) sum[c * 16 + i] += __uint_as_float(r[i]);
+  }
+}
+
 template <int NPC>
 __device__ __forceinline__ void put(__nv_bfloat16* const* pc, int64_t off, float a, float b) {
 #pragma unroll
@@ -156,19 +181,20 @@ struct Maps {
   CUtensorMap b[3];
 };
 
-// One 128 x 128 output tile per CTA.  The dominant product x0*y0 accumulates
-// in one of two TMEM buffers that alternate every FLUSH K blocks; the four
-// epilogue warps drain each finished buffer into FP32 registers (round to
-// nearest) while the MMA fills the other one, so the tensor core's truncating
-// accumulator never sums more than 4 * FLUSH MMAs of the large product.  The
-// cross products, 2^-8 smaller, accumulate over the whole K in a third buffer
-// whose truncation error stays below FP32 rounding of the total.
-template <int NP>
-__global__ void __launch_bounds__(THREADS, 1)
-    tc_hop_kernel(const __grid_constant__ Maps maps, Epi ep, int num_kb, int num_m, int num_n) {
+// One 128 x BNT output tile per CTA.  Every K block's products accumulate in one of
+// two TMEM buffers that alternate every FLUSH K blocks; the drain warps add each
+// finished buffer into FP32 registers (round to nearest) while the MMA fills the
+// other one, so the tensor core's truncating accumulator only ever sums a few
+// MMAs.  With 128-wide tiles the cross products (2^-8 smaller) accumulate over the
+// whole K in a third buffer instead.  The last column tile may be narrower
+// (n_last columns, a multiple of 16): its MMAs use N = n_last.
+template <int NP, int BNT>
+__global__ void __launch_bounds__(Geo<NP, BNT>::THREADS, 1)
+    tc_hop_kernel(const __grid_constant__ Maps maps, Epi ep, int num_kb, int num_m, int num_n, int n_last) {
   using SC = Scheme<NP>;
-  using G = Geo<NP>;
+  using G = Geo<NP, BNT>;
   constexpr int ST = G::STAGES;
+  constexpr int DC = G::DCOLS;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + ST * G::STAGE_BYTES);
@@ -195,7 +221,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   const int rem = bid - g * per_group;
   const int mt = first_m + rem % gm;
   const int nt = rem / gm;
-  const int m0 = mt * BM, n0 = nt * BN;
+  const int m0 = mt * BM, n0 = nt * BNT;
+  const int ntile = (nt == num_n - 1) ? n_last : BNT;  // columns of this tile (multiple of 16)
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < ST; ++s) {
@@ -204,7 +231,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(accf[b], 1);
-      mbar_init(acce[b], 4);  // one arrival per epilogue warp
+      mbar_init(acce[b], G::DRAIN_WARPS);  // one arrival per drain warp
     }
     mbar_init(done, 1);
     *abort_sh = 0;
@@ -235,12 +262,13 @@ __global__ void __launch_bounds__(THREADS, 1)
       for (int q = 0; q < SC::NPA; ++q) tma_load_2d(st + q * A_BYTES, &maps.a[q], kb * BK, m0, full[s]);
 #pragma unroll
       for (int q = 0; q < SC::NPW; ++q)
-        tma_load_2d(st + SC::NPA * A_BYTES + q * B_BYTES, &maps.b[q], kb * BK, n0, full[s]);
+        tma_load_2d(st + SC::NPA * A_BYTES + q * G::B_BYTES, &maps.b[q], kb * BK, n0, full[s]);
       issued = kb + 1;
     }
     *issued_sh = issued;
   } else if (warp == 1 && lane == 0) {
-    const uint32_t small = tmem + (uint32_t)(2 * BN);
+    const uint32_t idesc = make_idesc(ntile);
+    const uint32_t small = tmem + (uint32_t)(2 * BNT);
     for (int kb = 0; kb < num_kb; ++kb) {
       const int grp = kb / FLUSH, b = grp & 1;
       const bool first = (kb % FLUSH) == 0;
@@ -251,15 +279,21 @@ __global__ void __launch_bounds__(THREADS, 1)
       if (!mbar_wait(full[s], ph, abort_sh, ep.err, true)) break;
       tc_fence_after();
       const uint32_t st = sbase + s * G::STAGE_BYTES;
-      const uint32_t big = tmem + (uint32_t)(b * BN);
+      const uint32_t big = tmem + (uint32_t)(b * BNT);
 #pragma unroll
       for (int kk = 0; kk < BK / 16; ++kk) {
 #pragma unroll
         for (int pr = 0; pr < SC::NPROD; ++pr) {
           const uint64_t ad = sdesc(st + SC::pa(pr) * A_BYTES + kk * 32);
-          const uint64_t bd = sdesc(st + SC::NPA * A_BYTES + SC::pb(pr) * B_BYTES + kk * 32);
-          const uint32_t acc = (pr == 0) ? ((!first || kk > 0) ? 1u : 0u) : ((kb > 0 || kk > 0 || pr > 1) ? 1u : 0u);
-          mma_bf16(pr == 0 ? big : small, ad, bd, IDESC, acc);
+          const uint64_t bd = sdesc(st + SC::NPA * A_BYTES + SC::pb(pr) * G::B_BYTES + kk * 32);
+          if (G::CROSS) {
+            const uint32_t acc =
+                (pr == 0) ? ((!first || kk > 0) ? 1u : 0u) : ((kb > 0 || kk > 0 || pr > 1) ? 1u : 0u);
+            mma_bf16(pr == 0 ? big : small, ad, bd, idesc, acc);
+          } else {
+            const uint32_t acc = (first && kk == 0 && pr == 0) ? 0u : 1u;
+            mma_bf16(big, ad, bd, idesc, acc);
+          }
         }
       }
       mma_commit(empty[s]);
@@ -267,11 +301,14 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     mma_commit(done);  // completes once every MMA issued above has finished
   } else if (warp >= 4) {
-    const int q = warp - 4;
+    const int dw = warp - 4;
+    const int q = warp & 3;                  // TMEM lanes 32 q .. 32 q + 31 (rows of the tile)
+    const int col0 = (dw >> 2) * DC;         // this warp's columns [col0, col0 + DC)
     const uint32_t lane_base = (uint32_t)(q * 32) << 16;
-    float sum[BN];
+    const bool has_cols = col0 < ntile;
+    float sum[DC];
 #pragma unroll
-    for (int i = 0; i < BN; ++i) sum[i] = 0.0f;
+    for (int i = 0; i < DC; ++i) sum[i] = 0.0f;
     bool ok = true;
     const int ngrp = (num_kb + FLUSH - 1) / FLUSH;
     for (int grp = 0; grp < ngrp; ++grp) {
@@ -282,27 +319,30 @@ __global__ void __launch_bounds__(THREADS, 1)
         break;
       }
       tc_fence_after();
-      drain_add<BN>(tmem + lane_base + (uint32_t)(b * BN), sum);
+      if (has_cols) {
+        if (DC == 128) drain_add<128>(tmem + lane_base + (uint32_t)(b * BNT + col0), sum);
+        else drain_add16<DC>(tmem + lane_base + (uint32_t)(b * BNT + col0), sum);
+      }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(acce[b]);
     }
-    if (ok) {  // the cross products, once every MMA has completed
+    if (G::CROSS && ok) {  // the cross products, once every MMA has completed
       const bool w = mbar_wait(done, 0, abort_sh, ep.err, true);
       ok = __all_sync(0xffffffffu, w);
-      if (ok) {
+      if (ok && has_cols) {
         tc_fence_after();
-        drain_add<BN>(tmem + lane_base + (uint32_t)(2 * BN), sum);
+        drain_add<128>(tmem + lane_base + (uint32_t)(2 * BNT + col0), sum);
       }
     }
     const int64_t row = (int64_t)m0 + q * 32 + lane;
-    if (ok && !*abort_sh && row < ep.n) {
+    if (ok && has_cols && !*abort_sh && row < ep.n) {
       const int64_t n = ep.n, n2 = 2 * ep.n;
 #pragma unroll
-      for (int c = 0; c < BN / 32; ++c) {
+      for (int c = 0; c < DC / 32; ++c) {
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
-          const int64_t vg = (int64_t)(n0 >> 2) + c * 8 + t;
+          const int64_t vg = (int64_t)((n0 + col0) >> 2) + c * 8 + t;
           if (vg >= ep.k) continue;
           const float* v = sum + c * 32;
           const float2 ht = make_float2(v[4 * t], v[4 * t + 1]);        // (H x)_top(row)
@@ -464,24 +504,37 @@ static int prepare_p(const cplx* A, const cplx* B, int64_t n, Workspace& ws, POp
   return CHASE_BSE_OK;
 }
 
+// Output tile width: 128 columns.  (256-wide BF16x3 tiles with a 2-stage ring and 16
+// drain warps measured slower at n = 4096, k = 260: 293 against 306 TFLOP/s; the
+// kernel keeps both geometries.)
+template <int NP>
+struct TileN {
+  static constexpr int value = 128;
+};
+
 // One tensor-core application of H to the vectors held in the operand pieces
 // described by bmap, with epilogue `ep`.
 template <int NP>
 static int apply(const POperand& P, const CUtensorMap* bmap, Epi ep, cudaStream_t s) {
-  using G = Geo<NP>;
+  constexpr int BNT = TileN<NP>::value;
+  using G = Geo<NP, BNT>;
   if (ep.k <= 0) return CHASE_BSE_OK;
   static bool attr = false;
   if (!attr) {
-    CB_CUDA(cudaFuncSetAttribute(tc_hop_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM_BYTES));
+    CB_CUDA(cudaFuncSetAttribute(tc_hop_kernel<NP, BNT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 G::SMEM_BYTES));
     attr = true;
   }
   Maps maps;
   for (int q = 0; q < Scheme<NP>::NPA; ++q) maps.a[q] = P.map[q];
   for (int q = 0; q < Scheme<NP>::NPW; ++q) maps.b[q] = bmap[q];
   const int num_m = (int)cdiv(P.n, BM);
-  const int num_n = (int)cdiv(4 * ep.k, BN);
+  const int num_n = (int)cdiv(4 * ep.k, BNT);
+  const int64_t rest = 4 * ep.k - (int64_t)(num_n - 1) * BNT;  // columns of the last tile
+  const int n_last = (int)(((rest + 15) / 16) * 16);
   const int num_kb = (int)(P.kpad / BK);
-  tc_hop_kernel<NP><<<num_m * num_n, THREADS, G::SMEM_BYTES, s>>>(maps, ep, num_kb, num_m, num_n);
+  tc_hop_kernel<NP, BNT><<<num_m * num_n, G::THREADS, G::SMEM_BYTES, s>>>(maps, ep, num_kb, num_m, num_n,
+                                                                          n_last);
   count_launch();
   CB_LAUNCH();
   return CHASE_BSE_OK;
@@ -500,13 +553,13 @@ static int filter_impl(const cplx* A, const cplx* B, int64_t n, const cplx* Y0, 
                        double mu1, double mu_nevex, double muN, cplx* out, const double* ritz, const cplx* R,
                        cudaStream_t s, FilterStats* fs) {
   constexpr int NPW = Scheme<NP>::NPW;
-  using G = Geo<NP>;
   if (k == 0) return CHASE_BSE_OK;
   const int64_t n2 = 2 * n;
   Workspace ws(s);
   POperand P;
   CB_TRY(prepare_p<NP>(A, B, n, ws, P, s));
-  const int64_t rows = ((4 * k + BN - 1) / BN) * BN;  // whole tiles
+  constexpr int BNT = TileN<NP>::value;
+  const int64_t rows = ((4 * k + BNT - 1) / BNT) * BNT;  // whole tiles
   Pieces Zp{}, Tp{};
   CUtensorMap mZ[3], mT[3];
   for (int q = 0; q < NPW; ++q) {
@@ -514,8 +567,8 @@ static int filter_impl(const cplx* A, const cplx* B, int64_t n, const cplx* Y0, 
     CB_TRY(ws.alloc(&Tp.p[q], rows * P.kpad));
     CB_CUDA(cudaMemsetAsync(Zp.p[q], 0, sizeof(__nv_bfloat16) * rows * P.kpad, s));
     CB_CUDA(cudaMemsetAsync(Tp.p[q], 0, sizeof(__nv_bfloat16) * rows * P.kpad, s));
-    CB_TRY(make_map(&mZ[q], Zp.p[q], P.kpad, rows, BN));
-    CB_TRY(make_map(&mT[q], Tp.p[q], P.kpad, rows, BN));
+    CB_TRY(make_map(&mZ[q], Zp.p[q], P.kpad, rows, BNT));
+    CB_TRY(make_map(&mT[q], Tp.p[q], P.kpad, rows, BNT));
   }
   float2 *Zb[3], *src = nullptr;
   float* gam;
