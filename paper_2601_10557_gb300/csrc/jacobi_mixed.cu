@@ -3,13 +3,23 @@
 //
 // GB300 runs FP32 at 64x its FP64 rate, so the bulk of the Jacobi work (the early
 // sweeps, which rotate every pair) runs in FP32; FP64 accuracy is then recovered
-// with FP64-accurate tensor-core GEMMs (sliced GEMM) and a short FP64 Jacobi:
+// with FP64-accurate tensor-core GEMMs (sliced GEMM) and, if needed, a short FP64 Jacobi:
 //   1. FP32 Jacobi on G (scaled to ||G||_F ~ 1) until every |g_pq| is below
-//      2e-6 sqrt|g_pp g_qq| (the FP32 rotations need not be exactly unitary);
-//   2. V1 = the FP32 eigenvector matrix made unitary in FP64 by two Newton-Schulz
-//      steps X <- X (3I - X^* X) / 2 (the error 1e-5 -> 1e-10 -> 1e-20);
-//   3. G1 = V1^* G V1 (diagonal up to the FP32 level), hermitised;
-//   4. FP64 Jacobi on G1 (two or three sweeps from the FP32 level), V = V1 V2.
+//      2e-6 sqrt|g_pp g_qq| or 1e-8 ||G|| (the FP32 rotations need not be exactly
+//      unitary);
+//   2. two steps of the iterative refinement of Ogita and Aishima (2018, Japan J.
+//      Indust. Appl. Math.) on X = the FP32 eigenvectors in FP64: with
+//      R = I - X^* X and S = X^* G X, lam_i = s_ii / (1 - r_ii) and
+//      X <- X (I + E), E_ij = (s_ij + lam_j r_ij) / (lam_j - lam_i) where that
+//      correction is small (a pair test symmetric in i and j; the published method
+//      separates clusters by a norm bound delta), else r_ij / 2, E_ii = r_ii / 2
+//      (the first-order terms of X = X^ (I + E), X^* X = I, X^* G X diagonal);
+//      each step squares the error of the separated pairs (a third step can
+//      amplify the noise of nearly equal pairs, so there are two), and all the
+//      arithmetic is in FP64-accurate tensor-core GEMMs;
+//   3. G1 = X^* G X, hermitised;
+//   4. FP64 Jacobi on G1 (what the refinement left: near-degenerate pairs, often
+//      nothing), V = X V2.
 // The FP32 sweep has the FP64 sweep's structure: one cooperative kernel per sweep,
 // one grid barrier per round, G ping-ponged, the next round's rotations formed by
 // the threads that produce their pivots, V updated afterwards over the stored
@@ -18,6 +28,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <vector>
 
 #include "coop.cuh"
 #include "dense_kernels.cuh"
@@ -36,10 +48,12 @@ __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
   return mkf(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-// rotate when |g_pq|^2 > t2 |g_pp g_qq| and |g_pq|^2 > t2 / 4 ||G||^2 (G scaled: ||G||_F ~ 1)
+// rotate when |g_pq| > t sqrt|g_pp g_qq| (t2 = t^2) and |g_pq| > 1e-8 ||G|| (n2 = ||G||^2,
+// G scaled to ||G||_F ~ 1): the FP32 phase hands over eigenvectors accurate relative to
+// the diagonal, which the first-order refinement needs for nearly equal pairs
 __device__ __forceinline__ bool active32(float app, float aqq, float2 apq, float t2, float n2) {
   const float r2 = fmaf(apq.x, apq.x, apq.y * apq.y);
-  return r2 > t2 * fabsf(app * aqq) && r2 > 0.25f * t2 * n2 && r2 > 0.0f;
+  return r2 > t2 * fabsf(app * aqq) && r2 > 1e-16f * n2 && r2 > 0.0f;
 }
 __device__ Rot32 rotation32(float app, float aqq, float2 apq, float t2, float n2, int* applied) {
   Rot32 R{1.0f, 0.0f, 1.0f, 0.0f};
@@ -215,13 +229,70 @@ __global__ void to64_kernel(const float2* V32, int64_t total, cplx* V) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
     V[i] = mk((double)V32[i].x, (double)V32[i].y);
 }
-// T = (3 I - S) / 2
-__global__ void ns_kernel(const cplx* S, int64_t k, cplx* T) {
-  const int64_t total = k * k;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const cplx v = S[i];
-    T[i] = mk(((i % k) == (i / k) ? 1.5 : 0.0) - 0.5 * v.x, -0.5 * v.y);
+
+// lam_i = S_ii / (X^* X)_ii  (= s_ii / (1 - r_ii) with R = I - X^* X)
+__global__ void oa_lambda_kernel(const cplx* S, const cplx* S1, int64_t k, double* lam) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < k) lam[i] = S[i + i * k].x / S1[i + i * k].x;
+}
+// E_ij = (S_ij + lam_j R_ij) / (lam_j - lam_i) when that first-order correction is small
+// for the pair (|S_ij| + max(|lam_i|, |lam_j|) |R_ij| <= 1e-2 |lam_j - lam_i|, a test
+// symmetric in i and j so that E + E^* = R still holds), R_ij / 2 otherwise (R = I - S1):
+// the first-order terms of X = X^ (I + E) with X^* X = I and X^* G X diagonal.  Pairs
+// of nearly equal lam are only re-orthogonalised; the FP64 Jacobi afterwards separates
+// them.
+__global__ void oa_correction_kernel(const cplx* S, const cplx* S1, const double* lam, int64_t k, cplx* E) {
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < k * k;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx % k, j = idx / k;
+    const cplx r1 = S1[idx];
+    const cplx r = (i == j) ? mk(1.0 - r1.x, -r1.y) : mk(-r1.x, -r1.y);
+    const double gap = lam[j] - lam[i];
+    const cplx sv = S[idx];
+    const double bound = sqrt(cabs2(sv)) + fmax(fabs(lam[i]), fabs(lam[j])) * sqrt(cabs2(r));
+    if (i != j && bound <= 1e-2 * fabs(gap)) {
+      E[idx] = mk((sv.x + lam[j] * r.x) / gap, (sv.y + lam[j] * r.y) / gap);
+    } else {
+      E[idx] = mk(0.5 * r.x, 0.5 * r.y);
+    }
   }
+}
+// flags[i] = 1 for every index i of a pair (i, j) that the FP64 Jacobi would still
+// rotate: |g_ij| > t sqrt|g_ii g_jj| and |g_ij| > (t/2) ||G||_F
+__global__ void mark_active_kernel(const cplx* G, int64_t k, double t2, double n2, int* flags) {
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < k * k;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = idx % k, q = idx / k;
+    if (p >= q) continue;
+    const double r2 = cabs2(G[idx]);
+    if (r2 > t2 * fabs(G[p + p * k].x * G[q + q * k].x) && r2 > 0.25 * t2 * n2) {
+      flags[p] = 1;
+      flags[q] = 1;
+    }
+  }
+}
+// sub = G[act, act] (m x m)
+__global__ void gather_sub_kernel(const cplx* G, int64_t k, const int* act, int64_t m, cplx* sub) {
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < m * m;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx % m, j = idx / m;
+    sub[idx] = G[act[i] + (int64_t)act[j] * k];
+  }
+}
+// V2 = I with V2[act, act] = Vs; theta[act[i]] = ts[i]
+__global__ void scatter_sub_kernel(const cplx* Vs, const double* ts, const int* act, int64_t m, int64_t k, cplx* V2,
+                                   double* theta) {
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < m * m;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx % m, j = idx / m;
+    V2[act[i] + (int64_t)act[j] * k] = Vs[idx];
+    if (i == j) theta[act[i]] = ts[i];
+  }
+}
+
+__global__ void add_kernel(cplx* X, const cplx* D, int64_t total) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
+    X[i] = cadd(X[i], D[i]);
 }
 
 static unsigned gsz(int64_t total) {
@@ -334,18 +405,83 @@ int jacobi_eigh_mixed(cplx* G, int64_t k, cplx* V, double* theta, cplx* rot, dou
   to64_kernel<<<gsz(k * k), 256, 0, s>>>(V32, k * k, X);
   count_launch();
   CB_LAUNCH();
+  // two steps of the Ogita-Aishima refinement: R = I - X^* X, S = X^* G X,
+  // lam_i = s_ii / (1 - r_ii), X <- X (I + E) with the first-order correction E
+  double* lamd;
+  CB_TRY(ws.alloc(&lamd, k));
   for (int it = 0; it < 2; ++it) {
-    CB_TRY(gemm_hn(X, X, k, S, ws, sa, sb, s));
-    ns_kernel<<<gsz(k * k), 256, 0, s>>>(S, k, Y);
+    CB_TRY(gemm_hn(X, X, k, S, ws, sa, sb, s));   // S = X^* X
+    CB_TRY(gemm_nn(G, X, k, Y, tmp, sr, sb, s));  // Y = G X
+    CB_TRY(gemm_hn(X, Y, k, G1, ws, sa, sb, s));  // G1 = X^* G X
+    oa_lambda_kernel<<<(unsigned)((k + 255) / 256), 256, 0, s>>>(G1, S, k, lamd);
+    count_launch();
+    oa_correction_kernel<<<gsz(k * k), 256, 0, s>>>(G1, S, lamd, k, Y);
     count_launch();
     CB_LAUNCH();
-    CB_TRY(gemm_nn(X, Y, k, S, tmp, sr, sb, s));
-    std::swap(X, S);
+    CB_TRY(gemm_nn(X, Y, k, S, tmp, sr, sb, s));  // S = X E
+    add_kernel<<<gsz(k * k), 256, 0, s>>>(X, S, k * k);
+    count_launch();
+    CB_LAUNCH();
   }
   CB_TRY(gemm_nn(G, X, k, Y, tmp, sr, sb, s));  // Y = G V1
   CB_TRY(gemm_hn(X, Y, k, G1, ws, sa, sb, s));  // G1 = V1^* G V1
   CB_TRY(hermitize(G1, k, s));
-  CB_TRY(jacobi_eigh(G1, k, V2, theta, rot, red, 40, sweeps64_out, s, thr));
+  // What the refinement left (pairs of nearly equal eigenvalues) couples few indices:
+  // the FP64 Jacobi runs on the sub-problem of the indices in a pair above the
+  // threshold; the couplings between those and the others are below it.
+  int* flags;
+  CB_TRY(ws.alloc(&flags, k));
+  CB_CUDA(cudaMemsetAsync(flags, 0, sizeof(int) * k, s));
+  CB_TRY(offdiag_norms(G1, k, red, s));
+  double g1[2];
+  CB_CUDA(cudaMemcpyAsync(g1, red, sizeof(g1), cudaMemcpyDeviceToHost, s));
+  CB_CUDA(cudaStreamSynchronize(s));
+  const double tt = std::max(thr, 2e-16);
+  mark_active_kernel<<<gsz(k * k), 256, 0, s>>>(G1, k, tt * tt, g1[1], flags);
+  count_launch();
+  CB_LAUNCH();
+  std::vector<int> hf(k);
+  CB_CUDA(cudaMemcpyAsync(hf.data(), flags, sizeof(int) * k, cudaMemcpyDeviceToHost, s));
+  CB_CUDA(cudaStreamSynchronize(s));
+  std::vector<int> act;
+  for (int64_t i = 0; i < k; ++i)
+    if (hf[i]) act.push_back((int)i);
+  if (act.size() % 2)  // the Jacobi pairs indices: add one inactive index
+    for (int64_t i = 0; i < k; ++i)
+      if (!hf[i]) {
+        act.push_back((int)i);
+        break;
+      }
+  const int64_t m = (int64_t)act.size();
+  if (verbose()) fprintf(stderr, "[chase_bse] jacobi k %ld: FP32 %d sweeps, FP64 on %ld active indices\n", (long)k,
+                         sw, (long)m);
+  if (m > k / 2) {  // most indices still coupled: the whole problem
+    CB_TRY(jacobi_eigh(G1, k, V2, theta, rot, red, 40, sweeps64_out, s, thr));
+    return jm::gemm_nn(X, V2, k, V, tmp, sr, sb, s);  // V = V1 V2
+  }
+  CB_TRY(diag_real(G1, k, theta, s));
+  if (m == 0) {
+    if (sweeps64_out) *sweeps64_out = 0;
+    CB_CUDA(cudaMemcpyAsync(V, X, sizeof(cplx) * k * k, cudaMemcpyDeviceToDevice, s));
+    return CHASE_BSE_OK;
+  }
+  int* actd;
+  cplx *sub, *Vs;
+  double* ts;
+  CB_TRY(ws.alloc(&actd, m));
+  CB_TRY(ws.alloc(&sub, m * m));
+  CB_TRY(ws.alloc(&Vs, m * m));
+  CB_TRY(ws.alloc(&ts, m));
+  CB_CUDA(cudaMemcpyAsync(actd, act.data(), sizeof(int) * m, cudaMemcpyHostToDevice, s));
+  gather_sub_kernel<<<gsz(m * m), 256, 0, s>>>(G1, k, actd, m, sub);
+  count_launch();
+  CB_LAUNCH();
+  CB_TRY(jacobi_eigh(sub, m, Vs, ts, rot, red, 40, sweeps64_out, s, thr));
+  CB_TRY(set_identity(V2, k, s));
+  scatter_sub_kernel<<<gsz(m * m), 256, 0, s>>>(Vs, ts, actd, m, k, V2, theta);
+  count_launch();
+  CB_LAUNCH();
+  CB_CUDA(cudaStreamSynchronize(s));  // act (host) outlives its copy
   return jm::gemm_nn(X, V2, k, V, tmp, sr, sb, s);  // V = V1 V2
 }
 
