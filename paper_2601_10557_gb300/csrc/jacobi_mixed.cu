@@ -1,5 +1,5 @@
 // Mixed-precision eigensolver for the small hermitian problem of the oblique
-// Rayleigh-Ritz step (Algorithm 2, line 8), for G far from diagonal.
+// Rayleigh-Ritz step (G y = theta y in Algorithm 2), for G far from diagonal.
 //
 // GB300 runs FP32 at 64x its FP64 rate, so the bulk of the Jacobi work (the early
 // sweeps, which rotate every pair) runs in FP32; FP64 accuracy is then recovered

@@ -385,24 +385,24 @@ int rayleigh_ritz(const cplx* A, const cplx* B, int64_t n, const cplx* Q, int64_
   CB_TRY(ws.alloc(&red, 2));
   CB_TRY(ws.alloc(&info_d, 1));
   CB_TRY(ws.alloc(&idx_d, h));
-  // T = S H Q (Algorithm 2, lines 1-2), M = Q^* T (line 3)
+  // Algorithm 2: T = S H Q, M = Q^* T
   HopArgs a{};
   a.A = A; a.B = B; a.n = n; a.W = Q; a.k = k; a.out = T; a.mode = HOP_STORE; a.sflip = 1;
   CB_TRY(hop_fp64(a, s));
   CB_TRY(zgemm('C', 'N', k, k, n2, mk(1, 0), Q, n2, T, n2, mk(0, 0), M, k, s));
   CB_TRY(hermitize(M, k, s));
   int info = 0;
-  CB_TRY(cholesky(M, k, info_d, &info, s));  // line 4: M = L L^*
+  CB_TRY(cholesky(M, k, info_d, &info, s));  // M = L L^*
   if (info != 0) return CHASE_BSE_NOT_DEFINITE;
   CB_TRY(tri_inverse(M, k, Linv, scratch, s));
-  // line 5: M2 = I - 2 Q_2^* Q_2 (= Q^* S Q)
+  // M2 = I - 2 Q_2^* Q_2 (= Q^* S Q)
   CB_TRY(set_identity(M2, k, s));
   CB_TRY(zgemm('C', 'N', k, k, n, mk(-2, 0), Q + n, n2, Q + n, n2, mk(1, 0), M2, k, s));
-  // line 7: G = L^{-1} M2 L^{-*}
+  // G = L^{-1} M2 L^{-*}
   CB_TRY(zgemm('N', 'N', k, k, k, mk(1, 0), Linv, k, M2, k, mk(0, 0), Tmp, k, s));
   CB_TRY(zgemm('N', 'C', k, k, k, mk(1, 0), Tmp, k, Linv, k, mk(0, 0), G, k, s));
   CB_TRY(hermitize(G, k, s));
-  // line 8: G y = theta y
+  // G y = theta y
   int sweeps = 0;
   const auto tj = std::chrono::steady_clock::now();
   CB_TRY(jacobi_eigh(G, k, V, theta, rot, red, 40, &sweeps, s));
@@ -424,7 +424,7 @@ int rayleigh_ritz(const cplx* A, const cplx* B, int64_t n, const cplx* Q, int64_
   for (int64_t i = 0; i < h; ++i) ritz_host[i] = 1.0 / th[pos[i]];
   CB_CUDA(cudaMemcpyAsync(idx_d, pos.data(), sizeof(int) * h, cudaMemcpyHostToDevice, s));
   CB_TRY(gather_cols(Ypos, V, idx_d, k, h, s));
-  // line 9 (read as z = L^{-*} y) and the half back-transform W+ = Q Z+
+  // the back-substitution (read as z = L^{-*} y) and the half back-transform W+ = Q Z+
   CB_TRY(zgemm('C', 'N', k, h, k, mk(1, 0), Linv, k, Ypos, k, mk(0, 0), Z, k, s));
   CB_TRY(zgemm('N', 'N', n2, h, k, mk(1, 0), Q, n2, Z, k, mk(0, 0), Wpos, n2, s));
   if (R && res) {
@@ -590,7 +590,7 @@ static int rayleigh_ritz_jfixed(const cplx* A, const cplx* B, int64_t n, const c
   CB_TRY(ws.alloc(&info_d, 1));
   CB_TRY(ws.alloc(&idx_d, h));
   StageTimer tm(s, "rr(J)");
-  // lines 1-3: T = S H Q (top halves y = A x + B conj x), M = Q^* T = 2 Re(X^* Y)
+  // Algorithm 2: T = S H Q (top halves y = A x + B conj x), M = Q^* T = 2 Re(X^* Y)
   if (sliced) {
     CB_TRY(slice_rows(reinterpret_cast<const double*>(Qt), 2 * n, 0, sq, s));
     CB_TRY(sliced_gemm(*ph, sq, 1.0, reinterpret_cast<double*>(Tt), 1, 2 * n, false, s));
@@ -611,10 +611,10 @@ static int rayleigh_ritz_jfixed(const cplx* A, const cplx* B, int64_t n, const c
   }
   CB_TRY(pair_transform(Tmp, M, k, s));
   int info = 0;
-  CB_TRY(cholesky(M, k, info_d, &info, s));  // line 4
+  CB_TRY(cholesky(M, k, info_d, &info, s));  // M = L L^*
   if (info != 0) return CHASE_BSE_NOT_DEFINITE;
   CB_TRY(tri_inverse(M, k, Linv, scratch, s));
-  // line 5: Q^* S Q = 2 i Im(X^* X)
+  // Q^* S Q = 2 i Im(X^* X)
   if (sliced) {  // Im(x_i^* x_j) = x_i . (Im x_j, -Re x_j) on (re, im) pairs
     CB_TRY(slice_rows(reinterpret_cast<const double*>(Qt), 2 * n, 1, sqr, s));
     CB_CUDA(cudaMemsetAsync(Tmp, 0, sizeof(cplx) * k * k, s));
@@ -624,7 +624,7 @@ static int rayleigh_ritz_jfixed(const cplx* A, const cplx* B, int64_t n, const c
     CB_TRY(re_im_part(C, Tmp, k, 1, s));
   }
   CB_TRY(pair_transform(Tmp, M2, k, s));
-  // line 7: G = L^{-1} M2 L^{-*}
+  // G = L^{-1} M2 L^{-*}
   SlicedOp sl_rows, sl_b;  // real-form rows of a k x k factor, and the right operand
   if (sliced) {
     CB_TRY(sliced_alloc(ws, sl_rows, 2 * k, 2 * k, s));
@@ -643,7 +643,7 @@ static int rayleigh_ritz_jfixed(const cplx* A, const cplx* B, int64_t n, const c
   tm.mark("small");
   int sweeps = 0;
   int sweeps32 = 0;
-  if (sliced) CB_TRY(jacobi_eigh_mixed(G, k, V, theta, rot, red, &sweeps32, &sweeps, s, jthr));  // line 8
+  if (sliced) CB_TRY(jacobi_eigh_mixed(G, k, V, theta, rot, red, &sweeps32, &sweeps, s, jthr));  // G y = theta y
   else CB_TRY(jacobi_eigh(G, k, V, theta, rot, red, 40, &sweeps, s, jthr));
   tm.mark("jacobi");
   std::vector<double> th(k);
@@ -658,7 +658,7 @@ static int rayleigh_ritz_jfixed(const cplx* A, const cplx* B, int64_t n, const c
   CB_CUDA(cudaMemcpyAsync(idx_d, pos.data(), sizeof(int) * h, cudaMemcpyHostToDevice, s));
   CB_CUDA(cudaMemcpyAsync(rz, ritz_host, sizeof(double) * h, cudaMemcpyHostToDevice, s));
   CB_TRY(gather_cols(Ypos, V, idx_d, k, h, s));
-  // line 9 (z = L^{-*} y), back to the J-fixed basis (Z = U Z');
+  // z = L^{-*} y, back to the J-fixed basis (Z = U Z');
   // W+ = Q Z+ = [X Z; conj(X) Z]; S H W+ = [Y Z; conj(Y) Z]
   if (sliced) {  // Tmp = L^{-*} Y+: rows of L^{-*} are the conjugated columns of L^{-1}
     CB_TRY(conj_transpose(Linv, k, M2, s));
@@ -839,7 +839,7 @@ int solve(const cplx* A, const cplx* B, int64_t n, int64_t nev, int64_t nex, int
   std::vector<double> ritz_keep;  // Ritz values of the columns of W (mixed correction form)
   PhaseClock clk(s);
 
-  // Algorithm 3 line 1: W+ = randn(2n, nevex), lower half scaled by gamma
+  // Algorithm 3 start: W+ = randn(2n, nevex), lower half scaled by gamma
   if (o.W0) CB_CUDA(cudaMemcpyAsync(W, o.W0, sizeof(cplx) * n2 * nevex, cudaMemcpyDeviceToDevice, s));
   else CB_TRY(randn_complex(W, n2 * nevex, o.seed, 1, s));
   CB_TRY(scale_lower(W, n, nevex, o.gamma, s));
@@ -855,7 +855,7 @@ int solve(const cplx* A, const cplx* B, int64_t n, int64_t nev, int64_t nex, int
     CB_TRY(slice_hamiltonian(A, B, n, ph, s));
   }
 
-  // line 2: spectral bounds
+  // spectral bounds
   clk.start();
   double mu[4];
   CB_TRY(lanczos_bounds(A, B, n, V0, o.lanczos_vecs, o.lanczos_steps, nevex, mu, s, sliced ? &ph : nullptr));
@@ -880,13 +880,13 @@ int solve(const cplx* A, const cplx* B, int64_t n, int64_t nev, int64_t nex, int
     const auto it_start = std::chrono::steady_clock::now();
     const double ph0 = st.ms_filter + st.ms_qr + st.ms_rr + st.ms_resid;
     const int64_t kf = nevex - locked;
-    // line 4: W+ <- p(H^2) W+
+    // filter: W+ <- p(H^2) W+
     clk.start();
     const bool corr = mixed && !ritz_keep.empty();
     CB_TRY(filter(A, B, n, W, kf, degs.data(), prec.data(), mu1, mu_ne, muN, scheme,
                   corr ? ritz_keep.data() : nullptr, corr ? Rkeep : nullptr, s, &fs));
     st.ms_filter += clk.stop();
-    // lines 5-7: W- = K conj(W+), Q = [S Y+, S Y-, W+, W-] R^{-1}, drop the locked part;
+    // orthonormalisation: W- = K conj(W+), Q = [S Y+, S Y-, W+, W-] R^{-1}, drop the locked part;
     // J-fixed basis (top halves) unless its CholeskyQR2 breaks down
     clk.start();
     CB_TRY(build_jfixed(X, Ylock, locked, W, kf, n, s));
@@ -904,7 +904,7 @@ int solve(const cplx* A, const cplx* B, int64_t n, int64_t nev, int64_t nex, int
     cplx* Rvec = Rall;
     Workspace rws(s);
     if (!Rvec) CB_TRY(rws.alloc(&Rvec, n2 * kf));
-    // lines 8-11: Rayleigh-Ritz, W+ = Q Z+ and the residuals of the positive half
+    // Rayleigh-Ritz, W+ = Q Z+ and the residuals of the positive half
     // Jacobi accuracy of the small eigenproblem: the Ritz vectors need not be more
     // accurate than the subspace they come from; 1e-4 of the smallest residual of the
     // previous iteration (1e-8 before the first), down to the rounding level
@@ -928,7 +928,7 @@ int solve(const cplx* A, const cplx* B, int64_t n, int64_t nev, int64_t nex, int
       fprintf(stderr, "[chase_bse] it %d locked %ld kf %ld res0 %.3e resmax %.3e mu %.6g %.6g %.6g hh %d\n", it,
               (long)locked, (long)kf, res[0], mx, mu1, mu_ne, muN, hh);
     }
-    // lines 12-14: lock converged positive pairs
+    // lock converged positive pairs
     const int64_t want = std::min<int64_t>(nev - locked, kf);
     std::vector<int> conv, keep;
     for (int64_t i = 0; i < kf; ++i) {

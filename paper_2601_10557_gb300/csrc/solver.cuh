@@ -30,7 +30,7 @@ int qr(const cplx* X, int64_t n2, int64_t m, cplx* Q, int* used_hh, cudaStream_t
 
 // Algorithm 2 on Q (2n x k): ritz (host, k/2 ascending) and Wpos (2n x k/2).
 // With R and res (device), also the residual vectors R = H Wpos - Wpos diag(ritz)
-// and their norms, from H Wpos = S T Z+ (T = S H Q of line 2: no extra H product).
+// and their norms, from H Wpos = S T Z+ (T = S H Q of the Rayleigh-Ritz step: no extra H product).
 int rayleigh_ritz(const cplx* A, const cplx* B, int64_t n, const cplx* Q, int64_t k, double* ritz_host,
                   cplx* Wpos, cudaStream_t s, cplx* R = nullptr, double* res = nullptr);
 

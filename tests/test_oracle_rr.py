@@ -26,7 +26,7 @@ def test_qsq_identity_and_pm_symmetry():
     Wp[n:] *= 1e-3
     Q = _basis(Wp)
     ritz, W, theta, M2 = rr.rayleigh_ritz(P.A, P.B, Q, return_all=True)
-    # Algorithm 2 line 5: I - 2 Q_2^* Q_2 = Q^* S Q
+    # Algorithm 2: I - 2 Q_2^* Q_2 = Q^* S Q
     np.testing.assert_allclose(M2, Q.conj().T @ s_flip(Q), atol=1e-13)
     # Theorem positive-negative-symmetry_oblique_RR: spectrum of G is +- symmetric
     np.testing.assert_allclose(np.sort(theta), -np.sort(theta)[::-1], atol=1e-12 * np.abs(theta).max())
