@@ -16,13 +16,13 @@
 //   BF16x3: 2 pieces each, x0 y0 + x0 y1 + x1 y0          (~16 bits, ~1.5e-5)
 //   BF16x6: 3 pieces each, adds x0 y2 + x1 y1 + x2 y0      (FP32 class, ~2e-7)
 //
-// Kernel structure (one 128 x 128 output tile per CTA, 256 threads):
+// Kernel structure (one 128 x 128 output tile per CTA, 384 threads):
 //   warp 0   TMA producer: the A and B pieces of 64 K-elements (128B swizzle)
 //            into a 3-stage (BF16x3) or 2-stage (BF16x6) shared-memory ring
 //   warp 1   allocates all 512 TMEM columns (two accumulator buffers, each a
 //            hi*hi accumulator and one for the cross products); one lane issues
 //            the tcgen05.mma of a K block into buffer kb & 1
-//   warps 4-7 drain each K block's partial sums (tcgen05.ld) into FP32
+//   warps 4-11 drain the partial sums of every FLUSH K blocks (tcgen05.ld) into FP32
 //            registers while the next block accumulates in the other buffer,
 //            because the tensor core's FP32 accumulation truncates; then either
 //            (mode 0) store the next GEMM's B-operand planes, or
@@ -51,7 +51,6 @@ constexpr int BM = 128, BK = 64;
 constexpr int A_BYTES = BM * BK * 2;  // 16 KB per piece
 constexpr int GROUP_M = 8;            // tile raster: GROUP_M row tiles x all column tiles per group
 constexpr uint32_t TMEM_COLS = 512;   // two accumulator buffers (+ the cross products for 128-wide tiles)
-constexpr int FLUSH = 2;              // K blocks per drained partial sum
 // instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, 128 x n
 __device__ __forceinline__ uint32_t make_idesc(int n) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
@@ -62,23 +61,26 @@ template <int NP>
 struct Scheme;
 template <>
 struct Scheme<3> {  // BF16x3
-  static constexpr int NPA = 2, NPW = 2, NPROD = 3, STAGES = 3;
+  // FLUSH: K blocks per drained partial sum of x0 * y0 (16 truncating MMA additions
+  // stay far below the 2^-16 error of the BF16 pieces; measured unchanged from 8)
+  static constexpr int NPA = 2, NPW = 2, NPROD = 3, STAGES = 3, FLUSH = 4;
   __device__ static constexpr int pa(int i) { return i == 2 ? 1 : 0; }
   __device__ static constexpr int pb(int i) { return i == 1 ? 1 : 0; }
 };
 template <>
 struct Scheme<6> {  // BF16x6
-  static constexpr int NPA = 3, NPW = 3, NPROD = 6, STAGES = 2;
+  static constexpr int NPA = 3, NPW = 3, NPROD = 6, STAGES = 2, FLUSH = 2;
   // (0,0) (0,1) (1,0) (0,2) (1,1) (2,0)
   __device__ static constexpr int pa(int i) { return i == 2 ? 1 : (i == 4 ? 1 : (i == 5 ? 2 : 0)); }
   __device__ static constexpr int pb(int i) { return i == 1 ? 1 : (i == 3 ? 2 : (i == 4 ? 1 : 0)); }
 };
 // Tile geometry for BNT-wide output tiles.  128-wide: the x0 * y0 product drains from
 // two alternating TMEM buffers and the cross products accumulate over all of K in a
-// third; 4 drain warps of 128 columns.  256-wide (BF16x3 only): all products share the
-// two alternating buffers (drained every FLUSH K blocks, so the truncating accumulator
-// sums at most FLUSH * 4 * NPROD MMAs); 16 drain warps of 64 columns keep the FP32
-// partial sums in registers; a 2-stage ring of 96 KB.
+// third; 8 drain warps of 64 columns (two per TMEM lane quarter: half the drain latency
+// of 4 warps of 128 columns, and 135 registers a thread instead of 228).  256-wide
+// (BF16x3 only): all products share the two alternating buffers (drained every FLUSH
+// K blocks, so the truncating accumulator sums at most FLUSH * 4 * NPROD MMAs); 16 drain
+// warps of 64 columns keep the FP32 partial sums in registers; a 2-stage ring of 96 KB.
 template <int NP, int BNT>
 struct Geo {
   static constexpr int STAGES = (BNT == 256) ? 2 : Scheme<NP>::STAGES;
@@ -87,7 +89,7 @@ struct Geo {
   static constexpr int NBAR = 2 * STAGES + 5;  // full, empty, acc_full[2], acc_empty[2], done
   static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
   static constexpr bool CROSS = (BNT == 128);             // separate cross-product buffer
-  static constexpr int DCOLS = (BNT == 128) ? 128 : 64;    // columns per drain warp
+  static constexpr int DCOLS = 64;                         // columns per drain warp
   static constexpr int DRAIN_WARPS = 4 * (BNT / DCOLS);
   static constexpr int THREADS = 128 + 32 * DRAIN_WARPS;
   static_assert(STAGE_BYTES * STAGES + 1280 <= 232448, "shared memory");
@@ -195,6 +197,7 @@ __global__ void __launch_bounds__(Geo<NP, BNT>::THREADS, 1)
   using G = Geo<NP, BNT>;
   constexpr int ST = G::STAGES;
   constexpr int DC = G::DCOLS;
+  constexpr int FLUSH = SC::FLUSH;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + ST * G::STAGE_BYTES);
@@ -320,7 +323,7 @@ __global__ void __launch_bounds__(Geo<NP, BNT>::THREADS, 1)
       }
       tc_fence_after();
       if (has_cols) {
-        if (DC == 128) drain_add<128>(tmem + lane_base + (uint32_t)(b * BNT + col0), sum);
+        if (G::CROSS) drain_add<DC>(tmem + lane_base + (uint32_t)(b * BNT + col0), sum);
         else drain_add16<DC>(tmem + lane_base + (uint32_t)(b * BNT + col0), sum);
       }
       tc_fence_before();
@@ -332,7 +335,7 @@ __global__ void __launch_bounds__(Geo<NP, BNT>::THREADS, 1)
       ok = __all_sync(0xffffffffu, w);
       if (ok && has_cols) {
         tc_fence_after();
-        drain_add<128>(tmem + lane_base + (uint32_t)(2 * BNT + col0), sum);
+        drain_add<DC>(tmem + lane_base + (uint32_t)(2 * BNT + col0), sum);
       }
     }
     const int64_t row = (int64_t)m0 + q * 32 + lane;
