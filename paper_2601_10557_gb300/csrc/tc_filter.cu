@@ -108,6 +108,43 @@ struct Epi {
   const float* gamma;  // per column
   float alpha, beta, c;
   int* err;
+  float* part;  // split-K: one FP32 partial tile per CTA, column-major 128 x BNT
+  int* cnt;     // split-K: per tile, partial tiles written so far (zero between launches)
+  int sms;      // SMs of the device
+};
+
+// Work of one launch: every output tile (the full-width tiles in a grouped raster, then
+// the narrow last column tile of every row block) in nsplit K ranges.  CTA c takes split
+// c / ntiles of tile c % ntiles, so that the CTAs running at the same time stream the
+// same K blocks of A (one DRAM read serves every column tile of a row block).  With
+// nsplit > 1 the splits leave FP32 partial tiles; the CTA that writes a tile's last one
+// (a per-tile counter) sums them in split order and runs the epilogue, so no CTA waits
+// for another and the result does not depend on timing.
+struct Sched {
+  int nkb, num_m, num_n, nfull, ntiles, n_last, bnt, nsplit;
+  __device__ void unit(int c, int& t, int& kb0, int& kb1) const {
+    const int sp = c / ntiles;
+    t = c - sp * ntiles;
+    kb0 = (int)((int64_t)nkb * sp / nsplit);
+    kb1 = (int)((int64_t)nkb * (sp + 1) / nsplit);
+  }
+  // row and column origin and width of tile t
+  __device__ void origin(int t, int& m0, int& n0, int& ncols) const {
+    if (t < nfull) {
+      const int nnf = num_n - (ntiles > nfull ? 1 : 0);
+      const int per_group = GROUP_M * nnf;
+      const int g = t / per_group, first_m = g * GROUP_M;
+      const int gm = min(GROUP_M, num_m - first_m);
+      const int rem = t - g * per_group;
+      m0 = (first_m + rem % gm) * BM;
+      n0 = (rem / gm) * bnt;
+      ncols = bnt;
+    } else {
+      m0 = (t - nfull) * BM;
+      n0 = (num_n - 1) * bnt;
+      ncols = n_last;
+    }
+  }
 };
 
 // Shared-memory matrix descriptor: K-major tile written by TMA with 128-byte
@@ -183,16 +220,16 @@ struct Maps {
   CUtensorMap b[3];
 };
 
-// One 128 x BNT output tile per CTA.  Every K block's products accumulate in one of
-// two TMEM buffers that alternate every FLUSH K blocks; the drain warps add each
-// finished buffer into FP32 registers (round to nearest) while the MMA fills the
-// other one, so the tensor core's truncating accumulator only ever sums a few
-// MMAs.  With 128-wide tiles the cross products (2^-8 smaller) accumulate over the
-// whole K in a third buffer instead.  The last column tile may be narrower
+// One K range of one 128 x BNT output tile per CTA.  Every K block's products
+// accumulate in one of two TMEM buffers that alternate every FLUSH K blocks; the drain
+// warps add each finished buffer into FP32 registers (round to nearest) while the MMA
+// fills the other one, so the tensor core's truncating accumulator only ever sums a
+// few MMAs.  With 128-wide tiles the cross products (2^-8 smaller) accumulate over the
+// whole K range in a third buffer instead.  The last column tile may be narrower
 // (n_last columns, a multiple of 16): its MMAs use N = n_last.
 template <int NP, int BNT>
 __global__ void __launch_bounds__(Geo<NP, BNT>::THREADS, 1)
-    tc_hop_kernel(const __grid_constant__ Maps maps, Epi ep, int num_kb, int num_m, int num_n, int n_last) {
+    tc_hop_kernel(const __grid_constant__ Maps maps, Epi ep, Sched sc) {
   using SC = Scheme<NP>;
   using G = Geo<NP, BNT>;
   constexpr int ST = G::STAGES;
@@ -213,19 +250,13 @@ __global__ void __launch_bounds__(Geo<NP, BNT>::THREADS, 1)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + G::NBAR);
   volatile int* abort_sh = reinterpret_cast<volatile int*>(tmem_slot + 1);
   int* issued_sh = reinterpret_cast<int*>(tmem_slot + 2);
+  volatile int* last_sh = reinterpret_cast<volatile int*>(tmem_slot + 3);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-  // grouped raster over (m, n) tiles
-  const int bid = blockIdx.x;
-  const int per_group = GROUP_M * num_n;
-  const int g = bid / per_group;
-  const int first_m = g * GROUP_M;
-  const int gm = min(GROUP_M, num_m - first_m);
-  const int rem = bid - g * per_group;
-  const int mt = first_m + rem % gm;
-  const int nt = rem / gm;
-  const int m0 = mt * BM, n0 = nt * BNT;
-  const int ntile = (nt == num_n - 1) ? n_last : BNT;  // columns of this tile (multiple of 16)
+  int tile, kb0, kb1, m0, n0, ntile;  // ntile: columns of this tile (multiple of 16)
+  sc.unit(blockIdx.x, tile, kb0, kb1);
+  sc.origin(tile, m0, n0, ntile);
+  const int num_kb = kb1 - kb0;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < ST; ++s) {
@@ -262,10 +293,10 @@ __global__ void __launch_bounds__(Geo<NP, BNT>::THREADS, 1)
       const uint32_t st = sbase + s * G::STAGE_BYTES;
       mbar_expect_tx(full[s], G::STAGE_BYTES);
 #pragma unroll
-      for (int q = 0; q < SC::NPA; ++q) tma_load_2d(st + q * A_BYTES, &maps.a[q], kb * BK, m0, full[s]);
+      for (int q = 0; q < SC::NPA; ++q) tma_load_2d(st + q * A_BYTES, &maps.a[q], (kb0 + kb) * BK, m0, full[s]);
 #pragma unroll
       for (int q = 0; q < SC::NPW; ++q)
-        tma_load_2d(st + SC::NPA * A_BYTES + q * G::B_BYTES, &maps.b[q], kb * BK, n0, full[s]);
+        tma_load_2d(st + SC::NPA * A_BYTES + q * G::B_BYTES, &maps.b[q], (kb0 + kb) * BK, n0, full[s]);
       issued = kb + 1;
     }
     *issued_sh = issued;
@@ -336,6 +367,36 @@ __global__ void __launch_bounds__(Geo<NP, BNT>::THREADS, 1)
       if (ok && has_cols) {
         tc_fence_after();
         drain_add<DC>(tmem + lane_base + (uint32_t)(2 * BNT + col0), sum);
+      }
+    }
+    if (sc.nsplit > 1) {
+      // split tile: write this K range's partial; the last writer sums them all.  Every
+      // drain warp passes both named barriers, also after a failed wait.
+      constexpr int DRAIN_THREADS = 32 * G::DRAIN_WARPS;
+      const int row_t = q * 32 + lane;
+      float* mine = ep.part + (size_t)blockIdx.x * (BM * BNT);
+      if (ok && has_cols) {
+#pragma unroll
+        for (int c = 0; c < DC; ++c) mine[(size_t)(col0 + c) * BM + row_t] = sum[c];
+      }
+      __threadfence();
+      asm volatile("bar.sync 1, %0;" ::"r"(DRAIN_THREADS) : "memory");
+      if (dw == 0 && lane == 0) *last_sh = (atomicAdd(ep.cnt + tile, 1) == sc.nsplit - 1) ? 1 : 0;
+      asm volatile("bar.sync 1, %0;" ::"r"(DRAIN_THREADS) : "memory");
+      if (*last_sh) {
+        __threadfence();
+        if (ok && has_cols) {
+#pragma unroll
+          for (int c = 0; c < DC; ++c) sum[c] = 0.0f;
+          for (int sp = 0; sp < sc.nsplit; ++sp) {
+            const float* pp = ep.part + (size_t)(sp * sc.ntiles + tile) * (BM * BNT) + (size_t)col0 * BM + row_t;
+#pragma unroll
+            for (int c = 0; c < DC; ++c) sum[c] += __ldcg(pp + (size_t)c * BM);
+          }
+        }
+        if (dw == 0 && lane == 0) ep.cnt[tile] = 0;  // ready for the next launch
+      } else {
+        ok = false;  // another CTA finishes this tile
       }
     }
     const int64_t row = (int64_t)m0 + q * 32 + lane;
@@ -515,6 +576,26 @@ struct TileN {
   static constexpr int value = 128;
 };
 
+// K splits of a launch with `tiles` output tiles: the count (1 to MAX_SPLIT) that
+// minimises the estimated time, waves of CTAs x (1/splits + a fixed cost per CTA of
+// 5 % of a tile), with at least two drained groups of K blocks per split and at most
+// MAX_SPLIT x SMs CTAs (the partial-tile workspace).
+constexpr int MAX_SPLIT = 4;
+static int split_count(int tiles, int nkb, int sms, int flush) {
+  int best = 1;
+  double best_t = 0.0;
+  for (int sp = 1; sp <= MAX_SPLIT; ++sp) {
+    if (sp > 1 && (nkb / sp < 2 * flush || (int64_t)tiles * sp > (int64_t)MAX_SPLIT * sms)) break;
+    const double waves = (double)((tiles * sp + sms - 1) / sms);
+    const double t = waves * (1.0 / sp + 0.05);
+    if (sp == 1 || t < best_t - 1e-9) {
+      best = sp;
+      best_t = t;
+    }
+  }
+  return best;
+}
+
 // One tensor-core application of H to the vectors held in the operand pieces
 // described by bmap, with epilogue `ep`.
 template <int NP>
@@ -531,13 +612,17 @@ static int apply(const POperand& P, const CUtensorMap* bmap, Epi ep, cudaStream_
   Maps maps;
   for (int q = 0; q < Scheme<NP>::NPA; ++q) maps.a[q] = P.map[q];
   for (int q = 0; q < Scheme<NP>::NPW; ++q) maps.b[q] = bmap[q];
-  const int num_m = (int)cdiv(P.n, BM);
-  const int num_n = (int)cdiv(4 * ep.k, BNT);
-  const int64_t rest = 4 * ep.k - (int64_t)(num_n - 1) * BNT;  // columns of the last tile
-  const int n_last = (int)(((rest + 15) / 16) * 16);
-  const int num_kb = (int)(P.kpad / BK);
-  tc_hop_kernel<NP, BNT><<<num_m * num_n, G::THREADS, G::SMEM_BYTES, s>>>(maps, ep, num_kb, num_m, num_n,
-                                                                          n_last);
+  Sched sc{};
+  sc.num_m = (int)cdiv(P.n, BM);
+  sc.num_n = (int)cdiv(4 * ep.k, BNT);
+  const int64_t rest = 4 * ep.k - (int64_t)(sc.num_n - 1) * BNT;  // columns of the last tile
+  sc.n_last = (int)(((rest + 15) / 16) * 16);
+  sc.nkb = (int)(P.kpad / BK);
+  sc.bnt = BNT;
+  sc.ntiles = sc.num_m * sc.num_n;
+  sc.nfull = (sc.n_last < BNT) ? sc.num_m * (sc.num_n - 1) : sc.ntiles;
+  sc.nsplit = split_count(sc.ntiles, sc.nkb, ep.sms, Scheme<NP>::FLUSH);
+  tc_hop_kernel<NP, BNT><<<sc.ntiles * sc.nsplit, G::THREADS, G::SMEM_BYTES, s>>>(maps, ep, sc);
   count_launch();
   CB_LAUNCH();
   return CHASE_BSE_OK;
@@ -580,6 +665,22 @@ static int filter_impl(const cplx* A, const cplx* B, int64_t n, const cplx* Y0, 
   CB_TRY(ws.alloc(&gam, k));
   CB_TRY(ws.alloc(&err, 1));
   CB_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+  // split-K workspace: a partial tile per CTA of a split launch (fewer than
+  // MAX_SPLIT x SMs of them), one counter per tile
+  int dev = 0, sms = 0;
+  CB_CUDA(cudaGetDevice(&dev));
+  CB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int64_t max_tiles = cdiv(n, BM) * (rows / BNT);
+  float* part;
+  int* cnt;
+  CB_TRY(ws.alloc(&part, (int64_t)MAX_SPLIT * sms * BM * BNT));
+  CB_TRY(ws.alloc(&cnt, max_tiles));
+  CB_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * max_tiles, s));
+  auto sk = [&](Epi& e) {
+    e.part = part;
+    e.cnt = cnt;
+    e.sms = sms;
+  };
 
   const double a = mu_nevex * mu_nevex, b = muN * muN;
   const double c = 0.5 * (a + b), e = 0.5 * (b - a);
@@ -634,6 +735,7 @@ static int filter_impl(const cplx* A, const cplx* B, int64_t n, const cplx* Y0, 
     CB_CUDA(cudaMemcpyAsync(gam, gh.data(), sizeof(float) * k, cudaMemcpyHostToDevice, s));
     Epi ep{};
     ep.mode = 2; ep.n = n; ep.k = k; ep.kpad = P.kpad; ep.Znext = src; ep.Zcur = Zb[2]; ep.gamma = gam; ep.err = err;
+    sk(ep);
     CB_TRY(apply<NP>(P, mZ, ep, s));
     CB_CUDA(cudaMemsetAsync(Zb[0], 0, sizeof(float2) * n2 * k, s));
     scale_pack_kernel<NPW><<<gsz(n * k), 256, 0, s>>>(src, n, k, (float)al[0], Zb[1], Zp, P.kpad);
@@ -650,10 +752,12 @@ static int filter_impl(const cplx* A, const cplx* B, int64_t n, const cplx* Y0, 
     while (kj < k && degs[kj] >= j + 1) ++kj;
     Epi e1p{};
     e1p.mode = 0; e1p.n = n; e1p.k = kj; e1p.kpad = P.kpad; e1p.err = err;
+    sk(e1p);
     for (int q = 0; q < NPW; ++q) e1p.out[q] = Tp.p[q];
     CB_TRY(apply<NP>(P, mZ, e1p, s));  // T = H Z_j
     Epi e2p{};
     e2p.mode = 1; e2p.n = n; e2p.k = kj; e2p.kpad = P.kpad; e2p.err = err;
+    sk(e2p);
     for (int q = 0; q < NPW; ++q) e2p.out[q] = Zp.p[q];
     e2p.Znext = Zb[(j + 1) % 3]; e2p.Zcur = Zb[j % 3]; e2p.Zprev = Zb[(j + 2) % 3];
     e2p.alpha = (float)al[j]; e2p.beta = (float)be[j]; e2p.c = (float)c;
