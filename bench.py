@@ -89,7 +89,7 @@ def load_peaks():
     return dict(PEAKS_FALLBACK), "fallback"
 
 
-TC_TRAFFIC_N4096_K260 = (486775552 + 42145280 + 504331776 + 48718848) / 2.0  # bytes per launch
+TC_TRAFFIC_N4096_K260 = (486640128 + 43591680 + 503699456 + 50020864) / 2.0  # bytes per launch
 
 
 class ClockSampler:

@@ -113,37 +113,32 @@ struct Epi {
   int sms;      // SMs of the device
 };
 
-// Work of one launch: every output tile (the full-width tiles in a grouped raster, then
-// the narrow last column tile of every row block) in nsplit K ranges.  CTA c takes split
-// c / ntiles of tile c % ntiles, so that the CTAs running at the same time stream the
-// same K blocks of A (one DRAM read serves every column tile of a row block).  With
-// nsplit > 1 the splits leave FP32 partial tiles; the CTA that writes a tile's last one
-// (a per-tile counter) sums them in split order and runs the epilogue, so no CTA waits
-// for another and the result does not depend on timing.
+// Work of one launch: the 128 x BNT output tiles in clusters of two CTAs that hold
+// the row blocks 2p and 2p + 1 of the same column tile nt.  Each CTA loads its own A
+// block and one half of the B block, which TMA multicasts into both CTAs: B comes from
+// L2 once per pair (48 instead of 64 KB per CTA and K block).  The pairs (p, nt) run in
+// a grouped raster (GROUP_P pairs x all column tiles), repeated for nsplit K ranges, so
+// that the CTAs running at the same time stream the same K blocks of A.  With an odd
+// number of row blocks the last pair's second CTA mirrors its partner's tile and writes
+// nothing.  With nsplit > 1 the splits leave FP32 partial tiles; the CTA that writes a
+// tile's last one (a per-tile counter) sums them in split order and runs the epilogue,
+// so no CTA waits for another and the result does not depend on timing.
+constexpr int GROUP_P = GROUP_M / 2;
 struct Sched {
-  int nkb, num_m, num_n, nfull, ntiles, n_last, bnt, nsplit;
-  __device__ void unit(int c, int& t, int& kb0, int& kb1) const {
-    const int sp = c / ntiles;
-    t = c - sp * ntiles;
-    kb0 = (int)((int64_t)nkb * sp / nsplit);
-    kb1 = (int)((int64_t)nkb * (sp + 1) / nsplit);
-  }
-  // row and column origin and width of tile t
-  __device__ void origin(int t, int& m0, int& n0, int& ncols) const {
-    if (t < nfull) {
-      const int nnf = num_n - (ntiles > nfull ? 1 : 0);
-      const int per_group = GROUP_M * nnf;
-      const int g = t / per_group, first_m = g * GROUP_M;
-      const int gm = min(GROUP_M, num_m - first_m);
-      const int rem = t - g * per_group;
-      m0 = (first_m + rem % gm) * BM;
-      n0 = (rem / gm) * bnt;
-      ncols = bnt;
-    } else {
-      m0 = (t - nfull) * BM;
-      n0 = (num_n - 1) * bnt;
-      ncols = n_last;
-    }
+  int nkb, num_m, num_n, npairs, n_last, bnt, nsplit, ntiles;
+  __device__ void unit(int c, int& mt, int& nt, int& sp, bool& mirror) const {
+    const int rank = c & 1, cl = c >> 1;
+    const int per_split = npairs * num_n;
+    sp = cl / per_split;
+    const int pidx = cl - sp * per_split;
+    const int per_group = GROUP_P * num_n;
+    const int g = pidx / per_group, first = g * GROUP_P;
+    const int gp = min(GROUP_P, npairs - first);
+    const int rem = pidx - g * per_group;
+    nt = rem / gp;
+    mt = 2 * (first + rem % gp) + rank;
+    mirror = mt >= num_m;
+    if (mirror) mt = num_m - 1;
   }
 };
 
@@ -253,15 +248,20 @@ __global__ void __launch_bounds__(Geo<NP, BNT>::THREADS, 1)
   volatile int* last_sh = reinterpret_cast<volatile int*>(tmem_slot + 3);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-  int tile, kb0, kb1, m0, n0, ntile;  // ntile: columns of this tile (multiple of 16)
-  sc.unit(blockIdx.x, tile, kb0, kb1);
-  sc.origin(tile, m0, n0, ntile);
+  int mt, nt, sp;
+  bool mirror;
+  sc.unit(blockIdx.x, mt, nt, sp, mirror);
+  const int rank = (int)(blockIdx.x & 1);  // rank in the cluster of two
+  const int tile = mt * sc.num_n + nt;
+  const int m0 = mt * BM, n0 = nt * BNT;
+  const int ntile = (nt == sc.num_n - 1) ? sc.n_last : BNT;  // columns of this tile (multiple of 16)
+  const int kb0 = (int)((int64_t)sc.nkb * sp / sc.nsplit), kb1 = (int)((int64_t)sc.nkb * (sp + 1) / sc.nsplit);
   const int num_kb = kb1 - kb0;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < ST; ++s) {
       mbar_init(full[s], 1);
-      mbar_init(empty[s], 1);
+      mbar_init(empty[s], 2);  // released by the MMAs of both CTAs of the cluster
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(accf[b], 1);
@@ -280,6 +280,7 @@ __global__ void __launch_bounds__(Geo<NP, BNT>::THREADS, 1)
   }
   tc_fence_before();
   __syncthreads();
+  cluster_sync();  // the partner's barriers are initialised before any multicast reaches them
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   const uint32_t sbase = smem_u32(smem);
@@ -296,7 +297,8 @@ __global__ void __launch_bounds__(Geo<NP, BNT>::THREADS, 1)
       for (int q = 0; q < SC::NPA; ++q) tma_load_2d(st + q * A_BYTES, &maps.a[q], (kb0 + kb) * BK, m0, full[s]);
 #pragma unroll
       for (int q = 0; q < SC::NPW; ++q)
-        tma_load_2d(st + SC::NPA * A_BYTES + q * G::B_BYTES, &maps.b[q], (kb0 + kb) * BK, n0, full[s]);
+        tma_load_2d_mc(st + SC::NPA * A_BYTES + q * G::B_BYTES + rank * (G::B_BYTES / 2), &maps.b[q], (kb0 + kb) * BK,
+                       n0 + rank * (BNT / 2), full[s], 0x3);
       issued = kb + 1;
     }
     *issued_sh = issued;
@@ -330,7 +332,7 @@ __global__ void __launch_bounds__(Geo<NP, BNT>::THREADS, 1)
           }
         }
       }
-      mma_commit(empty[s]);
+      mma_commit_mc(empty[s], 0x3);
       if (last) mma_commit(accf[b]);
     }
     mma_commit(done);  // completes once every MMA issued above has finished
@@ -369,12 +371,14 @@ __global__ void __launch_bounds__(Geo<NP, BNT>::THREADS, 1)
         drain_add<DC>(tmem + lane_base + (uint32_t)(2 * BNT + col0), sum);
       }
     }
-    if (sc.nsplit > 1) {
+    if (mirror) {
+      ok = false;  // the partner CTA writes this tile
+    } else if (sc.nsplit > 1) {
       // split tile: write this K range's partial; the last writer sums them all.  Every
       // drain warp passes both named barriers, also after a failed wait.
       constexpr int DRAIN_THREADS = 32 * G::DRAIN_WARPS;
       const int row_t = q * 32 + lane;
-      float* mine = ep.part + (size_t)blockIdx.x * (BM * BNT);
+      float* mine = ep.part + (size_t)(sp * sc.ntiles + tile) * (BM * BNT);
       if (ok && has_cols) {
 #pragma unroll
         for (int c = 0; c < DC; ++c) mine[(size_t)(col0 + c) * BM + row_t] = sum[c];
@@ -388,8 +392,8 @@ __global__ void __launch_bounds__(Geo<NP, BNT>::THREADS, 1)
         if (ok && has_cols) {
 #pragma unroll
           for (int c = 0; c < DC; ++c) sum[c] = 0.0f;
-          for (int sp = 0; sp < sc.nsplit; ++sp) {
-            const float* pp = ep.part + (size_t)(sp * sc.ntiles + tile) * (BM * BNT) + (size_t)col0 * BM + row_t;
+          for (int j = 0; j < sc.nsplit; ++j) {
+            const float* pp = ep.part + (size_t)(j * sc.ntiles + tile) * (BM * BNT) + (size_t)col0 * BM + row_t;
 #pragma unroll
             for (int c = 0; c < DC; ++c) sum[c] += __ldcg(pp + (size_t)c * BM);
           }
@@ -445,10 +449,13 @@ __global__ void __launch_bounds__(Geo<NP, BNT>::THREADS, 1)
   tc_fence_before();
   __syncthreads();
   if (threadIdx.x == 0 && *abort_sh) {
-    // drain copies still in flight into this CTA's shared memory (bounded)
+    // drain copies still in flight into this CTA's shared memory (bounded), then give
+    // the partner's multicast copies time to land
     const int issued = *issued_sh;
     for (int kb = max(0, issued - ST); kb < issued; ++kb)
       mbar_wait(full[kb % ST], (uint32_t)(kb / ST) & 1u, abort_sh, ep.err, false);
+    const uint64_t t0 = gtimer();
+    while (gtimer() - t0 < 100000ull) __nanosleep(1000);
   }
   if (warp == 1) {
     // every MMA has finished before the accumulator memory is released
@@ -460,6 +467,7 @@ __global__ void __launch_bounds__(Geo<NP, BNT>::THREADS, 1)
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
   }
+  cluster_sync();  // no CTA leaves while its partner may still multicast into it
 }
 
 // ---------------------------------------------------------------- helpers
@@ -576,7 +584,7 @@ struct TileN {
   static constexpr int value = 128;
 };
 
-// K splits of a launch with `tiles` output tiles: the count (1 to MAX_SPLIT) that
+// K splits of a launch with `tiles` CTAs per split: the count (1 to MAX_SPLIT) that
 // minimises the estimated time, waves of CTAs x (1/splits + a fixed cost per CTA of
 // 5 % of a tile), with at least two drained groups of K blocks per split and at most
 // MAX_SPLIT x SMs CTAs (the partial-tile workspace).
@@ -620,9 +628,22 @@ static int apply(const POperand& P, const CUtensorMap* bmap, Epi ep, cudaStream_
   sc.nkb = (int)(P.kpad / BK);
   sc.bnt = BNT;
   sc.ntiles = sc.num_m * sc.num_n;
-  sc.nfull = (sc.n_last < BNT) ? sc.num_m * (sc.num_n - 1) : sc.ntiles;
-  sc.nsplit = split_count(sc.ntiles, sc.nkb, ep.sms, Scheme<NP>::FLUSH);
-  tc_hop_kernel<NP, BNT><<<sc.ntiles * sc.nsplit, G::THREADS, G::SMEM_BYTES, s>>>(maps, ep, sc);
+  sc.npairs = (sc.num_m + 1) / 2;
+  const int ctas = 2 * sc.npairs * sc.num_n;  // per K split
+  sc.nsplit = split_count(ctas, sc.nkb, ep.sms, Scheme<NP>::FLUSH);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(ctas * sc.nsplit));
+  cfg.blockDim = dim3(G::THREADS);
+  cfg.dynamicSmemBytes = G::SMEM_BYTES;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  CB_CUDA(cudaLaunchKernelEx(&cfg, tc_hop_kernel<NP, BNT>, maps, ep, sc));
   count_launch();
   CB_LAUNCH();
   return CHASE_BSE_OK;
@@ -655,8 +676,8 @@ static int filter_impl(const cplx* A, const cplx* B, int64_t n, const cplx* Y0, 
     CB_TRY(ws.alloc(&Tp.p[q], rows * P.kpad));
     CB_CUDA(cudaMemsetAsync(Zp.p[q], 0, sizeof(__nv_bfloat16) * rows * P.kpad, s));
     CB_CUDA(cudaMemsetAsync(Tp.p[q], 0, sizeof(__nv_bfloat16) * rows * P.kpad, s));
-    CB_TRY(make_map(&mZ[q], Zp.p[q], P.kpad, rows, BNT));
-    CB_TRY(make_map(&mT[q], Tp.p[q], P.kpad, rows, BNT));
+    CB_TRY(make_map(&mZ[q], Zp.p[q], P.kpad, rows, BNT / 2));  // half tiles, multicast
+    CB_TRY(make_map(&mT[q], Tp.p[q], P.kpad, rows, BNT / 2));
   }
   float2 *Zb[3], *src = nullptr;
   float* gam;
