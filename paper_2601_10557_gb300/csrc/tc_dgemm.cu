@@ -271,33 +271,64 @@ __global__ void sliced_finalize_kernel(const long long* hi, const long long* lo,
 // ---------------------------------------------------------------- slicing
 // One warp per row: exponent e with |x| < 2^e on the row, then the digits
 // d_t = rint(r_t), r_0 = x 2^(7-e), r_{t+1} = (r_t - d_t) 2^8.
+// Balanced base-256 digits of s = x 2^(7 - e) (|x| <= 2^e), in integer arithmetic:
+// N = round(x 2^(55 - e)) from the exponent and mantissa bits (|N| < 2^55, rounded half
+// away from zero), then d_6 .. d_1 the balanced low bytes of N (in [-128, 127]) and d_0
+// what is left (|d_0| <= 128): s = sum_t d_t 2^(-8t) up to 2^-49.
+__device__ __forceinline__ void int_digits(double x, int e, int* d) {
+  const long long b = __double_as_longlong(x);
+  const int ef = (int)((b >> 52) & 0x7ff);
+  long long mant = b & 0xfffffffffffffLL;
+  int ex = ef;
+  if (ef == 0) ex = 1;
+  else mant |= 1LL << 52;
+  const int sh = ex - 1020 - e;  // N = mant 2^sh; sh <= 2 for every |x| <= 2^e
+  long long N = 0;
+  if (sh >= 0) N = mant << sh;
+  else if (sh > -63) N = (mant + (1LL << (-sh - 1))) >> (-sh);
+  if (b < 0) N = -N;
+#pragma unroll
+  for (int t = S - 1; t >= 1; --t) {
+    const int dt = (int)((N + 128) & 255) - 128;
+    d[t] = dt;
+    N = (N - dt) >> 8;
+  }
+  d[0] = (int)N;
+}
+// frexp exponent of the largest |x| of a row from the magnitudes' bit patterns
+// (non-negative doubles order like their bits): 0 for a zero row.
+__device__ __forceinline__ int row_exponent(unsigned long long mbits) {
+  if (mbits == 0) return 0;
+  const int ef = (int)(mbits >> 52);
+  if (ef) return ef - 1022;
+  return (64 - __clzll((long long)mbits)) - 1074;  // subnormal
+}
 template <class Src>
 __global__ void slice_kernel(Src src, int64_t rows, int64_t K, int64_t kpad, int64_t plane, __nv_bfloat16* planes,
                              int* exps) {
   const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (r >= rows) return;
-  double m = 0.0;
+  unsigned long long m = 0;
   for (int64_t p = lane; 2 * p < K; p += 32) {
     const double2 v = src.pair(r, p);
-    m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
+    const unsigned long long a0 = (unsigned long long)__double_as_longlong(v.x) & 0x7fffffffffffffffull;
+    const unsigned long long a1 = (unsigned long long)__double_as_longlong(v.y) & 0x7fffffffffffffffull;
+    m = max(m, max(a0, a1));
   }
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-  int e = 0;
-  if (m > 0.0) frexp(m, &e);
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  const int e = row_exponent(m);
   __nv_bfloat16* row = planes + r * kpad;
   for (int64_t p = lane; 2 * p < kpad; p += 32) {
     double2 v = make_double2(0.0, 0.0);
     if (2 * p < K) v = src.pair(r, p);
-    double s0 = ldexp(v.x, 7 - e), s1 = ldexp(v.y, 7 - e);
+    int d0[S], d1[S];
+    int_digits(v.x, e, d0);
+    int_digits(v.y, e, d1);
 #pragma unroll
-    for (int t = 0; t < S; ++t) {
-      const double d0 = rint(s0), d1 = rint(s1);
+    for (int t = 0; t < S; ++t)
       *reinterpret_cast<__nv_bfloat162*>(row + t * plane + 2 * p) =
-          __halves2bfloat162(__float2bfloat16_rn((float)d0), __float2bfloat16_rn((float)d1));
-      s0 = (s0 - d0) * 256.0;
-      s1 = (s1 - d1) * 256.0;
-    }
+          __halves2bfloat162(__int2bfloat16_rn(d0[t]), __int2bfloat16_rn(d1[t]));
   }
   if (lane == 0) exps[r] = e;
 }
