@@ -143,6 +143,23 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+def reduce_scalar(dist, x: float, op: str, device) -> float:
+    """MAX or SUM of a per-rank scalar over the default process group (the
+    scalar itself without one)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def whole_job_tflops(dist, flops: float, ms: float, device) -> float:
+    """Whole-job throughput of N replicas: the flops of all ranks over the
+    slowest rank's time (ms)."""
+    return reduce_scalar(dist, flops, "sum", device) / (reduce_scalar(dist, ms, "max", device) / 1e3) / 1e12
+
+
 def make_inputs(wl: dict, seed: int):
     import bse_inputs as bi
     P = bi.make_problem(wl["n"], seed=seed, spec=wl["spec"], beta=wl["beta"])
@@ -270,24 +287,8 @@ def main():
     total_ms = ev0.elapsed_time(ev1)
     tts = total_ms / 1e3 / args.steps
 
-    def reduce_max(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    def reduce_sum(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
-
-    fms_max = reduce_max(fms)
-    fl_sum = reduce_sum(fl)
-    value = fl_sum / (fms_max / 1e3) / 1e12
-    tts_max = reduce_max(tts)
+    value = whole_job_tflops(dist, fl, fms, dev)
+    tts_max = reduce_scalar(dist, tts, "max", dev)
 
     # correctness of the timed result against cheap oracle-side properties
     lam_np = lam.cpu().numpy()
@@ -324,8 +325,8 @@ def main():
         efl += st2["filter_flops"]
     e1.record(stream)
     barrier()
-    e2e_ms = reduce_max(e0.elapsed_time(e1))
-    e2e_val = reduce_sum(efl) / (e2e_ms / 1e3) / 1e12
+    e2e_ms = reduce_scalar(dist, e0.elapsed_time(e1), "max", dev)
+    e2e_val = whole_job_tflops(dist, efl, e2e_ms, dev)
 
     # ---- roofline of the dominant kernel: one filter call at the workload's size
     deg_r = wl["deg"]
@@ -370,7 +371,7 @@ def main():
         step("fp64")
         f1.record(stream)
         barrier()
-        fp64_tts = reduce_max(f0.elapsed_time(f1) / 1e3)
+        fp64_tts = reduce_scalar(dist, f0.elapsed_time(f1) / 1e3, "max", dev)
 
     cpu = None
     if rank == 0 and world == 1:
