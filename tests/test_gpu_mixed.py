@@ -33,7 +33,9 @@ def _mus(P):
 
 
 @pytest.mark.parametrize("scheme", ["bf16x3", "bf16x6"])
-@pytest.mark.parametrize("n,k,maxdeg", [(128, 8, 1), (128, 8, 4), (300, 70, 8), (129, 33, 6)])
+# (300, 70): an odd number of row blocks (a mirror CTA in the last cluster) and a 2-way K
+# split; (640, 24): 5 row blocks and a 4-way K split of 6 CTAs per split
+@pytest.mark.parametrize("n,k,maxdeg", [(128, 8, 1), (128, 8, 4), (300, 70, 8), (129, 33, 6), (640, 24, 4)])
 def test_filter_tensor_core_matches_oracle(pkg, scheme, n, k, maxdeg):
     P = bi.make_problem(n, seed=n + k)
     A, B = problem_on_device(P)
