@@ -85,3 +85,45 @@ def filter_polynomial(x, deg: int, mu1: float, mu_nevex: float, muN: float):
     num = chebyshev_t(deg, (np.asarray(x, dtype=float) - c) / e)
     den = chebyshev_t(deg, np.array([(mu1 * mu1 - c) / e]))[0]
     return num / den
+
+
+def h2_blocks(A: np.ndarray, B: np.ndarray):
+    """(P, Q) with H^2 = [[P, Q], [conj(Q), conj(P)]] for H = [[A, B], [-conj(B), -conj(A)]]:
+    P = A A - B conj(B), Q = A B - B conj(A) (block product of H with itself; the
+    lower blocks are the conjugates because H^2 commutes with K conj).  Not the
+    paper's method, which applies H twice; this is the explicit-H^2 variant."""
+    P = A @ A - B @ B.conj()
+    Q = A @ B - B @ A.conj()
+    return P, Q
+
+
+def apply_h2_blocks(P: np.ndarray, Q: np.ndarray, W: np.ndarray) -> np.ndarray:
+    """H^2 W from the blocks of H^2: top P x + Q y, bottom conj(Q) x + conj(P) y."""
+    n = P.shape[0]
+    X, Y = W[:n], W[n:]
+    return np.vstack([P @ X + Q @ Y, Q.conj() @ X + P.conj() @ Y])
+
+
+def chebyshev_filter_explicit(P, Q, W0, degs, mu1, mu_nevex, muN):
+    """The filter of ``chebyshev_filter`` (same recurrence and per-column degrees) with
+    H^2 applied from its blocks (P, Q) of ``h2_blocks``: one product per H^2 step."""
+    degs = np.asarray(degs, dtype=int)
+    W0 = np.array(W0, dtype=np.complex128)
+    if W0.shape[1] == 0:
+        return W0.copy()
+    c, e, sigma1 = coefficients(mu1, mu_nevex, muN)
+    tau = 2.0 / sigma1
+    out = np.empty_like(W0)
+    Yprev = W0
+    Y = (sigma1 / e) * (apply_h2_blocks(P, Q, W0) - c * W0)
+    for i in np.where(degs == 1)[0]:
+        out[:, i] = Y[:, i]
+    sigma = sigma1
+    for j in range(1, int(degs.max())):
+        sigma_new = 1.0 / (tau - sigma)
+        Ynew = (2.0 * sigma_new / e) * (apply_h2_blocks(P, Q, Y) - c * Y) - (sigma * sigma_new) * Yprev
+        Yprev, Y = Y, Ynew
+        sigma = sigma_new
+        for i in np.where(degs == j + 1)[0]:
+            out[:, i] = Y[:, i]
+    return out

@@ -67,3 +67,34 @@ def residuals(A, B, W, ritz):
     H = hamiltonian(A, B)
     R = H @ W - W * ritz[None, :]
     return np.linalg.norm(R, axis=0)
+
+
+def fallback_dual_basis(Q: np.ndarray) -> np.ndarray:
+    """The dual basis of the non-hermitian fallback (Section 4.4, last paragraph):
+    Q_L = [S Q - Q (M - diag M)] diag(M)^{-1} with M = Q^* S Q, defined whenever the
+    diagonal of M has no zero (M itself may be singular).  For orthonormal Q,
+    Q_L^* Q = I."""
+    n = Q.shape[0] // 2
+    SQ = Q.copy()
+    SQ[n:, :] *= -1.0
+    M = Q.conj().T @ SQ
+    d = np.real(np.diag(M))
+    if np.any(d == 0.0):
+        raise ZeroDivisionError("Q^* S Q has a zero diagonal entry")
+    return (SQ - Q @ (M - np.diag(np.diag(M)))) / d[None, :]
+
+
+def rayleigh_ritz_fallback(A, B, Q):
+    """Non-hermitian fallback Rayleigh-Ritz: G = Q_L^* H Q with the dual basis of
+    ``fallback_dual_basis``, a general (non-hermitian) eigensolve of G, and the
+    Ritz pairs with positive real part, ascending: returns (ritz, W_plus) with unit
+    columns W_plus = Q Z_plus.  No spectral equivalence to a hermitian matrix is used."""
+    H = hamiltonian(A, B)
+    QL = fallback_dual_basis(Q)
+    G = QL.conj().T @ (H @ Q)
+    lam, Z = np.linalg.eig(G)
+    pos = np.where(lam.real > 0)[0]
+    pos = pos[np.argsort(lam.real[pos])]
+    W = Q @ Z[:, pos]
+    W = W / np.linalg.norm(W, axis=0, keepdims=True)
+    return lam[pos].real, W
