@@ -9,10 +9,12 @@ library.  Inputs come from the seeded generator module ``bse_inputs``.
 Modules
 -------
 dense          brute-force eigensolves of H (two independent routes + Jacobi)
-chebyshev      the Chebyshev filter on H^2 (Section 4.2, eq. three-term_recurrence_pseudo-hermitian)
+chebyshev      the Chebyshev filter on H^2 (Section 4.2, eq. three-term_recurrence_pseudo-hermitian);
+               also the explicit-H^2 variant (H^2 from its blocks, not the paper's method)
 lanczos        pseudo-hermitian Lanczos spectral bounds (Section 4.1)
 qr             CholeskyQR2 with a Householder fallback (Section 4.3)
-rayleigh_ritz  oblique Rayleigh-Ritz with hermitian spectral equivalence (Algorithm 2)
+rayleigh_ritz  oblique Rayleigh-Ritz with hermitian spectral equivalence (Algorithm 2);
+               also the non-hermitian fallback dual basis (Section 4.4, last paragraph)
 solver         the outer subspace iteration (Algorithm 3)
 gradient       eigenvalue gradient with respect to A and B (Theorem SH_HPD: u = S v)
 
