@@ -16,21 +16,25 @@
 //   BF16x3: 2 pieces each, x0 y0 + x0 y1 + x1 y0          (~16 bits, ~1.5e-5)
 //   BF16x6: 3 pieces each, adds x0 y2 + x1 y1 + x2 y0      (FP32 class, ~2e-7)
 //
-// Kernel structure (one 128 x 128 output tile per CTA, 384 threads):
-//   warp 0   TMA producer: the A and B pieces of 64 K-elements (128B swizzle)
-//            into a 3-stage (BF16x3) or 2-stage (BF16x6) shared-memory ring
-//   warp 1   allocates all 512 TMEM columns (two accumulator buffers, each a
-//            hi*hi accumulator and one for the cross products); one lane issues
-//            the tcgen05.mma of a K block into buffer kb & 1
+// Kernel structure (one K range of one 128 x 128 output tile per CTA, 384 threads;
+// clusters of two CTAs on vertically adjacent row blocks of one column tile):
+//   warp 0   TMA producer: its own A pieces and one half of the B pieces of 64
+//            K-elements (128B swizzle), the B halves multicast into both CTAs of the
+//            cluster, into a 3-stage (BF16x3) or 2-stage (BF16x6) shared-memory ring
+//            whose stages both CTAs' MMAs release
+//   warp 1   allocates all 512 TMEM columns (two alternating x0*y0 buffers and one
+//            for the cross products); one lane issues the tcgen05.mma of a K block
 //   warps 4-11 drain the partial sums of every FLUSH K blocks (tcgen05.ld) into FP32
-//            registers while the next block accumulates in the other buffer,
-//            because the tensor core's FP32 accumulation truncates; then either
+//            registers while the next group accumulates in the other buffer,
+//            because the tensor core's FP32 accumulation truncates; then (with a K
+//            split) write a partial tile, the last writer of a tile summing them,
+//            and either
 //            (mode 0) store the next GEMM's B-operand planes, or
 //            (mode 1) the fused three-term recurrence in FP32 plus the planes, or
 //            (mode 2) Z = H X + gamma_col * X (no planes).
 // Every mbarrier wait is bounded (2 s of %globaltimer); on expiry the kernel
-// sets an error flag, waits (bounded) for its own copies in flight, frees its
-// TMEM and returns.
+// sets an error flag, waits (bounded) for the copies in flight into its shared
+// memory, frees its TMEM and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
