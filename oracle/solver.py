@@ -46,7 +46,7 @@ from .chebyshev import chebyshev_filter, coefficients
 from .dense import fix_phase
 from .lanczos import spectral_bounds, lanczos_tridiagonal, ritz_and_weights
 from .qr import cholesky_qr2
-from .rayleigh_ritz import rayleigh_ritz, residuals
+from .rayleigh_ritz import rayleigh_ritz, rayleigh_ritz_fallback, residuals
 
 GAMMA = 1e-3
 
@@ -92,8 +92,14 @@ def degrees(ritz, res, tol, mu1, mu_nevex, muN, deg_min, deg_max, prev_res=None,
 
 
 def solve(A, B, nev, nex, deg, tol, W0raw, starts, lanczos_steps=26, deg_min=None,
-          deg_max=None, maxiter=25):
-    """Returns dict(lam[nev], V[2n, nev], iterations, history, mu)."""
+          deg_max=None, maxiter=25, rr="oblique"):
+    """Returns dict(lam[nev], V[2n, nev], iterations, history, mu).
+
+    rr: "oblique" (Algorithm 2) or "fallback" (the non-hermitian dual basis of the last
+    paragraph of Section 4.4, for a singular Q^* S Q)."""
+    if rr not in ("oblique", "fallback"):
+        raise ValueError("rr must be 'oblique' or 'fallback'")
+    rr_step = rayleigh_ritz if rr == "oblique" else rayleigh_ritz_fallback
     n = A.shape[0]
     nevex = nev + nex
     deg_min = deg if deg_min is None else deg_min
@@ -116,7 +122,7 @@ def solve(A, B, nev, nex, deg, tol, W0raw, starts, lanczos_steps=26, deg_min=Non
         X = np.concatenate([s_flip(Yp), s_flip(k_conj(Yp)), Wf, k_conj(Wf)], axis=1)
         Q, used_hh = cholesky_qr2(X)
         Q = Q[:, 2 * locked:]
-        ritz, Wpos = rayleigh_ritz(A, B, Q)
+        ritz, Wpos = rr_step(A, B, Q)
         res = residuals(A, B, Wpos, ritz) / rhat
         history.append(dict(ritz=ritz.copy(), res=res.copy(), degs=degs.copy(),
                             locked=locked, householder=used_hh,

@@ -94,3 +94,19 @@ def test_fallback_rr_is_exact_on_invariant_subspaces(m):
     assert np.linalg.norm(H @ W - W * ritz[None, :], axis=0).max() <= 1e-10 * np.linalg.norm(H, 2)
     ritz2, _ = rayleigh_ritz.rayleigh_ritz(P.A, P.B, Q)
     np.testing.assert_allclose(ritz, ritz2, rtol=1e-11)
+
+
+def test_oracle_solve_with_the_fallback_rr_reaches_the_dense_eigenpairs():
+    """Algorithm 3 with the fallback Rayleigh-Ritz in place of Algorithm 2 still returns
+    the nev smallest positive eigenpairs of the dense brute force."""
+    from oracle import solver
+    n, nev, nex = 64, 6, 6
+    P = bi.make_problem(n, seed=0)
+    W0, V0 = bi.start_block(n, nev + nex, 0), bi.lanczos_starts(n, 4, 0)
+    ref, _ = dense.smallest_positive(P.A, P.B, nev)
+    out = solver.solve(P.A, P.B, nev, nex, 12, 1e-10, W0, V0, deg_min=4, deg_max=24, maxiter=40, rr="fallback")
+    assert out["converged"] == nev
+    np.testing.assert_allclose(out["lam"], ref, rtol=1e-10)
+    H = dense.hamiltonian(P.A, P.B)
+    R = H @ out["V"] - out["V"] * out["lam"][None, :]
+    assert np.linalg.norm(R, axis=0).max() <= 1e-9 * np.linalg.norm(H, 2)
