@@ -309,6 +309,7 @@ __global__ void __launch_bounds__(Geo<NP, BNT>::THREADS, 1)
   } else if (warp == 1 && lane == 0) {
     const uint32_t idesc = make_idesc(ntile);
     const uint32_t small = tmem + (uint32_t)(2 * BNT);
+    const uint64_t dbase = sdesc(sbase);
     for (int kb = 0; kb < num_kb; ++kb) {
       const int grp = kb / FLUSH, b = grp & 1;
       const bool first = (kb % FLUSH) == 0;
@@ -324,8 +325,11 @@ __global__ void __launch_bounds__(Geo<NP, BNT>::THREADS, 1)
       for (int kk = 0; kk < BK / 16; ++kk) {
 #pragma unroll
         for (int pr = 0; pr < SC::NPROD; ++pr) {
-          const uint64_t ad = sdesc(st + SC::pa(pr) * A_BYTES + kk * 32);
-          const uint64_t bd = sdesc(st + SC::NPA * A_BYTES + SC::pb(pr) * G::B_BYTES + kk * 32);
+          // sdesc is linear in the address here (its 14-bit start field holds address / 16 of
+          // a 1024-aligned ring below 256 KB and cannot carry): a hoisted base plus constants
+          const uint64_t sd = dbase + (uint64_t)((uint32_t)(st - sbase) >> 4);
+          const uint64_t ad = sd + (uint64_t)((SC::pa(pr) * A_BYTES + kk * 32) >> 4);
+          const uint64_t bd = sd + (uint64_t)((SC::NPA * A_BYTES + SC::pb(pr) * G::B_BYTES + kk * 32) >> 4);
           if (G::CROSS) {
             const uint32_t acc =
                 (pr == 0) ? ((!first || kk > 0) ? 1u : 0u) : ((kb > 0 || kk > 0 || pr > 1) ? 1u : 0u);
