@@ -138,6 +138,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     *issued_sh = issued;
   } else if (warp == 1 && lane == 0) {
+    const uint64_t dbase = sdesc64(sbase);
     for (int kb = 0; kb < nkb; ++kb) {
       const int grp = kb / CHUNK, b = grp & 1;
       const bool first = (kb % CHUNK) == 0;
@@ -151,10 +152,13 @@ __global__ void __launch_bounds__(THREADS, 1)
       const uint32_t buf = tmem + (uint32_t)(b * GCOLS);
 #pragma unroll
       for (int kk = 0; kk < BK / 16; ++kk) {
-        const uint64_t bd = sdesc64(st + S * A_SLICE + kk * 32);
+        // sdesc64 is linear in the address here (its 14-bit start field holds address / 16
+        // of a ring below 256 KB and cannot carry): a hoisted base plus constants
+        const uint64_t sd = dbase + (uint64_t)((uint32_t)(st - sbase) >> 4);
+        const uint64_t bd = sd + (uint64_t)((S * A_SLICE + kk * 32) >> 4);
 #pragma unroll
         for (int t = 0; t < S; ++t) {
-          const uint64_t ad = sdesc64(st + t * A_SLICE + kk * 32);
+          const uint64_t ad = sd + (uint64_t)((t * A_SLICE + kk * 32) >> 4);
           const uint32_t acc = (first && kk == 0 && t == 0) ? 0u : 1u;
           mma_bf16(buf + (uint32_t)(t * BNS), ad, bd, idesc_n((S - t) * BNS), acc);
         }
