@@ -45,7 +45,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="n4096")
-    p.add_argument("--precision", default="auto", choices=["auto", "fp64", "mixed", "bf16x3", "bf16x6"])
+    p.add_argument("--precision", default="auto", choices=["auto", "fp64", "mixed", "fp16x3", "bf16x3", "bf16x6"])
     p.add_argument("--no-fp64-compare", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=None)
     p.add_argument("--filter-only", action="store_true",

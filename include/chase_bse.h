@@ -56,7 +56,12 @@ typedef enum chase_bse_precision {
   CHASE_BSE_MIXED_BF16X3 = 1,  /* filter products on tcgen05 tensor cores from BF16
                                   pieces, x = x0 + x1, 3 products, FP32 accumulation
                                   (about 16-bit accurate); everything else FP64      */
-  CHASE_BSE_MIXED_BF16X6 = 2   /* as above with 3 pieces and 6 products (FP32 class) */
+  CHASE_BSE_MIXED_BF16X6 = 2,  /* as above with 3 pieces and 6 products (FP32 class) */
+  CHASE_BSE_MIXED_FP16X3 = 3   /* filter products from FP16 pieces x = x0 + x1 (11 +
+                                  11 bits, every operand row scaled by a power of two
+                                  into FP16's range), 3 products, FP32 accumulation:
+                                  FP32-class accuracy at the cost of BF16X3; the
+                                  default mixed precision                            */
 } chase_bse_precision;
 /* In chase_bse_solve the mixed filter runs, from the second iteration on, on the
  * correction q(H^2) r2 with r2 = (H^2 - lambda^2) v of each Ritz pair (FP64
@@ -162,11 +167,14 @@ int chase_bse_residuals(const void* A, const void* B, int64_t n, const void* W,
  * the 2n x k scratch block lives in a fixed array of
  * CHASE_BSE_NOALLOC_MAX_ENTRIES complex128 entries (8 MiB) that every device
  * using the library holds until the process exits, and the call performs no
- * allocation or free.
+ * allocation or free: its H product runs as one launch over the whole K range,
+ * without the split-K partial sums of chase_bse_residuals (slower when 2n * k is
+ * small, identical results up to the order of the FP64 sums).
  *   - 2n * k > CHASE_BSE_NOALLOC_MAX_ENTRIES returns BAD_ARG; nothing runs.
  *   - The first call on a device looks up the array's device address (once per
  *     device, with that device current); make that first call before any stream
- *     capture.
+ *     capture.  The address is kept for the life of the process: after a
+ *     cudaDeviceReset of that device, reload the library (a new process).
  *   - All calls share the array, which keeps the last call's contents: calls
  *     whose kernels overlap on the GPU (different streams, or different host
  *     threads, without ordering between them) race on it and give wrong
@@ -224,6 +232,11 @@ void chase_bse_trim_memory(void);
 /* Diagnostics (no counterpart in the paper): the number of CUDA kernels this
  * library has launched since it was loaded, summed over all threads. */
 int64_t chase_bse_launch_count(void);
+
+/* Diagnostics (no counterpart in the paper): the number of device allocations
+ * (stream-ordered, from the library's pool) the library has requested since it
+ * was loaded, summed over all threads. */
+int64_t chase_bse_alloc_count(void);
 
 #ifdef __cplusplus
 }

@@ -20,7 +20,10 @@ LIB_PATH = os.path.join(_HERE, "libchase_bse.so")
 FP64 = 0
 MIXED_BF16X3 = 1
 MIXED_BF16X6 = 2
-_PREC = {"fp64": FP64, "mixed": MIXED_BF16X3, "bf16x3": MIXED_BF16X3, "bf16x6": MIXED_BF16X6}
+MIXED_FP16X3 = 3
+# "mixed" is the default tensor-core scheme (FP16 pieces, FP32-class products)
+_PREC = {"fp64": FP64, "mixed": MIXED_FP16X3, "fp16x3": MIXED_FP16X3, "bf16x3": MIXED_BF16X3,
+         "bf16x6": MIXED_BF16X6}
 
 
 class ChaseBSEError(RuntimeError):
@@ -80,7 +83,8 @@ _lib: Optional[ctypes.CDLL] = None
 
 EXPORTS = ["chase_bse_solve", "chase_bse_filter", "chase_bse_rr", "chase_bse_residuals", "chase_bse_grad",
            "chase_bse_strerror", "chase_bse_version", "chase_bse_has_mixed", "chase_bse_launch_count",
-           "chase_bse_residuals_noalloc", "chase_bse_dgemm_sliced", "chase_bse_trim_memory"]
+           "chase_bse_residuals_noalloc", "chase_bse_dgemm_sliced", "chase_bse_trim_memory",
+           "chase_bse_alloc_count"]
 
 # 2n * k limit of chase_bse_residuals_noalloc (its fixed device scratch, complex128 entries)
 NOALLOC_MAX_ENTRIES = 1 << 19
@@ -107,6 +111,7 @@ def lib() -> ctypes.CDLL:
     L.chase_bse_strerror.argtypes = [ctypes.c_int]
     L.chase_bse_strerror.restype = ctypes.c_char_p
     L.chase_bse_launch_count.restype = ctypes.c_int64
+    L.chase_bse_alloc_count.restype = ctypes.c_int64
     L.chase_bse_trim_memory.restype = None
     for name in ["chase_bse_solve", "chase_bse_filter", "chase_bse_rr", "chase_bse_residuals", "chase_bse_grad",
                  "chase_bse_version", "chase_bse_has_mixed", "chase_bse_residuals_noalloc",
@@ -119,6 +124,11 @@ def lib() -> ctypes.CDLL:
 def launch_count() -> int:
     """Kernels launched by the library so far (diagnostics)."""
     return int(lib().chase_bse_launch_count())
+
+
+def alloc_count() -> int:
+    """Device allocations requested by the library so far (diagnostics)."""
+    return int(lib().chase_bse_alloc_count())
 
 
 def trim_memory() -> None:

@@ -22,6 +22,8 @@ int chase_bse_version(void) { return 100; }
 
 int64_t chase_bse_launch_count(void) { return cb::launch_count(); }
 
+int64_t chase_bse_alloc_count(void) { return cb::alloc_count(); }
+
 int chase_bse_has_mixed(void) { return cb::mixed_available() ? 1 : 0; }
 
 void chase_bse_trim_memory(void) { cb::pool_trim(); }
@@ -52,14 +54,15 @@ int chase_bse_filter(const void* A, const void* B, int64_t n, void* W, int64_t k
   if (k == 0) return CHASE_BSE_OK;
   if (!A || !B || !W || !degs || n < 1 || k < 0 || !(mu1 > 0) || !(mu_nevex > mu1) || !(muN > mu_nevex))
     return CHASE_BSE_BAD_ARG;
-  if (precision != CHASE_BSE_FP64 && precision != CHASE_BSE_MIXED_BF16X3 && precision != CHASE_BSE_MIXED_BF16X6)
+  if (precision != CHASE_BSE_FP64 && precision != CHASE_BSE_MIXED_BF16X3 && precision != CHASE_BSE_MIXED_BF16X6 &&
+      precision != CHASE_BSE_MIXED_FP16X3)
     return CHASE_BSE_BAD_ARG;
   for (int64_t i = 0; i < k; ++i)
     if (degs[i] < 1) return CHASE_BSE_BAD_ARG;
   CB_GUARD({
     std::vector<int> prec(k, precision == CHASE_BSE_FP64 ? 0 : 1);
     return cb::filter((const cplx*)A, (const cplx*)B, n, (cplx*)W, k, degs, prec.data(), mu1, mu_nevex, muN,
-                      precision == CHASE_BSE_MIXED_BF16X6 ? 6 : 3, nullptr, nullptr, (cudaStream_t)stream, nullptr);
+                      precision, nullptr, nullptr, (cudaStream_t)stream, nullptr);
   })
 }
 

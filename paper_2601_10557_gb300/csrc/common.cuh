@@ -68,6 +68,9 @@ inline cudaError_t dalloc(T** p, size_t bytes, cudaStream_t s) {
   return dalloc(reinterpret_cast<void**>(p), bytes, s);
 }
 void pool_trim();
+// Number of device allocations the library has requested (every one goes through
+// dalloc), for diagnostics and for the allocation-free entry point's tests.
+int64_t alloc_count();
 
 // Stream-ordered workspace: every buffer is released when the owner goes out
 // of scope (cudaFreeAsync on the same stream).

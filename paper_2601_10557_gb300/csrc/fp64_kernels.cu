@@ -164,7 +164,7 @@ template <int BM, int BNW, int TM, int TNW>
 static int hop_launch(const HopArgs& a, cudaStream_t s) {
   const int64_t tiles = (int64_t)cdiv(a.n, BM) * cdiv(a.k, BNW);
   const int64_t n2 = 2 * a.n;
-  const int64_t nsplit = split_count(tiles, n2, 256);
+  const int64_t nsplit = a.no_split ? 1 : split_count(tiles, n2, 256);
   if (nsplit <= 1) {
     dim3 grid(cdiv(a.n, BM), cdiv(a.k, BNW));
     hop_kernel<BM, BNW, TM, TNW, 16><<<grid, (BM / TM) * (BNW / TNW), 0, s>>>(a, nullptr, 0);

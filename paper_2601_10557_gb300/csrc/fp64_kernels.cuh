@@ -28,6 +28,7 @@ struct HopArgs {
   const cplx* Wc;    // HOP_CHEB: current iterate (ld 2n)
   const cplx* Wp;    // HOP_CHEB: previous iterate (ld 2n), unused if beta == 0
   const double* lambda;  // HOP_RESID
+  int no_split;      // 1: one launch over the whole K range (no split-K partials, allocates nothing)
 };
 
 int hop_fp64(const HopArgs& a, cudaStream_t s);

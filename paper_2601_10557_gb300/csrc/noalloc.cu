@@ -51,8 +51,10 @@ extern "C" int chase_bse_residuals_noalloc(const void* A, const void* B, int64_t
   CB_TRY(scratch_address(&R));
   cudaStream_t s = (cudaStream_t)stream;
   // every entry of the 2n x k block is written by the residual kernel, so the
-  // previous call's contents need no clearing
+  // previous call's contents need no clearing; the H product runs as one launch over
+  // the whole K range (no split-K partial sums, which would need workspace)
   cb::HopArgs a{};
+  a.no_split = 1;
   a.A = (const cb::cplx*)A;
   a.B = (const cb::cplx*)B;
   a.n = n;

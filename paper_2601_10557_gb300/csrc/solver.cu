@@ -21,7 +21,11 @@ std::mutex g_pool_mu;
 cudaMemPool_t g_pools[64] = {};
 }  // namespace
 
+static std::atomic<int64_t> g_allocs{0};
+int64_t alloc_count() { return g_allocs.load(std::memory_order_relaxed); }
+
 cudaError_t dalloc(void** p, size_t bytes, cudaStream_t s) {
+  g_allocs.fetch_add(1, std::memory_order_relaxed);
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
@@ -808,12 +812,12 @@ int solve(const cplx* A, const cplx* B, int64_t n, int64_t nev, int64_t nex, int
       o.maxiter < 1 || o.deg_min < 1 || o.deg_max < o.deg_min || o.lanczos_steps < 2 || o.lanczos_vecs < 1 ||
       o.lanczos_vecs > 64 ||
       (o.precision != CHASE_BSE_FP64 && o.precision != CHASE_BSE_MIXED_BF16X3 &&
-       o.precision != CHASE_BSE_MIXED_BF16X6))
+       o.precision != CHASE_BSE_MIXED_BF16X6 && o.precision != CHASE_BSE_MIXED_FP16X3))
     return CHASE_BSE_BAD_ARG;
   if (o.fp64_products != 0 && o.fp64_products != 1) return CHASE_BSE_BAD_ARG;
   const bool mixed = o.precision != CHASE_BSE_FP64;
   const bool sliced = mixed && o.fp64_products == 0;
-  const int scheme = o.precision == CHASE_BSE_MIXED_BF16X6 ? 6 : 3;
+  const int scheme = o.precision;  // FilterScheme codes equal the precision codes
   if (mixed && !mixed_available()) return CHASE_BSE_UNSUPPORTED;
   cudaStream_t s = (cudaStream_t)o.stream;
   const int64_t n2 = 2 * n, nevex = nev + nex;

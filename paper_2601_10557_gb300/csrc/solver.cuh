@@ -10,9 +10,13 @@ struct FilterStats {
   int64_t launches = 0;
 };
 
+// Tensor-core filter schemes (split products, tc_filter.cu); the values equal the
+// chase_bse_precision codes that select them.
+enum FilterScheme : int { SCHEME_BF16X3 = 1, SCHEME_BF16X6 = 2, SCHEME_FP16X3 = 3 };
+
 // Chebyshev filter on H^2, in place on W (2n x k); degs/prec are per column
-// (host).  prec[i] = 0: FP64 path, 1: tensor-core path with `scheme` (3 or 6
-// BF16 products).  With ritz (host, per column) and R (device, 2n x k, the FP64
+// (host).  prec[i] = 0: FP64 path, 1: tensor-core path with `scheme`
+// (FilterScheme).  With ritz (host, per column) and R (device, 2n x k, the FP64
 // residual vectors H w - ritz w) the tensor-core columns use the correction form.
 int filter(const cplx* A, const cplx* B, int64_t n, cplx* W, int64_t k, const int* degs, const int* prec,
            double mu1, double mu_nevex, double muN, int scheme, const double* ritz, const cplx* R, cudaStream_t s,
@@ -46,7 +50,7 @@ int gradient(const cplx* V, const double* w, int64_t n, int64_t nev, cplx* gA, c
 
 // Mixed-precision (tcgen05) filter on a column group whose columns are sorted
 // by descending degree; defined in the tensor-core translation unit.
-// scheme: 3 = BF16x3, 6 = BF16x6 split products.
+// scheme: a FilterScheme.
 int filter_mixed_sorted(const cplx* A, const cplx* B, int64_t n, cplx* Y0, int64_t k, const int* degs_sorted,
                         double mu1, double mu_nevex, double muN, cplx* out, int scheme, cudaStream_t s,
                         FilterStats* fs);

@@ -9,19 +9,28 @@
 // so that (H w)_top = P w and (H w)_bot = -conj(P u) land in four adjacent
 // accumulator columns of the same TMEM lane (row i of the tile).
 //
-// Split products on BF16 tensor cores: an operand x is written as a sum of
-// BF16 pieces x = x0 + x1 (+ x2), x0 = bf16(x), x1 = bf16(x - x0), ..., and the
-// product keeps the cross terms down to the target accuracy, all accumulated
-// into one FP32 TMEM accumulator:
-//   BF16x3: 2 pieces each, x0 y0 + x0 y1 + x1 y0          (~16 bits, ~1.5e-5)
-//   BF16x6: 3 pieces each, adds x0 y2 + x1 y1 + x2 y0      (FP32 class, ~2e-7)
+// Split products on 16-bit tensor cores: an operand x is written as a sum of
+// pieces x = x0 + x1 (+ x2), x0 = rn(x), x1 = rn(x - x0), ..., and the product
+// keeps the cross terms down to the target accuracy, all accumulated in FP32:
+//   FP16x3: 2 FP16 pieces each (11 + 11 bits), x0 y0 + x0 y1 + x1 y0   (~2^-22)
+//   BF16x3: 2 BF16 pieces each (8 + 8 bits), same products             (~2^-16)
+//   BF16x6: 3 BF16 pieces each, adds x0 y2 + x1 y1 + x2 y0             (~2^-24)
+// (FP16 pieces of this kind: Ootomo and Yokota, Int. J. HPC Appl. 2022.)  FP16 has
+// a 5-bit exponent, so every operand row is scaled by a power of two: row r of P
+// by 2^prow[r] (its largest entry in [2^12, 2^13)), vector v by 2^vexp[v], chosen
+// from an upper bound of its entries below 2^13: the bound of an output of H is
+// L * max|input| with L the largest absolute row sum of P, and that of the
+// recurrence combines the maxima of its terms; every epilogue records the true
+// maximum of each output vector (one atomic max per warp and vector) for the
+// next bound.  The epilogue divides the accumulator by 2^(prow + vexp).  Entries
+// far below the bound only lose precision relative to the bound, which keeps the
+// product's error below that of an FP32 GEMM (|dy| <~ 2^-22 L max|w|).  The
+// BF16 schemes use the same scaling (harmless: BF16 has FP32's exponent range).
 //
-// Kernel structure (one K range of one 128 x 128 output tile per CTA, 384 threads;
-// clusters of two CTAs on vertically adjacent row blocks of one column tile):
-//   warp 0   TMA producer: its own A pieces and one half of the B pieces of 64
-//            K-elements (128B swizzle), the B halves multicast into both CTAs of the
-//            cluster, into a 3-stage (BF16x3) or 2-stage (BF16x6) shared-memory ring
-//            whose stages both CTAs' MMAs release
+// Kernel structure (one K range of one 128 x 128 output tile per CTA, 384 threads):
+//   warp 0   TMA producer: the A pieces and the B pieces of 64 K-elements (128B
+//            swizzle) into a 3-stage (two pieces) or 2-stage (three pieces)
+//            shared-memory ring
 //   warp 1   allocates all 512 TMEM columns (two alternating x0*y0 buffers and one
 //            for the cross products); one lane issues the tcgen05.mma of a K block
 //   warps 4-11 drain the partial sums of every FLUSH K blocks (tcgen05.ld) into FP32
@@ -29,15 +38,16 @@
 //            because the tensor core's FP32 accumulation truncates; then (with a K
 //            split) write a partial tile, the last writer of a tile summing them,
 //            and either
-//            (mode 0) store the next GEMM's B-operand planes, or
-//            (mode 1) the fused three-term recurrence in FP32 plus the planes, or
-//            (mode 2) Z = H X + gamma_col * X (no planes).
+//            (mode 0) store the next GEMM's B-operand pieces, or
+//            (mode 1) the fused three-term recurrence in FP32 plus the pieces, or
+//            (mode 2) Z = H X + gamma_col * X (no pieces).
 // Every mbarrier wait is bounded (2 s of %globaltimer); on expiry the kernel
-// sets an error flag, waits (bounded) for the copies in flight into its shared
+// sets an error flag, waits (bounded) for its copies in flight into its shared
 // memory, frees its TMEM and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 #include <cmath>
@@ -55,16 +65,40 @@ constexpr int BM = 128, BK = 64;
 constexpr int A_BYTES = BM * BK * 2;  // 16 KB per piece
 constexpr int GROUP_M = 8;            // tile raster: GROUP_M row tiles x all column tiles per group
 constexpr uint32_t TMEM_COLS = 512;   // two accumulator buffers (+ the cross products for 128-wide tiles)
-// instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, 128 x n
-__device__ __forceinline__ uint32_t make_idesc(int n) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+constexpr int VEXP_MAX = 100;         // |operand exponents| are clamped to this
+// instruction descriptor, kind::f16: D = F32, A = B = BF16 (bf16) or FP16, both K-major, 128 x n
+__device__ __forceinline__ uint32_t make_idesc(int n, bool bf16) {
+  return (1u << 4) | (bf16 ? ((1u << 7) | (1u << 10)) : 0u) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(BM >> 4) << 24);
 }
 
-// Scheme: pieces of A (NPA) and B (NPW), product list (product 0 is x0 * y0).
-template <int NP>
+// 16-bit piece types
+template <class T>
+struct Piece;
+template <>
+struct Piece<__nv_bfloat16> {
+  using T2 = __nv_bfloat162;
+  static constexpr bool BF16 = true;
+  __device__ static __nv_bfloat16 rn(float x) { return __float2bfloat16_rn(x); }
+  __device__ static float back(__nv_bfloat16 x) { return __bfloat162float(x); }
+  __device__ static T2 pair(__nv_bfloat16 a, __nv_bfloat16 b) { return __halves2bfloat162(a, b); }
+};
+template <>
+struct Piece<__half> {
+  using T2 = __half2;
+  static constexpr bool BF16 = false;
+  __device__ static __half rn(float x) { return __float2half_rn(x); }
+  __device__ static float back(__half x) { return __half2float(x); }
+  __device__ static T2 pair(__half a, __half b) { return __halves2half2(a, b); }
+};
+
+// Scheme: piece type, pieces of A (NPA) and B (NPW), product list (product 0 is x0 * y0).
+enum : int { SCH_BF16X3 = 1, SCH_BF16X6 = 2, SCH_FP16X3 = 3 };
+template <int SCH>
 struct Scheme;
 template <>
-struct Scheme<3> {  // BF16x3
+struct Scheme<SCH_BF16X3> {
+  using T = __nv_bfloat16;
   // FLUSH: K blocks per drained partial sum of x0 * y0 (16 truncating MMA additions
   // stay far below the 2^-16 error of the BF16 pieces; measured unchanged from 8)
   static constexpr int NPA = 2, NPW = 2, NPROD = 3, STAGES = 3, FLUSH = 4;
@@ -72,7 +106,15 @@ struct Scheme<3> {  // BF16x3
   __device__ static constexpr int pb(int i) { return i == 1 ? 1 : 0; }
 };
 template <>
-struct Scheme<6> {  // BF16x6
+struct Scheme<SCH_FP16X3> {
+  using T = __half;
+  static constexpr int NPA = 2, NPW = 2, NPROD = 3, STAGES = 3, FLUSH = 4;
+  __device__ static constexpr int pa(int i) { return i == 2 ? 1 : 0; }
+  __device__ static constexpr int pb(int i) { return i == 1 ? 1 : 0; }
+};
+template <>
+struct Scheme<SCH_BF16X6> {
+  using T = __nv_bfloat16;
   static constexpr int NPA = 3, NPW = 3, NPROD = 6, STAGES = 2, FLUSH = 2;
   // (0,0) (0,1) (1,0) (0,2) (1,1) (2,0)
   __device__ static constexpr int pa(int i) { return i == 2 ? 1 : (i == 4 ? 1 : (i == 5 ? 2 : 0)); }
@@ -82,14 +124,14 @@ struct Scheme<6> {  // BF16x6
 // two alternating TMEM buffers and the cross products accumulate over all of K in a
 // third; 8 drain warps of 64 columns (two per TMEM lane quarter: half the drain latency
 // of 4 warps of 128 columns, and 135 registers a thread instead of 228).  256-wide
-// (BF16x3 only): all products share the two alternating buffers (drained every FLUSH
-// K blocks, so the truncating accumulator sums at most FLUSH * 4 * NPROD MMAs); 16 drain
-// warps of 64 columns keep the FP32 partial sums in registers; a 2-stage ring of 96 KB.
-template <int NP, int BNT>
+// (two pieces only): all products share the two alternating buffers (drained every
+// FLUSH K blocks, so the truncating accumulator sums at most FLUSH * 4 * NPROD MMAs);
+// 16 drain warps of 64 columns keep the FP32 partial sums in registers; a 2-stage ring.
+template <int SCH, int BNT>
 struct Geo {
-  static constexpr int STAGES = (BNT == 256) ? 2 : Scheme<NP>::STAGES;
+  static constexpr int STAGES = (BNT == 256) ? 2 : Scheme<SCH>::STAGES;
   static constexpr int B_BYTES = BNT * BK * 2;
-  static constexpr int STAGE_BYTES = Scheme<NP>::NPA * A_BYTES + Scheme<NP>::NPW * B_BYTES;
+  static constexpr int STAGE_BYTES = Scheme<SCH>::NPA * A_BYTES + Scheme<SCH>::NPW * B_BYTES;
   static constexpr int NBAR = 2 * STAGES + 5;  // full, empty, acc_full[2], acc_empty[2], done
   static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
   static constexpr bool CROSS = (BNT == 128);             // separate cross-product buffer
@@ -101,48 +143,71 @@ struct Geo {
 };
 
 struct Epi {
-  int mode;           // 0: operand planes, 1: recurrence, 2: H X + gamma X
+  int mode;           // 0: operand pieces, 1: recurrence, 2: H X + gamma X
   int64_t n, k;       // rows of P, active vectors
-  int64_t kpad;       // elements per plane row
-  __nv_bfloat16* out[3];  // output operand pieces (NPW used)
+  int64_t kpad;       // elements per piece row
+  void* out[3];       // output operand pieces (NPW used)
   float2* Znext;
   const float2* Zcur;
   const float2* Zprev;
   const float2* src;
   const float* gamma;  // per column
   float alpha, beta, c;
+  // operand scaling: P' = diag(2^prow) P, input B' = w 2^vexp_in[v]; the pieces this
+  // launch writes get 2^vexp_out[v] chosen from the bound
+  //   ca * amax_a[v] + cb * amax_b[v] + cc * amax_c[v] + |gamma[v]| * amax_d[v]
+  // (amax_*: largest |component| of each input vector); amax_out receives the largest
+  // |component| of each output vector
+  const int* prow;
+  const int* vexp_in;
+  int* vexp_out;
+  float* amax_out;
+  const float* amax_a;
+  const float* amax_b;
+  const float* amax_c;
+  const float* amax_d;
+  float ca, cb, cc;
   int* err;
   float* part;  // split-K: one FP32 partial tile per CTA, column-major 128 x BNT
   int* cnt;     // split-K: per tile, partial tiles written so far (zero between launches)
   int sms;      // SMs of the device
 };
 
-// Work of one launch: the 128 x BNT output tiles in clusters of two CTAs that hold
-// the row blocks 2p and 2p + 1 of the same column tile nt.  Each CTA loads its own A
-// block and one half of the B block, which TMA multicasts into both CTAs: B comes from
-// L2 once per pair (48 instead of 64 KB per CTA and K block).  The pairs (p, nt) run in
-// a grouped raster (GROUP_P pairs x all column tiles), repeated for nsplit K ranges, so
-// that the CTAs running at the same time stream the same K blocks of A.  With an odd
-// number of row blocks the last pair's second CTA mirrors its partner's tile and writes
-// nothing.  With nsplit > 1 the splits leave FP32 partial tiles; the CTA that writes a
-// tile's last one (a per-tile counter) sums them in split order and runs the epilogue,
-// so no CTA waits for another and the result does not depend on timing.
-constexpr int GROUP_P = GROUP_M / 2;
+// 2^e as a float, |e| <= 126
+__device__ __forceinline__ float exp2i(int e) { return __int_as_float((e + 127) << 23); }
+// Operand exponent for entries bounded by b: b 2^e < 2^13 (b = m 2^x, m in [1/2, 1) -> e = 13 - x);
+// 0 for a zero, infinite or NaN bound.
+__device__ __forceinline__ int out_exp(float b) {
+  if (!(b > 0.0f) || !(b <= 3.0e38f)) return 0;
+  const int bits = __float_as_int(b);
+  const int x = ((bits >> 23) & 0xff) - 126;  // subnormal b: a smaller x, still a valid scale
+  return min(max(13 - x, -VEXP_MAX), VEXP_MAX);
+}
+__device__ __forceinline__ float vec_bound(const Epi& ep, int64_t v) {
+  float b = ep.ca * ep.amax_a[v];
+  if (ep.cb != 0.0f) b += ep.cb * ep.amax_b[v];
+  if (ep.cc != 0.0f) b += ep.cc * ep.amax_c[v];
+  if (ep.amax_d) b += fabsf(ep.gamma[v]) * ep.amax_d[v];
+  return b;
+}
+
+// Work of one launch: the 128 x BNT output tiles in a grouped raster (GROUP_M row
+// tiles x all column tiles), repeated for nsplit K ranges, so that the CTAs running at
+// the same time stream the same K blocks of A.  With nsplit > 1 the splits leave FP32
+// partial tiles; the CTA that writes a tile's last one (a per-tile counter) sums them in
+// split order and runs the epilogue, so no CTA waits for another and the result does
+// not depend on timing.
 struct Sched {
-  int nkb, num_m, num_n, npairs, n_last, bnt, nsplit, ntiles;
-  __device__ void unit(int c, int& mt, int& nt, int& sp, bool& mirror) const {
-    const int rank = c & 1, cl = c >> 1;
-    const int per_split = npairs * num_n;
-    sp = cl / per_split;
-    const int pidx = cl - sp * per_split;
-    const int per_group = GROUP_P * num_n;
-    const int g = pidx / per_group, first = g * GROUP_P;
-    const int gp = min(GROUP_P, npairs - first);
-    const int rem = pidx - g * per_group;
-    nt = rem / gp;
-    mt = 2 * (first + rem % gp) + rank;
-    mirror = mt >= num_m;
-    if (mirror) mt = num_m - 1;
+  int nkb, num_m, num_n, n_last, bnt, nsplit, ntiles;
+  __device__ void unit(int c, int& mt, int& nt, int& sp) const {
+    sp = c / ntiles;
+    const int t = c - sp * ntiles;
+    const int per_group = GROUP_M * num_n;
+    const int g = t / per_group, first = g * GROUP_M;
+    const int gm = min(GROUP_M, num_m - first);
+    const int rem = t - g * per_group;
+    nt = rem / gm;
+    mt = first + rem % gm;
   }
 };
 
@@ -187,31 +252,34 @@ __device__ __forceinline__ void drain_add16(uint32_t col, float* sum) {
   }
 }
 
-template <int NPC>
-__device__ __forceinline__ void put(__nv_bfloat16* const* pc, int64_t off, float a, float b) {
+// NPC pieces of the pair (a, b) at element offset off of every piece plane
+template <class T, int NPC>
+__device__ __forceinline__ void put(void* const* pc, int64_t off, float a, float b) {
+  using PT = Piece<T>;
 #pragma unroll
   for (int q = 0; q < NPC; ++q) {
-    const __nv_bfloat16 ha = __float2bfloat16_rn(a), hb = __float2bfloat16_rn(b);
-    *reinterpret_cast<__nv_bfloat162*>(pc[q] + off) = __halves2bfloat162(ha, hb);
-    a -= __bfloat162float(ha);
-    b -= __bfloat162float(hb);
+    const T ha = PT::rn(a), hb = PT::rn(b);
+    *reinterpret_cast<typename PT::T2*>(static_cast<T*>(pc[q]) + off) = PT::pair(ha, hb);
+    a -= PT::back(ha);
+    b -= PT::back(hb);
   }
 }
 // The four B-operand rows of vector v at K positions 2i (top entry t = w(i))
-// and 2(n+i) (bottom entry b = w(n+i)).
-template <int NPC>
-__device__ __forceinline__ void store_operand(__nv_bfloat16* const* pc, int64_t kpad, int64_t n, int64_t v, int64_t i,
-                                              float2 t, float2 b) {
+// and 2(n+i) (bottom entry b = w(n+i)), scaled by sc (a power of two).
+template <class T, int NPC>
+__device__ __forceinline__ void store_operand(void* const* pc, int64_t kpad, int64_t n, int64_t v, int64_t i,
+                                              float2 t, float2 b, float sc) {
+  t.x *= sc; t.y *= sc; b.x *= sc; b.y *= sc;
   const int64_t r0 = (4 * v) * kpad, r1 = r0 + kpad, r2 = r1 + kpad, r3 = r2 + kpad;
   const int64_t pt = 2 * i, pb = 2 * (n + i);
-  put<NPC>(pc, r0 + pt, t.x, -t.y);
-  put<NPC>(pc, r0 + pb, b.x, -b.y);
-  put<NPC>(pc, r1 + pt, t.y, t.x);
-  put<NPC>(pc, r1 + pb, b.y, b.x);
-  put<NPC>(pc, r2 + pt, b.x, b.y);   // u(i) = conj(b)
-  put<NPC>(pc, r2 + pb, t.x, t.y);   // u(n+i) = conj(t)
-  put<NPC>(pc, r3 + pt, -b.y, b.x);
-  put<NPC>(pc, r3 + pb, -t.y, t.x);
+  put<T, NPC>(pc, r0 + pt, t.x, -t.y);
+  put<T, NPC>(pc, r0 + pb, b.x, -b.y);
+  put<T, NPC>(pc, r1 + pt, t.y, t.x);
+  put<T, NPC>(pc, r1 + pb, b.y, b.x);
+  put<T, NPC>(pc, r2 + pt, b.x, b.y);   // u(i) = conj(b)
+  put<T, NPC>(pc, r2 + pb, t.x, t.y);   // u(n+i) = conj(t)
+  put<T, NPC>(pc, r3 + pt, -b.y, b.x);
+  put<T, NPC>(pc, r3 + pb, -t.y, t.x);
 }
 
 struct Maps {
@@ -223,14 +291,15 @@ struct Maps {
 // accumulate in one of two TMEM buffers that alternate every FLUSH K blocks; the drain
 // warps add each finished buffer into FP32 registers (round to nearest) while the MMA
 // fills the other one, so the tensor core's truncating accumulator only ever sums a
-// few MMAs.  With 128-wide tiles the cross products (2^-8 smaller) accumulate over the
-// whole K range in a third buffer instead.  The last column tile may be narrower
-// (n_last columns, a multiple of 16): its MMAs use N = n_last.
-template <int NP, int BNT>
-__global__ void __launch_bounds__(Geo<NP, BNT>::THREADS, 1)
+// few MMAs.  With 128-wide tiles the cross products (2^-8 or 2^-11 smaller)
+// accumulate over the whole K range in a third buffer instead.  The last column tile
+// may be narrower (n_last columns, a multiple of 16): its MMAs use N = n_last.
+template <int SCH, int BNT>
+__global__ void __launch_bounds__(Geo<SCH, BNT>::THREADS, 1)
     tc_hop_kernel(const __grid_constant__ Maps maps, Epi ep, Sched sc) {
-  using SC = Scheme<NP>;
-  using G = Geo<NP, BNT>;
+  using SC = Scheme<SCH>;
+  using G = Geo<SCH, BNT>;
+  using T = typename SC::T;
   constexpr int ST = G::STAGES;
   constexpr int DC = G::DCOLS;
   constexpr int FLUSH = SC::FLUSH;
@@ -253,9 +322,7 @@ __global__ void __launch_bounds__(Geo<NP, BNT>::THREADS, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   int mt, nt, sp;
-  bool mirror;
-  sc.unit(blockIdx.x, mt, nt, sp, mirror);
-  const int rank = (int)(blockIdx.x & 1);  // rank in the cluster of two
+  sc.unit(blockIdx.x, mt, nt, sp);
   const int tile = mt * sc.num_n + nt;
   const int m0 = mt * BM, n0 = nt * BNT;
   const int ntile = (nt == sc.num_n - 1) ? sc.n_last : BNT;  // columns of this tile (multiple of 16)
@@ -265,7 +332,7 @@ __global__ void __launch_bounds__(Geo<NP, BNT>::THREADS, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < ST; ++s) {
       mbar_init(full[s], 1);
-      mbar_init(empty[s], 2);  // released by the MMAs of both CTAs of the cluster
+      mbar_init(empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(accf[b], 1);
@@ -284,7 +351,6 @@ __global__ void __launch_bounds__(Geo<NP, BNT>::THREADS, 1)
   }
   tc_fence_before();
   __syncthreads();
-  cluster_sync();  // the partner's barriers are initialised before any multicast reaches them
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   const uint32_t sbase = smem_u32(smem);
@@ -301,13 +367,12 @@ __global__ void __launch_bounds__(Geo<NP, BNT>::THREADS, 1)
       for (int q = 0; q < SC::NPA; ++q) tma_load_2d(st + q * A_BYTES, &maps.a[q], (kb0 + kb) * BK, m0, full[s]);
 #pragma unroll
       for (int q = 0; q < SC::NPW; ++q)
-        tma_load_2d_mc(st + SC::NPA * A_BYTES + q * G::B_BYTES + rank * (G::B_BYTES / 2), &maps.b[q], (kb0 + kb) * BK,
-                       n0 + rank * (BNT / 2), full[s], 0x3);
+        tma_load_2d(st + SC::NPA * A_BYTES + q * G::B_BYTES, &maps.b[q], (kb0 + kb) * BK, n0, full[s]);
       issued = kb + 1;
     }
     *issued_sh = issued;
   } else if (warp == 1 && lane == 0) {
-    const uint32_t idesc = make_idesc(ntile);
+    const uint32_t idesc = make_idesc(ntile, Piece<T>::BF16);
     const uint32_t small = tmem + (uint32_t)(2 * BNT);
     const uint64_t dbase = sdesc(sbase);
     for (int kb = 0; kb < num_kb; ++kb) {
@@ -340,7 +405,7 @@ __global__ void __launch_bounds__(Geo<NP, BNT>::THREADS, 1)
           }
         }
       }
-      mma_commit_mc(empty[s], 0x3);
+      mma_commit(empty[s]);
       if (last) mma_commit(accf[b]);
     }
     mma_commit(done);  // completes once every MMA issued above has finished
@@ -379,9 +444,7 @@ __global__ void __launch_bounds__(Geo<NP, BNT>::THREADS, 1)
         drain_add<DC>(tmem + lane_base + (uint32_t)(2 * BNT + col0), sum);
       }
     }
-    if (mirror) {
-      ok = false;  // the partner CTA writes this tile
-    } else if (sc.nsplit > 1) {
+    if (sc.nsplit > 1) {
       // split tile: write this K range's partial; the last writer sums them all.  Every
       // drain warp passes both named barriers, also after a failed wait.
       constexpr int DRAIN_THREADS = 32 * G::DRAIN_WARPS;
@@ -412,24 +475,27 @@ __global__ void __launch_bounds__(Geo<NP, BNT>::THREADS, 1)
       }
     }
     const int64_t row = (int64_t)m0 + q * 32 + lane;
-    if (ok && has_cols && !*abort_sh && row < ep.n) {
+    const bool rvalid = row < ep.n;
+    const bool go = ok && has_cols && __all_sync(0xffffffffu, *abort_sh == 0);  // warp-uniform
+    if (go) {
       const int64_t n = ep.n, n2 = 2 * ep.n;
+      const float rs = rvalid ? exp2i(-ep.prow[row]) : 0.0f;  // undo the row scaling of P
 #pragma unroll
       for (int c = 0; c < DC / 32; ++c) {
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
           const int64_t vg = (int64_t)((n0 + col0) >> 2) + c * 8 + t;
-          if (vg >= ep.k) continue;
+          if (vg >= ep.k) continue;  // uniform over the warp
           const float* v = sum + c * 32;
-          const float2 ht = make_float2(v[4 * t], v[4 * t + 1]);        // (H x)_top(row)
-          const float2 hb = make_float2(-v[4 * t + 2], v[4 * t + 3]);   // (H x)_bot(row)
+          const float vs = exp2i(-ep.vexp_in[vg]);  // and the scaling of the input vector
+          const float2 ht = make_float2(v[4 * t] * rs * vs, v[4 * t + 1] * rs * vs);        // (H x)_top(row)
+          const float2 hb = make_float2(-v[4 * t + 2] * rs * vs, v[4 * t + 3] * rs * vs);   // (H x)_bot(row)
           const int64_t ot = vg * n2 + row, ob = ot + n;
-          if (ep.mode == 0) {
-            store_operand<SC::NPW>(ep.out, ep.kpad, n, vg, row, ht, hb);
-          } else if (ep.mode == 1) {
+          float2 zt = ht, zb = hb;
+          if (ep.mode == 1 && rvalid) {
             const float2 ct = ep.Zcur[ot], cbv = ep.Zcur[ob];
-            float2 zt = make_float2(ep.alpha * (ht.x - ep.c * ct.x), ep.alpha * (ht.y - ep.c * ct.y));
-            float2 zb = make_float2(ep.alpha * (hb.x - ep.c * cbv.x), ep.alpha * (hb.y - ep.c * cbv.y));
+            zt = make_float2(ep.alpha * (ht.x - ep.c * ct.x), ep.alpha * (ht.y - ep.c * ct.y));
+            zb = make_float2(ep.alpha * (hb.x - ep.c * cbv.x), ep.alpha * (hb.y - ep.c * cbv.y));
             if (ep.beta != 0.0f) {
               const float2 pt = ep.Zprev[ot], pb = ep.Zprev[ob];
               zt.x += ep.beta * pt.x; zt.y += ep.beta * pt.y;
@@ -441,15 +507,24 @@ __global__ void __launch_bounds__(Geo<NP, BNT>::THREADS, 1)
               zt.x += gmm * st.x; zt.y += gmm * st.y;
               zb.x += gmm * sb.x; zb.y += gmm * sb.y;
             }
-            ep.Znext[ot] = zt;
-            ep.Znext[ob] = zb;
-            store_operand<SC::NPW>(ep.out, ep.kpad, n, vg, row, zt, zb);
-          } else {
+          } else if (ep.mode == 2 && rvalid) {
             const float gmm = ep.gamma[vg];
             const float2 ct = ep.Zcur[ot], cbv = ep.Zcur[ob];
-            ep.Znext[ot] = make_float2(ht.x + gmm * ct.x, ht.y + gmm * ct.y);
-            ep.Znext[ob] = make_float2(hb.x + gmm * cbv.x, hb.y + gmm * cbv.y);
+            zt = make_float2(ht.x + gmm * ct.x, ht.y + gmm * ct.y);
+            zb = make_float2(hb.x + gmm * cbv.x, hb.y + gmm * cbv.y);
           }
+          if (ep.mode != 0 && rvalid) {
+            ep.Znext[ot] = zt;
+            ep.Znext[ob] = zb;
+          }
+          if (ep.mode != 2) {
+            const int e = out_exp(vec_bound(ep, vg));
+            if (rvalid) store_operand<T, SC::NPW>(ep.out, ep.kpad, n, vg, row, zt, zb, exp2i(e));
+            if (lane == 0) ep.vexp_out[vg] = e;  // the same value from every tile
+          }
+          const float m = rvalid ? fmaxf(fmaxf(fabsf(zt.x), fabsf(zt.y)), fmaxf(fabsf(zb.x), fabsf(zb.y))) : 0.0f;
+          const unsigned mm = __reduce_max_sync(0xffffffffu, __float_as_uint(m));
+          if (lane == 0) atomicMax(reinterpret_cast<unsigned*>(ep.amax_out) + vg, mm);
         }
       }
     }
@@ -457,13 +532,10 @@ __global__ void __launch_bounds__(Geo<NP, BNT>::THREADS, 1)
   tc_fence_before();
   __syncthreads();
   if (threadIdx.x == 0 && *abort_sh) {
-    // drain copies still in flight into this CTA's shared memory (bounded), then give
-    // the partner's multicast copies time to land
+    // drain copies still in flight into this CTA's shared memory (bounded)
     const int issued = *issued_sh;
     for (int kb = max(0, issued - ST); kb < issued; ++kb)
       mbar_wait(full[kb % ST], (uint32_t)(kb / ST) & 1u, abort_sh, ep.err, false);
-    const uint64_t t0 = gtimer();
-    while (gtimer() - t0 < 100000ull) __nanosleep(1000);
   }
   if (warp == 1) {
     // every MMA has finished before the accumulator memory is released
@@ -475,29 +547,90 @@ __global__ void __launch_bounds__(Geo<NP, BNT>::THREADS, 1)
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
   }
-  cluster_sync();  // no CTA leaves while its partner may still multicast into it
 }
 
 // ---------------------------------------------------------------- helpers
 struct Pieces {
-  __nv_bfloat16* p[3];
+  void* p[3];
 };
 
-// P = [A | B] (row-major complex128) -> NPC BF16 pieces, row i, K = (re, im) pairs.
-template <int NPC>
-__global__ void split_p_kernel(const cplx* A, const cplx* B, int64_t n, int64_t kpad, Pieces out) {
-  const int64_t total = n * 2 * n;
-  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = idx / (2 * n), l = idx % (2 * n);
+// block-wide max and sum of one value per thread (blockDim.x a multiple of 32, <= 1024)
+__device__ __forceinline__ void block_max_sum(float& m, float& s) {
+  __shared__ float wm[32], ws[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    s += __shfl_xor_sync(0xffffffffu, s, o);
+  }
+  if (lane == 0) {
+    wm[w] = m;
+    ws[w] = s;
+  }
+  __syncthreads();
+  if (w == 0) {
+    m = lane < nw ? wm[lane] : 0.0f;
+    s = lane < nw ? ws[lane] : 0.0f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+      s += __shfl_xor_sync(0xffffffffu, s, o);
+    }
+    if (lane == 0) {
+      wm[0] = m;
+      ws[0] = s;
+    }
+  }
+  __syncthreads();
+  m = wm[0];
+  s = ws[0];
+}
+
+// P = [A | B] (row-major complex128) -> NPC pieces, one CTA per row i, K = (re, im)
+// pairs, scaled by 2^prow[i] (largest entry of the row in [2^12, 2^13)); L receives the
+// largest row sum of |Re| + |Im| (unscaled), the bound factor of an H application.
+template <class T, int NPC>
+__global__ void split_p_kernel(const cplx* A, const cplx* B, int64_t n, int64_t kpad, Pieces out, int* prow,
+                               float* L) {
+  const int64_t i = blockIdx.x;
+  float m = 0.0f, sum = 0.0f;
+  for (int64_t l = threadIdx.x; l < 2 * n; l += blockDim.x) {
     const cplx p = (l < n) ? A[i * n + l] : B[i * n + (l - n)];
-    put<NPC>(out.p, i * kpad + 2 * l, (float)p.x, (float)p.y);
+    const float x = fabsf((float)p.x), y = fabsf((float)p.y);
+    m = fmaxf(m, fmaxf(x, y));
+    sum += x + y;
+  }
+  block_max_sum(m, sum);
+  const int e = out_exp(m);
+  if (threadIdx.x == 0) {
+    prow[i] = e;
+    atomicMax(reinterpret_cast<unsigned*>(L), __float_as_uint(sum));
+  }
+  const float sc = exp2i(e);
+  for (int64_t l = threadIdx.x; l < 2 * n; l += blockDim.x) {
+    const cplx p = (l < n) ? A[i * n + l] : B[i * n + (l - n)];
+    put<T, NPC>(out.p, i * kpad + 2 * l, (float)p.x * sc, (float)p.y * sc);
   }
 }
-// complex128 block (2n x k) -> FP32 master and, optionally, operand pieces
-template <int NPC>
+// amax[v] = largest |Re|, |Im| of column v of the complex128 block W (2n x k), rounded to
+// FP32, and vexp[v] its operand exponent; one CTA per column
+__global__ void col_amax_kernel(const cplx* W, int64_t n2, float* amax, int* vexp) {
+  const int64_t v = blockIdx.x;
+  float m = 0.0f, unused = 0.0f;
+  for (int64_t i = threadIdx.x; i < n2; i += blockDim.x) {
+    const cplx w = W[v * n2 + i];
+    m = fmaxf(m, fmaxf(fabsf((float)w.x), fabsf((float)w.y)));
+  }
+  block_max_sum(m, unused);
+  if (threadIdx.x == 0) {
+    amax[v] = m;
+    vexp[v] = out_exp(m);
+  }
+}
+// complex128 block (2n x k) -> FP32 master and, optionally, operand pieces (exponents vexp)
+template <class T, int NPC>
 __global__ void pack_kernel(const cplx* W, int64_t n, int64_t k, float2* Z, Pieces out, int with_pieces,
-                            int64_t kpad) {
+                            int64_t kpad, const int* vexp) {
   const int64_t total = n * k;
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
@@ -509,22 +642,29 @@ __global__ void pack_kernel(const cplx* W, int64_t n, int64_t k, float2* Z, Piec
       Z[v * 2 * n + i] = t;
       Z[v * 2 * n + n + i] = b;
     }
-    if (with_pieces) store_operand<NPC>(out.p, kpad, n, v, i, t, b);
+    if (with_pieces) store_operand<T, NPC>(out.p, kpad, n, v, i, t, b, exp2i(vexp[v]));
   }
 }
-// Z = scale * X (FP32 master) and its operand pieces
-template <int NPC>
+// Z = scale * X (FP32 master) and its operand pieces; the largest component of column v
+// is |scale| amax_x[v] (up to rounding), which sets its exponent
+template <class T, int NPC>
 __global__ void scale_pack_kernel(const float2* X, int64_t n, int64_t k, float scale, float2* Z, Pieces out,
-                                  int64_t kpad) {
+                                  int64_t kpad, const float* amax_x, float* amax_z, int* vexp_z) {
   const int64_t total = n * k;
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = idx % n, v = idx / n;
+    const float am = fabsf(scale) * amax_x[v];
+    const int e = out_exp(am);
+    if (i == 0) {
+      amax_z[v] = am;
+      vexp_z[v] = e;
+    }
     const float2 xt = X[v * 2 * n + i], xb = X[v * 2 * n + n + i];
     const float2 t = make_float2(scale * xt.x, scale * xt.y), b = make_float2(scale * xb.x, scale * xb.y);
     Z[v * 2 * n + i] = t;
     Z[v * 2 * n + n + i] = b;
-    store_operand<NPC>(out.p, kpad, n, v, i, t, b);
+    store_operand<T, NPC>(out.p, kpad, n, v, i, t, b, exp2i(e));
   }
 }
 // out[:, v] = (double) Zsel[:, v] + coef[v] * base[:, v]   (coef/base optional)
@@ -542,16 +682,16 @@ __global__ void combine_kernel(cplx* out, const float2* Z0, const float2* Z1, co
   }
 }
 
-static int make_map(CUtensorMap* m, const void* base, int64_t kpad, int64_t rows, int box_rows) {
+static int make_map(CUtensorMap* m, const void* base, int64_t kpad, int64_t rows, int box_rows, bool bf16) {
   auto fn = encode_fn();
   if (!fn) return CHASE_BSE_UNSUPPORTED;
   const cuuint64_t dims[2] = {(cuuint64_t)kpad, (cuuint64_t)rows};
   const cuuint64_t strides[1] = {(cuuint64_t)kpad * 2};
   const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
   const cuuint32_t estr[2] = {1, 1};
-  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r = fn(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
+                  const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? CHASE_BSE_OK : CHASE_BSE_CUDA_ERROR;
 }
 
@@ -560,34 +700,43 @@ static inline unsigned gsz(int64_t total) {
   return (unsigned)std::min<int64_t>(std::max<int64_t>(b, 1), 16384);
 }
 
-// The operand of P = [A | B] in NPA BF16 pieces, with its tensor maps.
+// The operand of P = [A | B] in NPA pieces, with its tensor maps, row exponents and
+// the bound factor L (device scalar).
 struct POperand {
   int64_t n = 0, kpad = 0;
   Pieces pc{};
   CUtensorMap map[3];
+  int* prow = nullptr;
+  float* L = nullptr;
 };
 
-template <int NP>
+template <int SCH>
 static int prepare_p(const cplx* A, const cplx* B, int64_t n, Workspace& ws, POperand& P, cudaStream_t s) {
-  constexpr int NPA = Scheme<NP>::NPA;
+  using T = typename Scheme<SCH>::T;
+  constexpr int NPA = Scheme<SCH>::NPA;
   P.n = n;
   P.kpad = ((4 * n + BK - 1) / BK) * BK;
   const int64_t rows = ((n + BM - 1) / BM) * BM;  // whole tiles: every TMA box lies inside the tensor
   for (int q = 0; q < NPA; ++q) {
-    CB_TRY(ws.alloc(&P.pc.p[q], rows * P.kpad));
-    CB_CUDA(cudaMemsetAsync(P.pc.p[q], 0, sizeof(__nv_bfloat16) * rows * P.kpad, s));
+    T* pq;
+    CB_TRY(ws.alloc(&pq, rows * P.kpad));
+    P.pc.p[q] = pq;
+    CB_CUDA(cudaMemsetAsync(pq, 0, sizeof(T) * rows * P.kpad, s));
   }
-  split_p_kernel<NPA><<<gsz(2 * n * n), 256, 0, s>>>(A, B, n, P.kpad, P.pc);
+  CB_TRY(ws.alloc(&P.prow, n));
+  CB_TRY(ws.alloc(&P.L, 1));
+  CB_CUDA(cudaMemsetAsync(P.L, 0, sizeof(float), s));
+  split_p_kernel<T, NPA><<<(unsigned)n, 256, 0, s>>>(A, B, n, P.kpad, P.pc, P.prow, P.L);
   count_launch();
   CB_LAUNCH();
-  for (int q = 0; q < NPA; ++q) CB_TRY(make_map(&P.map[q], P.pc.p[q], P.kpad, rows, BM));
+  for (int q = 0; q < NPA; ++q) CB_TRY(make_map(&P.map[q], P.pc.p[q], P.kpad, rows, BM, Piece<T>::BF16));
   return CHASE_BSE_OK;
 }
 
 // Output tile width: 128 columns.  (256-wide BF16x3 tiles with a 2-stage ring and 16
 // drain warps measured slower at n = 4096, k = 260: 293 against 306 TFLOP/s; the
 // kernel keeps both geometries.)
-template <int NP>
+template <int SCH>
 struct TileN {
   static constexpr int value = 128;
 };
@@ -614,20 +763,21 @@ static int split_count(int tiles, int nkb, int sms, int flush) {
 
 // One tensor-core application of H to the vectors held in the operand pieces
 // described by bmap, with epilogue `ep`.
-template <int NP>
+template <int SCH>
 static int apply(const POperand& P, const CUtensorMap* bmap, Epi ep, cudaStream_t s) {
-  constexpr int BNT = TileN<NP>::value;
-  using G = Geo<NP, BNT>;
+  constexpr int BNT = TileN<SCH>::value;
+  using G = Geo<SCH, BNT>;
   if (ep.k <= 0) return CHASE_BSE_OK;
   static bool attr = false;
   if (!attr) {
-    CB_CUDA(cudaFuncSetAttribute(tc_hop_kernel<NP, BNT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    CB_CUDA(cudaFuncSetAttribute(tc_hop_kernel<SCH, BNT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  G::SMEM_BYTES));
     attr = true;
   }
   Maps maps;
-  for (int q = 0; q < Scheme<NP>::NPA; ++q) maps.a[q] = P.map[q];
-  for (int q = 0; q < Scheme<NP>::NPW; ++q) maps.b[q] = bmap[q];
+  for (int q = 0; q < Scheme<SCH>::NPA; ++q) maps.a[q] = P.map[q];
+  for (int q = 0; q < Scheme<SCH>::NPW; ++q) maps.b[q] = bmap[q];
+  ep.prow = P.prow;
   Sched sc{};
   sc.num_m = (int)cdiv(P.n, BM);
   sc.num_n = (int)cdiv(4 * ep.k, BNT);
@@ -636,22 +786,8 @@ static int apply(const POperand& P, const CUtensorMap* bmap, Epi ep, cudaStream_
   sc.nkb = (int)(P.kpad / BK);
   sc.bnt = BNT;
   sc.ntiles = sc.num_m * sc.num_n;
-  sc.npairs = (sc.num_m + 1) / 2;
-  const int ctas = 2 * sc.npairs * sc.num_n;  // per K split
-  sc.nsplit = split_count(ctas, sc.nkb, ep.sms, Scheme<NP>::FLUSH);
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(ctas * sc.nsplit));
-  cfg.blockDim = dim3(G::THREADS);
-  cfg.dynamicSmemBytes = G::SMEM_BYTES;
-  cfg.stream = s;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = 2;
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  CB_CUDA(cudaLaunchKernelEx(&cfg, tc_hop_kernel<NP, BNT>, maps, ep, sc));
+  sc.nsplit = split_count(sc.ntiles, sc.nkb, ep.sms, Scheme<SCH>::FLUSH);
+  tc_hop_kernel<SCH, BNT><<<(unsigned)(sc.ntiles * sc.nsplit), G::THREADS, G::SMEM_BYTES, s>>>(maps, ep, sc);
   count_launch();
   CB_LAUNCH();
   return CHASE_BSE_OK;
@@ -665,27 +801,32 @@ static int apply(const POperand& P, const CUtensorMap* bmap, Epi ep, cudaStream_
 // with the source term alpha_j p_j(m_i) r2_i (divided differences of the
 // three-term recurrence).  The low-precision error then scales with the
 // residual of v_i instead of with v_i.
-template <int NP>
+template <int SCH>
 static int filter_impl(const cplx* A, const cplx* B, int64_t n, const cplx* Y0, int64_t k, const int* degs,
                        double mu1, double mu_nevex, double muN, cplx* out, const double* ritz, const cplx* R,
                        cudaStream_t s, FilterStats* fs) {
-  constexpr int NPW = Scheme<NP>::NPW;
+  using T = typename Scheme<SCH>::T;
+  constexpr int NPW = Scheme<SCH>::NPW;
+  constexpr bool BF = Piece<T>::BF16;
   if (k == 0) return CHASE_BSE_OK;
   const int64_t n2 = 2 * n;
   Workspace ws(s);
   POperand P;
-  CB_TRY(prepare_p<NP>(A, B, n, ws, P, s));
-  constexpr int BNT = TileN<NP>::value;
+  CB_TRY(prepare_p<SCH>(A, B, n, ws, P, s));
+  constexpr int BNT = TileN<SCH>::value;
   const int64_t rows = ((4 * k + BNT - 1) / BNT) * BNT;  // whole tiles
   Pieces Zp{}, Tp{};
   CUtensorMap mZ[3], mT[3];
   for (int q = 0; q < NPW; ++q) {
-    CB_TRY(ws.alloc(&Zp.p[q], rows * P.kpad));
-    CB_TRY(ws.alloc(&Tp.p[q], rows * P.kpad));
-    CB_CUDA(cudaMemsetAsync(Zp.p[q], 0, sizeof(__nv_bfloat16) * rows * P.kpad, s));
-    CB_CUDA(cudaMemsetAsync(Tp.p[q], 0, sizeof(__nv_bfloat16) * rows * P.kpad, s));
-    CB_TRY(make_map(&mZ[q], Zp.p[q], P.kpad, rows, BNT / 2));  // half tiles, multicast
-    CB_TRY(make_map(&mT[q], Tp.p[q], P.kpad, rows, BNT / 2));
+    T *zq, *tq;
+    CB_TRY(ws.alloc(&zq, rows * P.kpad));
+    CB_TRY(ws.alloc(&tq, rows * P.kpad));
+    Zp.p[q] = zq;
+    Tp.p[q] = tq;
+    CB_CUDA(cudaMemsetAsync(zq, 0, sizeof(T) * rows * P.kpad, s));
+    CB_CUDA(cudaMemsetAsync(tq, 0, sizeof(T) * rows * P.kpad, s));
+    CB_TRY(make_map(&mZ[q], zq, P.kpad, rows, BNT, BF));
+    CB_TRY(make_map(&mT[q], tq, P.kpad, rows, BNT, BF));
   }
   float2 *Zb[3], *src = nullptr;
   float* gam;
@@ -716,6 +857,23 @@ static int filter_impl(const cplx* A, const cplx* B, int64_t n, const cplx* Y0, 
   const double sigma1 = e / (mu1 * mu1 - c);
   const double tau = 2.0 / sigma1;
   const int maxdeg = degs[0];
+  // per-vector maxima and operand exponents, one slot of k entries per vector block:
+  // Z_j (j = 0 .. maxdeg), T_j = H Z_j (j < maxdeg), the residual block R and the
+  // correction source r2
+  const int64_t nslot = 2 * (int64_t)maxdeg + 3;
+  float* amax;
+  int* vexp;
+  CB_TRY(ws.alloc(&amax, nslot * k));
+  CB_TRY(ws.alloc(&vexp, nslot * k));
+  CB_CUDA(cudaMemsetAsync(amax, 0, sizeof(float) * nslot * k, s));
+  CB_CUDA(cudaMemsetAsync(vexp, 0, sizeof(int) * nslot * k, s));
+  auto slotZ = [&](int j) { return (int64_t)j * k; };
+  auto slotT = [&](int j) { return (int64_t)(maxdeg + 1 + j) * k; };
+  const int64_t slotR = (int64_t)(2 * maxdeg + 1) * k, slotS = (int64_t)(2 * maxdeg + 2) * k;
+  float L = 0.0f;
+  CB_CUDA(cudaMemcpyAsync(&L, P.L, sizeof(float), cudaMemcpyDeviceToHost, s));
+  CB_CUDA(cudaStreamSynchronize(s));
+
   std::vector<double> al(maxdeg), be(maxdeg);  // alpha_j, beta_j of the scaled recurrence
   {
     double sigma = sigma1;
@@ -752,22 +910,29 @@ static int filter_impl(const cplx* A, const cplx* B, int64_t n, const cplx* Y0, 
   CB_CUDA(cudaEventCreate(&e1));
   CB_CUDA(cudaEventRecord(e0, s));
   if (!corr) {
-    pack_kernel<NPW><<<gsz(n * k), 256, 0, s>>>(Y0, n, k, Zb[0], Zp, 1, P.kpad);  // Z_0 = W
+    col_amax_kernel<<<(unsigned)k, 256, 0, s>>>(Y0, n2, amax + slotZ(0), vexp + slotZ(0));
+    count_launch();
+    pack_kernel<T, NPW><<<gsz(n * k), 256, 0, s>>>(Y0, n, k, Zb[0], Zp, 1, P.kpad, vexp + slotZ(0));  // Z_0 = W
     count_launch();
     CB_LAUNCH();
   } else {
     // r2 = H R + ritz R on the tensor cores; Z_0 = 0; Z_1 = alpha_0 r2
     CB_TRY(ws.alloc(&src, n2 * k));
-    pack_kernel<NPW><<<gsz(n * k), 256, 0, s>>>(R, n, k, Zb[2], Zp, 1, P.kpad);
+    col_amax_kernel<<<(unsigned)k, 256, 0, s>>>(R, n2, amax + slotR, vexp + slotR);
+    count_launch();
+    pack_kernel<T, NPW><<<gsz(n * k), 256, 0, s>>>(R, n, k, Zb[2], Zp, 1, P.kpad, vexp + slotR);
     count_launch();
     for (int64_t i = 0; i < k; ++i) gh[i] = (float)ritz[i];
     CB_CUDA(cudaMemcpyAsync(gam, gh.data(), sizeof(float) * k, cudaMemcpyHostToDevice, s));
     Epi ep{};
     ep.mode = 2; ep.n = n; ep.k = k; ep.kpad = P.kpad; ep.Znext = src; ep.Zcur = Zb[2]; ep.gamma = gam; ep.err = err;
+    ep.vexp_in = vexp + slotR;
+    ep.amax_out = amax + slotS;
     sk(ep);
-    CB_TRY(apply<NP>(P, mZ, ep, s));
+    CB_TRY(apply<SCH>(P, mZ, ep, s));
     CB_CUDA(cudaMemsetAsync(Zb[0], 0, sizeof(float2) * n2 * k, s));
-    scale_pack_kernel<NPW><<<gsz(n * k), 256, 0, s>>>(src, n, k, (float)al[0], Zb[1], Zp, P.kpad);
+    scale_pack_kernel<T, NPW><<<gsz(n * k), 256, 0, s>>>(src, n, k, (float)al[0], Zb[1], Zp, P.kpad,
+                                                          amax + slotS, amax + slotZ(1), vexp + slotZ(1));
     count_launch();
     CB_LAUNCH();
     j0 = 1;
@@ -783,20 +948,35 @@ static int filter_impl(const cplx* A, const cplx* B, int64_t n, const cplx* Y0, 
     e1p.mode = 0; e1p.n = n; e1p.k = kj; e1p.kpad = P.kpad; e1p.err = err;
     sk(e1p);
     for (int q = 0; q < NPW; ++q) e1p.out[q] = Tp.p[q];
-    CB_TRY(apply<NP>(P, mZ, e1p, s));  // T = H Z_j
+    e1p.vexp_in = vexp + slotZ(j);
+    e1p.vexp_out = vexp + slotT(j);
+    e1p.amax_out = amax + slotT(j);
+    e1p.amax_a = amax + slotZ(j);
+    e1p.ca = L;
+    CB_TRY(apply<SCH>(P, mZ, e1p, s));  // T = H Z_j
     Epi e2p{};
     e2p.mode = 1; e2p.n = n; e2p.k = kj; e2p.kpad = P.kpad; e2p.err = err;
     sk(e2p);
     for (int q = 0; q < NPW; ++q) e2p.out[q] = Zp.p[q];
     e2p.Znext = Zb[(j + 1) % 3]; e2p.Zcur = Zb[j % 3]; e2p.Zprev = Zb[(j + 2) % 3];
     e2p.alpha = (float)al[j]; e2p.beta = (float)be[j]; e2p.c = (float)c;
+    e2p.vexp_in = vexp + slotT(j);
+    e2p.vexp_out = vexp + slotZ(j + 1);
+    e2p.amax_out = amax + slotZ(j + 1);
+    e2p.amax_a = amax + slotT(j);
+    e2p.amax_b = amax + slotZ(j);
+    e2p.amax_c = amax + slotZ(j > 0 ? j - 1 : 0);
+    e2p.ca = (float)(std::fabs(al[j]) * L);
+    e2p.cb = (float)std::fabs(al[j] * c);
+    e2p.cc = (float)std::fabs(be[j]);
     if (corr) {
       for (int64_t i = 0; i < kj; ++i) gh[i] = (float)(al[j] * pj[(size_t)j * k + i]);
       CB_CUDA(cudaMemcpyAsync(gam, gh.data(), sizeof(float) * kj, cudaMemcpyHostToDevice, s));
       e2p.src = src;
       e2p.gamma = gam;
+      e2p.amax_d = amax + slotS;
     }
-    CB_TRY(apply<NP>(P, mT, e2p, s));  // Z_{j+1} = alpha (H T - c Z_j) + beta Z_{j-1} (+ source)
+    CB_TRY(apply<SCH>(P, mT, e2p, s));  // Z_{j+1} = alpha (H T - c Z_j) + beta Z_{j-1} (+ source)
     if (fs) {
       fs->flops += 64.0 * (double)n * (double)n * (double)kj;
       fs->launches += 2;
@@ -844,21 +1024,39 @@ bool mixed_available() {
   return major == 10 && minor == 3 && tc::encode_fn() != nullptr;
 }
 
+template <int SCH>
+static int filter_dispatch(const cplx* A, const cplx* B, int64_t n, cplx* V, int64_t k, const int* degs,
+                           double mu1, double mu_nevex, double muN, cplx* out, const double* ritz, const cplx* R,
+                           cudaStream_t s, FilterStats* fs) {
+  return tc::filter_impl<SCH>(A, B, n, V, k, degs, mu1, mu_nevex, muN, out, ritz, R, s, fs);
+}
+
+static int filter_scheme(int scheme, const cplx* A, const cplx* B, int64_t n, cplx* V, int64_t k, const int* degs,
+                         double mu1, double mu_nevex, double muN, cplx* out, const double* ritz, const cplx* R,
+                         cudaStream_t s, FilterStats* fs) {
+  switch (scheme) {
+    case SCHEME_BF16X3:
+      return filter_dispatch<tc::SCH_BF16X3>(A, B, n, V, k, degs, mu1, mu_nevex, muN, out, ritz, R, s, fs);
+    case SCHEME_BF16X6:
+      return filter_dispatch<tc::SCH_BF16X6>(A, B, n, V, k, degs, mu1, mu_nevex, muN, out, ritz, R, s, fs);
+    case SCHEME_FP16X3:
+      return filter_dispatch<tc::SCH_FP16X3>(A, B, n, V, k, degs, mu1, mu_nevex, muN, out, ritz, R, s, fs);
+    default:
+      return CHASE_BSE_BAD_ARG;
+  }
+}
+
 int filter_mixed_sorted(const cplx* A, const cplx* B, int64_t n, cplx* Y0, int64_t k, const int* degs_sorted,
                         double mu1, double mu_nevex, double muN, cplx* out, int scheme, cudaStream_t s,
                         FilterStats* fs) {
-  if (scheme == 6)
-    return tc::filter_impl<6>(A, B, n, Y0, k, degs_sorted, mu1, mu_nevex, muN, out, nullptr, nullptr, s, fs);
-  return tc::filter_impl<3>(A, B, n, Y0, k, degs_sorted, mu1, mu_nevex, muN, out, nullptr, nullptr, s, fs);
+  return filter_scheme(scheme, A, B, n, Y0, k, degs_sorted, mu1, mu_nevex, muN, out, nullptr, nullptr, s, fs);
 }
 
 int filter_mixed_correction_sorted(const cplx* A, const cplx* B, int64_t n, cplx* V, int64_t k,
                                    const int* degs_sorted, const double* ritz_sorted, const cplx* R, double mu1,
                                    double mu_nevex, double muN, cplx* out, int scheme, cudaStream_t s,
                                    FilterStats* fs) {
-  if (scheme == 6)
-    return tc::filter_impl<6>(A, B, n, V, k, degs_sorted, mu1, mu_nevex, muN, out, ritz_sorted, R, s, fs);
-  return tc::filter_impl<3>(A, B, n, V, k, degs_sorted, mu1, mu_nevex, muN, out, ritz_sorted, R, s, fs);
+  return filter_scheme(scheme, A, B, n, V, k, degs_sorted, mu1, mu_nevex, muN, out, ritz_sorted, R, s, fs);
 }
 
 }  // namespace cb

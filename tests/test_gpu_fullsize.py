@@ -14,7 +14,7 @@ GPU output with the plain FP64 formulas:
   (S H, S), the number of negative eigenvalues of S H - sigma S is the number of
   eigenvalues of H in (0, sigma); just above lambda_nev it is nev, just below
   lambda_1 it is 0;
-* sampled columns of the filter against the oracle filter (column by column);
+* the whole filter block against the oracle filter (element by element);
 * the eigenvalue gradient against the oracle's formula on the same vectors and
   against central finite differences of the solve.
 """
@@ -28,7 +28,9 @@ from tests.gpu_util import rel_fro, to_dev
 
 pytestmark = pytest.mark.gpu
 
-TOL_FILTER = {"fp64": 1e-12, "mixed": 6e-5}
+# FP64 filter: 1e-12; tensor-core filter (FP16x3, the default mixed scheme): the 1e-5
+# gate of an FP32 filter, relative Frobenius over the whole block
+TOL_FILTER = {"fp64": 1e-12, "mixed": 1e-5}
 
 
 @pytest.fixture(scope="module")
@@ -70,7 +72,9 @@ def _negative_count(M):
 
 
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])
-def test_c2_filter_sampled_columns(pkg, c2, precision):
+def test_c2_filter_full_block(pkg, c2, precision):
+    """The whole n = 4096, k = 260, degree-20 filter block against the oracle filter,
+    element by element (relative Frobenius over the block)."""
     if precision == "mixed" and not pkg.has_mixed():
         pytest.fail("tensor-core filter not available on this device")
     wl, P, W0, _ = c2
@@ -78,11 +82,12 @@ def test_c2_filter_sampled_columns(pkg, c2, precision):
     mus = (1.0, 2.0, 45.0)
     W = to_dev(W0)
     pkg.filter(to_dev(P.A), to_dev(P.B), W, [deg] * k, *mus, precision=precision)
-    got = W.cpu().numpy()
-    cols = [0, 137, k - 1]
-    ref = chebyshev.chebyshev_filter(P.A, P.B, W0[cols].T, [deg] * len(cols), *mus)
-    for j, c in enumerate(cols):
-        assert rel_fro(got[c], ref[:, j]) < TOL_FILTER[precision], c
+    got = W.cpu().numpy().T
+    ref = chebyshev.chebyshev_filter(P.A, P.B, W0.T, [deg] * k, *mus)
+    assert rel_fro(got, ref) < TOL_FILTER[precision]
+    # and column by column (no column may hide behind the large ones)
+    colerr = np.linalg.norm(got - ref, axis=0) / np.linalg.norm(ref, axis=0)
+    assert colerr.max() < 10 * TOL_FILTER[precision], colerr.max()
 
 
 def test_c2_mixed_solve_properties(pkg, c2):

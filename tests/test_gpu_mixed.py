@@ -10,10 +10,12 @@ from tests.gpu_util import problem_on_device, rel_fro, starts, to_dev
 pytestmark = pytest.mark.gpu
 
 # Relative Frobenius tolerances of the tensor-core filter against the FP64 oracle.
-# BF16x6 keeps 24 significant bits of each operand (FP32 class): the 1e-5 gate of
-# an FP32 filter applies.  BF16x3 keeps 16 bits of each operand: the representation
-# error is 2 * 2^-17 = 1.5e-5 per product, and the recurrence adds a small factor.
-TOL = {"bf16x6": 1e-5, "bf16x3": 6e-5}
+# FP16x3 (the default mixed scheme) keeps 22 significant bits of each operand and
+# BF16x6 24 (FP32 class): the 1e-5 gate of an FP32 filter applies.  BF16x3 keeps
+# 16 bits of each operand: the representation error is 2 * 2^-17 = 1.5e-5 per
+# product, and the recurrence adds a small factor; it is kept as a labelled
+# low-accuracy option.
+TOL = {"fp16x3": 1e-5, "bf16x6": 1e-5, "bf16x3": 6e-5}
 
 
 @pytest.fixture(scope="module")
@@ -32,9 +34,9 @@ def _mus(P):
     return 0.9 * pos[0], pos[len(pos) // 6], 1.05 * pos[-1]
 
 
-@pytest.mark.parametrize("scheme", ["bf16x3", "bf16x6"])
-# (300, 70): an odd number of row blocks (a mirror CTA in the last cluster) and a 2-way K
-# split; (640, 24): 5 row blocks and a 4-way K split of 6 CTAs per split
+@pytest.mark.parametrize("scheme", ["fp16x3", "bf16x3", "bf16x6"])
+# (300, 70): an odd number of row blocks, a narrow last column tile and a 2-way K split;
+# (640, 24): 5 row blocks and a 4-way K split of 6 CTAs per split
 @pytest.mark.parametrize("n,k,maxdeg", [(128, 8, 1), (128, 8, 4), (300, 70, 8), (129, 33, 6), (640, 24, 4)])
 def test_filter_tensor_core_matches_oracle(pkg, scheme, n, k, maxdeg):
     P = bi.make_problem(n, seed=n + k)
@@ -49,7 +51,7 @@ def test_filter_tensor_core_matches_oracle(pkg, scheme, n, k, maxdeg):
     assert err < TOL[scheme], err
 
 
-@pytest.mark.parametrize("scheme", ["bf16x3", "bf16x6"])
+@pytest.mark.parametrize("scheme", ["fp16x3", "bf16x3", "bf16x6"])
 def test_solve_mixed_matches_brute_force(pkg, scheme):
     n, nev, nex = 64, 8, 6
     P = bi.make_problem(n, seed=11)
@@ -73,7 +75,27 @@ def test_solve_mixed_n512_workload(pkg):
     A, B = problem_on_device(P)
     W0, V0 = starts(n, nev + nex, 0)
     lam, V, st = pkg.solve(A, B, nev, nex, cfg["deg"], cfg["tol"], W0=to_dev(W0), V0=to_dev(V0),
-                           deg_min=cfg["deg_min"], deg_max=cfg["deg_max"], precision="bf16x3")
+                           deg_min=cfg["deg_min"], deg_max=cfg["deg_max"], precision="mixed")
     ref, _ = dense.smallest_positive(P.A, P.B, nev)
     np.testing.assert_allclose(lam.cpu().numpy(), ref, rtol=1e-10)
     assert st["max_residual"] <= cfg["tol"]
+
+
+@pytest.mark.parametrize("scheme", ["fp16x3", "bf16x6"])
+def test_filter_tensor_core_column_scales(pkg, scheme):
+    """Columns whose magnitudes span 1e-20 .. 1e20 (far outside FP16's range): every
+    operand row is scaled by a power of two, so each column keeps the 1e-5 accuracy
+    relative to its own norm."""
+    n, k = 200, 12
+    P = bi.make_problem(n, seed=7)
+    A, B = problem_on_device(P)
+    W0 = bi.start_block(n, k, 5)
+    W0 *= (10.0 ** np.linspace(-20, 20, k))[:, None]
+    degs = np.full(k, 5)
+    mu1, mune, muN = _mus(P)
+    W = to_dev(W0)
+    pkg.filter(A, B, W, degs, mu1, mune, muN, precision=scheme)
+    Y = chebyshev.chebyshev_filter(P.A, P.B, W0.T, degs, mu1, mune, muN)
+    got = W.cpu().numpy().T
+    for j in range(k):
+        assert rel_fro(got[:, j], Y[:, j]) < TOL[scheme], j

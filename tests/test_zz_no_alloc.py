@@ -36,23 +36,49 @@ def _case(n, k, seed):
     return A, B, Wt, lam
 
 
-def test_noalloc_matches_allocating_entry_point_on_two_calls(lib):
-    L = lib.lib()
+def _call(L, fn, A, B, W, lam, out, n, k, stream):
     vp = ctypes.c_void_p
+    return getattr(L, fn)(vp(A.data_ptr()), vp(B.data_ptr()), n, vp(W.data_ptr()), vp(lam.data_ptr()), k,
+                          vp(out.data_ptr()), vp(stream))
+
+
+# (4096, 64) and (1024, 256): 2n * k = 2^19 (the scratch limit) with an output grid small
+# enough that chase_bse_residuals splits K into partial sums (workspace it allocates);
+# (200, 37) and (96, 5): small cases, the second running over stale contents of the first
+CASES = [(4096, 64, 1), (1024, 256, 2), (200, 37, 3), (96, 5, 4)]
+
+
+def test_noalloc_matches_allocating_entry_point_on_two_calls(lib):
+    """Two calls in a row per case, each against chase_bse_residuals, with no device
+    allocation by the library across the no-alloc calls."""
+    L = lib.lib()
     stream = torch.cuda.current_stream().cuda_stream
-    # two calls in a row, the second smaller so it runs over stale contents of the first
-    for n, k, seed in [(200, 37, 1), (96, 5, 2)]:
+    for n, k, seed in CASES:
         A, B, W, lam = _case(n, k, seed)
         ref = torch.zeros(k, dtype=torch.float64, device=A.device)
-        out = torch.full((k,), float("nan"), dtype=torch.float64, device=A.device)
-        st = L.chase_bse_residuals(vp(A.data_ptr()), vp(B.data_ptr()), n, vp(W.data_ptr()), vp(lam.data_ptr()), k,
-                                   vp(ref.data_ptr()), vp(stream))
-        assert st == 0
-        st = L.chase_bse_residuals_noalloc(vp(A.data_ptr()), vp(B.data_ptr()), n, vp(W.data_ptr()),
-                                           vp(lam.data_ptr()), k, vp(out.data_ptr()), vp(stream))
-        assert st == 0
+        assert _call(L, "chase_bse_residuals", A, B, W, lam, ref, n, k, stream) == 0
         torch.cuda.synchronize()
-        np.testing.assert_allclose(out.cpu().numpy(), ref.cpu().numpy(), rtol=1e-12, atol=0)
+        for _ in range(2):
+            out = torch.full((k,), float("nan"), dtype=torch.float64, device=A.device)
+            before = L.chase_bse_alloc_count()
+            assert _call(L, "chase_bse_residuals_noalloc", A, B, W, lam, out, n, k, stream) == 0
+            torch.cuda.synchronize()
+            assert L.chase_bse_alloc_count() == before, (n, k)
+            np.testing.assert_allclose(out.cpu().numpy(), ref.cpu().numpy(), rtol=1e-12, atol=0)
+
+
+def test_allocating_entry_point_does_allocate_on_a_split_case(lib):
+    """The counter sees the split-K workspace of chase_bse_residuals at (4096, 64), so a
+    zero count for the no-alloc call above is a real observation."""
+    L = lib.lib()
+    stream = torch.cuda.current_stream().cuda_stream
+    n, k = 4096, 64
+    A, B, W, lam = _case(n, k, 1)
+    out = torch.zeros(k, dtype=torch.float64, device=A.device)
+    before = L.chase_bse_alloc_count()
+    assert _call(L, "chase_bse_residuals", A, B, W, lam, out, n, k, stream) == 0
+    torch.cuda.synchronize()
+    assert L.chase_bse_alloc_count() > before
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch(lib):
