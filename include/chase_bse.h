@@ -105,6 +105,8 @@ typedef struct chase_bse_stats {
   double ms_filter_mixed;  /* time of the tensor-core filter launches                 */
   int64_t filter_launches; /* GEMM launches of the filter                             */
   double max_residual;     /* largest scaled residual of the returned pairs           */
+  double lanczos_mu1, lanczos_mu_nevex, lanczos_muN;  /* the bounds of Section 4.1 as the
+                              Lanczos estimate returned them, before any update     */
 } chase_bse_stats;
 
 /* Full solve (Algorithm 3).
@@ -213,6 +215,24 @@ int chase_bse_grad(const void* V, const double* w, int64_t n, int64_t nev, void*
 int chase_bse_dgemm_sliced(const double* A, int64_t lda, const double* B, int64_t ldb,
                            int64_t M, int64_t N, int64_t K, double alpha, double* C,
                            int64_t ldc, void* stream);
+
+/* Per-vector Chebyshev degrees for the next filter (host only, no GPU work): the
+ * degree rule the solver applies after each Rayleigh-Ritz step.  The paper sets the
+ * degree of each vector from its convergence rate (Section 6; the formula it cites is
+ * not printed); this library's reading, with a = mu_nevex^2, b = muN^2,
+ * c = (a+b)/2, e = (b-a)/2 and t_i = (ritz_i^2 - c)/e:
+ *   rho_i = 1/(|t_i| + sqrt(t_i^2 - 1))   (1 when |t_i| <= 1), the predicted
+ *           damping of the residual per H^2 step, replaced by the observed rate
+ *           (res_i/prev_res_i)^(1/prev_deg_i) when that is slower (0 < res_i <
+ *           prev_res_i, prev_res_i finite);
+ *   degs_i = deg_min if res_i <= tol, deg_max if rho_i >= 1, else
+ *            clamp(ceil(ln(tol/res_i)/ln(rho_i)) + 1, deg_min, deg_max).
+ *   ritz, res, prev_res, prev_deg, degs: host arrays of k entries (prev_res may
+ *   hold +inf for "no history"); 1 <= deg_min <= deg_max; 0 < mu_nevex < muN.
+ * Returns BAD_ARG on invalid arguments. */
+int chase_bse_degrees(const double* ritz, const double* res, const double* prev_res,
+                      const int32_t* prev_deg, int64_t k, double tol, double mu_nevex,
+                      double muN, int32_t deg_min, int32_t deg_max, int32_t* degs);
 
 /* Static description of a status code. */
 const char* chase_bse_strerror(int status);

@@ -73,6 +73,9 @@ class Stats(ctypes.Structure):
         ("ms_filter_mixed", ctypes.c_double),
         ("filter_launches", ctypes.c_int64),
         ("max_residual", ctypes.c_double),
+        ("lanczos_mu1", ctypes.c_double),
+        ("lanczos_mu_nevex", ctypes.c_double),
+        ("lanczos_muN", ctypes.c_double),
     ]
 
     def as_dict(self) -> dict:
@@ -84,7 +87,7 @@ _lib: Optional[ctypes.CDLL] = None
 EXPORTS = ["chase_bse_solve", "chase_bse_filter", "chase_bse_rr", "chase_bse_residuals", "chase_bse_grad",
            "chase_bse_strerror", "chase_bse_version", "chase_bse_has_mixed", "chase_bse_launch_count",
            "chase_bse_residuals_noalloc", "chase_bse_dgemm_sliced", "chase_bse_trim_memory",
-           "chase_bse_alloc_count"]
+           "chase_bse_alloc_count", "chase_bse_degrees"]
 
 # 2n * k limit of chase_bse_residuals_noalloc (its fixed device scratch, complex128 entries)
 NOALLOC_MAX_ENTRIES = 1 << 19
@@ -108,6 +111,7 @@ def lib() -> ctypes.CDLL:
     L.chase_bse_residuals_noalloc.argtypes = [vp, vp, i64, vp, vp, i64, vp, vp]
     L.chase_bse_grad.argtypes = [vp, vp, i64, i64, vp, vp, vp]
     L.chase_bse_dgemm_sliced.argtypes = [vp, i64, vp, i64, i64, i64, i64, dbl, vp, i64, vp]
+    L.chase_bse_degrees.argtypes = [vp, vp, vp, vp, i64, dbl, dbl, dbl, i32, i32, vp]
     L.chase_bse_strerror.argtypes = [ctypes.c_int]
     L.chase_bse_strerror.restype = ctypes.c_char_p
     L.chase_bse_launch_count.restype = ctypes.c_int64
@@ -115,7 +119,7 @@ def lib() -> ctypes.CDLL:
     L.chase_bse_trim_memory.restype = None
     for name in ["chase_bse_solve", "chase_bse_filter", "chase_bse_rr", "chase_bse_residuals", "chase_bse_grad",
                  "chase_bse_version", "chase_bse_has_mixed", "chase_bse_residuals_noalloc",
-                 "chase_bse_dgemm_sliced"]:
+                 "chase_bse_dgemm_sliced", "chase_bse_degrees"]:
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -295,6 +299,23 @@ def dgemm_sliced(A: torch.Tensor, B: torch.Tensor, alpha: float = 1.0, stream=No
     _check(lib().chase_bse_dgemm_sliced(_ptr(A), K, _ptr(B), K, M, N, K, float(alpha), _ptr(C), M,
                                         ctypes.c_void_p(_stream(stream))), "chase_bse_dgemm_sliced")
     return C.T
+
+
+def degrees(ritz, res, prev_res, prev_deg, tol: float, mu_nevex: float, muN: float, deg_min: int,
+            deg_max: int):
+    """chase_bse_degrees: the solver's per-vector degree rule (host only); returns a list."""
+    import numpy as np
+    ritz = np.ascontiguousarray(ritz, dtype=np.float64)
+    k = len(ritz)
+    res = np.ascontiguousarray(res, dtype=np.float64)
+    prev_res = np.ascontiguousarray(prev_res, dtype=np.float64)
+    prev_deg = np.ascontiguousarray(prev_deg, dtype=np.int32)
+    if not (len(res) == len(prev_res) == len(prev_deg) == k):
+        raise ValueError("ritz, res, prev_res and prev_deg must have the same length")
+    out = np.zeros(k, dtype=np.int32)
+    _check(lib().chase_bse_degrees(ritz.ctypes.data, res.ctypes.data, prev_res.ctypes.data, prev_deg.ctypes.data,
+                                   k, tol, mu_nevex, muN, deg_min, deg_max, out.ctypes.data), "chase_bse_degrees")
+    return out.tolist()
 
 
 def grad(V: torch.Tensor, w: torch.Tensor, stream=None):

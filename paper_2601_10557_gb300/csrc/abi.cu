@@ -16,6 +16,19 @@ using cb::cplx;
     return CHASE_BSE_CUDA_ERROR;       \
   }
 
+static int degrees_host(const double* ritz, const double* res, const double* prev_res, const int32_t* prev_deg,
+                        int64_t k, double tol, double mu_nevex, double muN, int32_t deg_min, int32_t deg_max,
+                        int32_t* degs) {
+  std::vector<double> r(ritz, ritz + k);
+  std::vector<double> q(res, res + k);
+  std::vector<double> p(prev_res, prev_res + k);
+  std::vector<int> pd(prev_deg, prev_deg + k);
+  std::vector<int> d;
+  cb::degrees_update(r, q, p, pd, tol, mu_nevex, muN, deg_min, deg_max, d);
+  for (int64_t i = 0; i < k; ++i) degs[i] = d[i];
+  return CHASE_BSE_OK;
+}
+
 extern "C" {
 
 int chase_bse_version(void) { return 100; }
@@ -84,6 +97,15 @@ int chase_bse_residuals(const void* A, const void* B, int64_t n, const void* W, 
 int chase_bse_grad(const void* V, const double* w, int64_t n, int64_t nev, void* gA, void* gB, void* stream) {
   if (!V || !w || !gA || !gB || n < 1 || nev < 1) return CHASE_BSE_BAD_ARG;
   CB_GUARD(return cb::gradient((const cplx*)V, w, n, nev, (cplx*)gA, (cplx*)gB, (cudaStream_t)stream);)
+}
+
+int chase_bse_degrees(const double* ritz, const double* res, const double* prev_res, const int32_t* prev_deg,
+                      int64_t k, double tol, double mu_nevex, double muN, int32_t deg_min, int32_t deg_max,
+                      int32_t* degs) {
+  if (k < 0 || (k > 0 && (!ritz || !res || !prev_res || !prev_deg || !degs)) || !(tol > 0) || deg_min < 1 ||
+      deg_max < deg_min || !(mu_nevex > 0) || !(muN > mu_nevex))
+    return CHASE_BSE_BAD_ARG;
+  CB_GUARD(return degrees_host(ritz, res, prev_res, prev_deg, k, tol, mu_nevex, muN, deg_min, deg_max, degs);)
 }
 
 int chase_bse_dgemm_sliced(const double* A, int64_t lda, const double* B, int64_t ldb, int64_t M, int64_t N,

@@ -767,6 +767,8 @@ struct PhaseClock {
   }
 };
 
+}  // namespace
+
 // Per-vector degree from the convergence rate: predicted rate per H^2 step
 // rho = 1/(|t| + sqrt(t^2 - 1)), t = (lambda^2 - c)/e, replaced by the observed
 // rate (r/r_prev)^(1/deg_prev) when that is slower; deg = ceil(ln(tol/r)/ln rho) + 1.
@@ -789,7 +791,6 @@ void degrees_update(const std::vector<double>& ritz, const std::vector<double>& 
     degs[i] = std::min(std::max(d, dmin), dmax);
   }
 }
-}  // namespace
 
 int solve(const cplx* A, const cplx* B, int64_t n, int64_t nev, int64_t nex, int deg, double tol,
           const chase_bse_opts* opts_in, double* evals, cplx* evecs, chase_bse_stats* stats) {
@@ -869,6 +870,9 @@ int solve(const cplx* A, const cplx* B, int64_t n, int64_t nev, int64_t nex, int
   st.ms_lanczos = clk.stop();
   double mu1 = mu[0], mu_ne = mu[1], muN = mu[2];
   const double rhat = mu[3];
+  st.lanczos_mu1 = mu[0];
+  st.lanczos_mu_nevex = mu[1];
+  st.lanczos_muN = mu[2];
   // mu_1 is the normalisation point p(mu_1^2) = 1 and must stay below mu_nevex
   mu1 = std::min(mu1, 0.5 * mu_ne);
 

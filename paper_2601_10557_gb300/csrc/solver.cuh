@@ -46,6 +46,11 @@ int residuals(const cplx* A, const cplx* B, int64_t n, const cplx* W, const doub
 int solve(const cplx* A, const cplx* B, int64_t n, int64_t nev, int64_t nex, int deg, double tol,
           const chase_bse_opts* opts, double* evals, cplx* evecs, chase_bse_stats* stats);
 
+// The per-vector degree rule (see chase_bse_degrees): host only.
+void degrees_update(const std::vector<double>& ritz, const std::vector<double>& res,
+                    const std::vector<double>& prev_res, const std::vector<int>& prev_deg, double tol, double mu_ne,
+                    double muN, int dmin, int dmax, std::vector<int>& degs);
+
 int gradient(const cplx* V, const double* w, int64_t n, int64_t nev, cplx* gA, cplx* gB, cudaStream_t s);
 
 // Mixed-precision (tcgen05) filter on a column group whose columns are sorted

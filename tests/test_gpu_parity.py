@@ -91,15 +91,24 @@ def test_rayleigh_ritz_matches_oracle(pkg, n, h):
     assert np.all(ov[gap > 1e-6] > 1 - 1e-9)
 
 
-def test_lanczos_bounds_match_oracle(pkg):
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_lanczos_bounds_match_oracle(pkg, precision):
+    """mu_1, mu_nevex (the DOS quantile), mu_N and rho_hat of the library's Lanczos run
+    (FP64 pipe, or the FP64-accurate tensor-core products in mixed mode) against the
+    oracle's on the same start vectors."""
+    if precision == "mixed" and not pkg.has_mixed():
+        pytest.fail("tensor-core path not available on this device")
     n, nev, nex = 128, 10, 6
     P = bi.make_problem(n, seed=6)
     A, B = problem_on_device(P)
     W0, V0 = starts(n, nev + nex, 6)
     _, _, st = pkg.solve(A, B, nev, nex, 10, 1e-10, W0=to_dev(W0), V0=to_dev(V0), deg_min=4, deg_max=24,
-                         maxiter=1, allow_partial=True)
+                         maxiter=1, allow_partial=True, precision=precision)
     mu_ref = lanczos.spectral_bounds(P.A, P.B, V0, 26, nev + nex)
     rhat = osolver.rho_hat(P.A, P.B, V0, 26)
+    np.testing.assert_allclose(st["lanczos_mu1"], mu_ref[0], rtol=1e-8)
+    np.testing.assert_allclose(st["lanczos_mu_nevex"], mu_ref[1], rtol=1e-8)
+    np.testing.assert_allclose(st["lanczos_muN"], mu_ref[2], rtol=1e-8)
     # after one iteration mu_nevex/mu1 are updated from Ritz values; mu_N and rho_hat are the Lanczos ones
     np.testing.assert_allclose(st["muN"], mu_ref[2], rtol=1e-8)
     np.testing.assert_allclose(st["rho_hat"], rhat, rtol=1e-8)
