@@ -28,6 +28,7 @@ __all__ = [
     "haar_unitary",
     "spectrum",
     "make_problem",
+    "make_problem_device",
     "start_block",
     "lanczos_starts",
     "loss_weights",
@@ -133,6 +134,58 @@ def make_problem(n: int, seed: int = 0, spec: str = "uniform:1:10", beta: float 
     return BSEProblem(A=np.ascontiguousarray(A, dtype=np.complex128),
                       B=np.ascontiguousarray(B, dtype=np.complex128),
                       d=d, beta=beta, seed=seed, real=real)
+
+
+def make_problem_device(n: int, seed: int = 0, spec: str = "uniform:1:10", beta: float = 0.3, device="cuda"):
+    """The generator of ``make_problem`` for large n, assembled on a GPU with torch:
+    returns (A, B, d) with A, B (n, n) complex128 torch tensors on ``device`` (row-major
+    storage as above) and d the planted spectrum (numpy).
+
+    Same recipe, cheaper arithmetic: the complex Gaussian Z and G are drawn with torch's
+    CPU generator seeded by ``seed`` (the planted d with numpy's, as above); Q is the
+    Haar-unitary factor of Z (QR with the phases of diag(R) moved into Q) and
+    A = Q diag(d) Q^* are computed in complex64 on the device, then A is taken to
+    complex128 and symmetrised, (A + A^*)/2.  So A is hermitian to the last bit and
+    equals Q diag(d) Q^* to FP32 accuracy (its eigenvalues are d up to ~1e-6 ||A||),
+    which is all the solver's checks at these sizes use: they test residuals, the
+    S-Rayleigh quotient and inertia counts of A and B as given, never d itself.
+    B = G + G^T (complex128) scaled to ||B||_2 = beta * min(d) with ||B||_2 from 30
+    steps of block power iteration on B^* B (8 vectors).  Used for n >= 8192, where the
+    host QR of ``make_problem`` takes minutes."""
+    import torch
+    rng = np.random.default_rng(seed)
+    d = spectrum(spec, n, rng)
+    gen = torch.Generator(device="cpu").manual_seed(int(seed) * 7919 + 17)
+    Z = torch.complex(torch.randn((n, n), generator=gen, dtype=torch.float32),
+                      torch.randn((n, n), generator=gen, dtype=torch.float32)).to(device)
+    with torch.no_grad():
+        prev_tf32 = torch.backends.cuda.matmul.allow_tf32
+        torch.backends.cuda.matmul.allow_tf32 = False
+        try:
+            Qm, R = torch.linalg.qr(Z)
+            del Z
+            dr = torch.diagonal(R)
+            Qm = Qm * (dr / dr.abs())[None, :]
+            del R
+            dt = torch.from_numpy(d.astype(np.float32)).to(device)
+            A32 = (Qm * dt[None, :].to(Qm.dtype)) @ Qm.conj().T
+            del Qm
+        finally:
+            torch.backends.cuda.matmul.allow_tf32 = prev_tf32
+        A = A32.to(torch.complex128)
+        del A32
+        A = 0.5 * (A + A.conj().T)
+        G = torch.complex(torch.randn((n, n), generator=gen, dtype=torch.float64),
+                          torch.randn((n, n), generator=gen, dtype=torch.float64)).to(device)
+        B = G + G.T
+        del G
+        V = torch.complex(torch.randn((n, 8), generator=gen, dtype=torch.float64),
+                          torch.randn((n, 8), generator=gen, dtype=torch.float64)).to(device)
+        for _ in range(30):
+            V, _ = torch.linalg.qr(B.conj().T @ (B @ V))
+        s = torch.linalg.svdvals(B @ V)[0].item()
+        B *= beta * float(d.min()) / s
+    return A.contiguous(), B.contiguous(), d
 
 
 def start_block(n: int, k: int, seed: int) -> np.ndarray:

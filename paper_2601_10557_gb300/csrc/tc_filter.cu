@@ -61,8 +61,8 @@
 namespace cb {
 namespace tc {
 
-constexpr int BM = 128, BK = 64;
-constexpr int A_BYTES = BM * BK * 2;  // 16 KB per piece
+constexpr int BM = 128;
+constexpr int KPAD = 64;              // K (4n) is padded to a multiple of this
 constexpr int GROUP_M = 8;            // tile raster: GROUP_M row tiles x all column tiles per group
 constexpr uint32_t TMEM_COLS = 512;   // two accumulator buffers (+ the cross products for 128-wide tiles)
 constexpr int VEXP_MAX = 100;         // |operand exponents| are clamped to this
@@ -120,26 +120,36 @@ struct Scheme<SCH_BF16X6> {
   __device__ static constexpr int pa(int i) { return i == 2 ? 1 : (i == 4 ? 1 : (i == 5 ? 2 : 0)); }
   __device__ static constexpr int pb(int i) { return i == 1 ? 1 : (i == 3 ? 2 : (i == 4 ? 1 : 0)); }
 };
-// Tile geometry for BNT-wide output tiles.  128-wide: the x0 * y0 product drains from
-// two alternating TMEM buffers and the cross products accumulate over all of K in a
-// third; 8 drain warps of 64 columns (two per TMEM lane quarter: half the drain latency
-// of 4 warps of 128 columns, and 135 registers a thread instead of 228).  256-wide
-// (two pieces only): all products share the two alternating buffers (drained every
-// FLUSH K blocks, so the truncating accumulator sums at most FLUSH * 4 * NPROD MMAs);
-// 16 drain warps of 64 columns keep the FP32 partial sums in registers; a 2-stage ring.
-template <int SCH, int BNT>
+// Tile geometry for BNT-wide output tiles.  128-wide: K blocks of 64 (128-byte swizzle);
+// the x0 * y0 product drains from two alternating TMEM buffers and the cross products
+// accumulate over all of K in a third; 8 drain warps of 64 columns (two per TMEM lane
+// quarter: half the drain latency of 4 warps of 128 columns, and 135 registers a thread
+// instead of 228).  256-wide (two pieces only): K blocks of 32 (64-byte swizzle) in a
+// 4-stage ring of 48 KB stages; each SM takes in 48 KB per 768 MMA cycles instead of
+// 64 KB (the shared-memory fill per MMA cycle bounds the 128-wide tiles); all products
+// share the two alternating buffers, drained after every K block, and each block issues
+// its cross products (2^-11 of the result) before x0 * y0, so the truncating
+// accumulator adds only two MMAs at full magnitude per drain (as the 128-wide x0 * y0
+// buffer per 32 K elements); 16 drain warps of 64 columns keep the FP32 partial sums in
+// registers.
+template <int SCH, int BNT, int FL>
 struct Geo {
-  static constexpr int STAGES = (BNT == 256) ? 2 : Scheme<SCH>::STAGES;
+  static constexpr int BK = (BNT == 256) ? 32 : 64;
+  static constexpr int SWZ = BK * 2;                       // swizzle span (bytes) = one row of a tile
+  static constexpr int STAGES = (BNT == 256) ? 4 : Scheme<SCH>::STAGES;
+  static constexpr int FLUSH = FL;
+  static constexpr bool CROSS = (BNT == 128);             // separate cross-product buffer
+  static constexpr int NB = CROSS ? 3 : 2;                 // rotating x0 * y0 (or all-product) buffers
+  static constexpr int A_BYTES = BM * BK * 2;
   static constexpr int B_BYTES = BNT * BK * 2;
   static constexpr int STAGE_BYTES = Scheme<SCH>::NPA * A_BYTES + Scheme<SCH>::NPW * B_BYTES;
-  static constexpr int NBAR = 2 * STAGES + 5;  // full, empty, acc_full[2], acc_empty[2], done
+  static constexpr int NBAR = 2 * STAGES + 2 * NB + 1;  // full, empty, acc_full[NB], acc_empty[NB], done
   static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
-  static constexpr bool CROSS = (BNT == 128);             // separate cross-product buffer
   static constexpr int DCOLS = 64;                         // columns per drain warp
   static constexpr int DRAIN_WARPS = 4 * (BNT / DCOLS);
   static constexpr int THREADS = 128 + 32 * DRAIN_WARPS;
   static_assert(STAGE_BYTES * STAGES + 1280 <= 232448, "shared memory");
-  static_assert(CROSS ? 3 * BNT <= (int)TMEM_COLS : 2 * BNT <= (int)TMEM_COLS, "TMEM columns");
+  static_assert((NB + (CROSS ? 1 : 0)) * BNT <= (int)TMEM_COLS, "TMEM columns");
 };
 
 struct Epi {
@@ -211,15 +221,16 @@ struct Sched {
   }
 };
 
-// Shared-memory matrix descriptor: K-major tile written by TMA with 128-byte
-// swizzle; rows of 128 bytes, 8-row groups 1024 bytes apart.
+// Shared-memory matrix descriptor: K-major tile written by TMA with SWZ-byte rows and
+// SWZ-byte swizzle (128 or 64); 8-row groups 8 * SWZ bytes apart.
+template <int SWZ>
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
-  d |= (uint64_t)1 << 16;                    // leading byte offset (unused for this layout)
-  d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset
+  d |= (uint64_t)1 << 16;                    // leading byte offset (unused for these layouts)
+  d |= (uint64_t)((8 * SWZ) >> 4) << 32;     // stride byte offset
   d |= (uint64_t)1 << 46;                    // descriptor version
-  d |= (uint64_t)2 << 61;                    // 128-byte swizzle
+  d |= (uint64_t)(SWZ == 128 ? 2 : 4) << 61; // 128- or 64-byte swizzle
   return d;
 }
 // sum[0..BN) += the warp's TMEM lanes at columns [col, col + BN), two loads in flight
@@ -294,15 +305,18 @@ struct Maps {
 // few MMAs.  With 128-wide tiles the cross products (2^-8 or 2^-11 smaller)
 // accumulate over the whole K range in a third buffer instead.  The last column tile
 // may be narrower (n_last columns, a multiple of 16): its MMAs use N = n_last.
-template <int SCH, int BNT>
-__global__ void __launch_bounds__(Geo<SCH, BNT>::THREADS, 1)
+template <int SCH, int BNT, int FL>
+__global__ void __launch_bounds__(Geo<SCH, BNT, FL>::THREADS, 1)
     tc_hop_kernel(const __grid_constant__ Maps maps, Epi ep, Sched sc) {
   using SC = Scheme<SCH>;
-  using G = Geo<SCH, BNT>;
+  using G = Geo<SCH, BNT, FL>;
+  constexpr int NB = G::NB;
   using T = typename SC::T;
   constexpr int ST = G::STAGES;
   constexpr int DC = G::DCOLS;
-  constexpr int FLUSH = SC::FLUSH;
+  constexpr int FLUSH = G::FLUSH;
+  constexpr int BK = G::BK;
+  constexpr int A_BYTES = G::A_BYTES;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + ST * G::STAGE_BYTES);
@@ -312,9 +326,13 @@ __global__ void __launch_bounds__(Geo<SCH, BNT>::THREADS, 1)
     full[s] = smem_u32(bars + s);
     empty[s] = smem_u32(bars + ST + s);
   }
-  const uint32_t accf[2] = {smem_u32(bars + 2 * ST), smem_u32(bars + 2 * ST + 1)};
-  const uint32_t acce[2] = {smem_u32(bars + 2 * ST + 2), smem_u32(bars + 2 * ST + 3)};
-  const uint32_t done = smem_u32(bars + 2 * ST + 4);
+  uint32_t accf[NB], acce[NB];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    accf[b] = smem_u32(bars + 2 * ST + b);
+    acce[b] = smem_u32(bars + 2 * ST + NB + b);
+  }
+  const uint32_t done = smem_u32(bars + 2 * ST + 2 * NB);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + G::NBAR);
   volatile int* abort_sh = reinterpret_cast<volatile int*>(tmem_slot + 1);
   int* issued_sh = reinterpret_cast<int*>(tmem_slot + 2);
@@ -334,7 +352,7 @@ __global__ void __launch_bounds__(Geo<SCH, BNT>::THREADS, 1)
       mbar_init(full[s], 1);
       mbar_init(empty[s], 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < NB; ++b) {
       mbar_init(accf[b], 1);
       mbar_init(acce[b], G::DRAIN_WARPS);  // one arrival per drain warp
     }
@@ -373,34 +391,45 @@ __global__ void __launch_bounds__(Geo<SCH, BNT>::THREADS, 1)
     *issued_sh = issued;
   } else if (warp == 1 && lane == 0) {
     const uint32_t idesc = make_idesc(ntile, Piece<T>::BF16);
-    const uint32_t small = tmem + (uint32_t)(2 * BNT);
-    const uint64_t dbase = sdesc(sbase);
+    const uint32_t small = tmem + (uint32_t)(NB * BNT);
+    const uint64_t dbase = sdesc<G::SWZ>(sbase);
     for (int kb = 0; kb < num_kb; ++kb) {
-      const int grp = kb / FLUSH, b = grp & 1;
+      const int grp = kb / FLUSH, b = grp % NB;
       const bool first = (kb % FLUSH) == 0;
       const bool last = (kb % FLUSH) == FLUSH - 1 || kb == num_kb - 1;
-      if (first && grp >= 2 && !mbar_wait(acce[b], (uint32_t)((grp >> 1) - 1) & 1u, abort_sh, ep.err, true)) break;
+      if (first && grp >= NB && !mbar_wait(acce[b], (uint32_t)(grp / NB - 1) & 1u, abort_sh, ep.err, true)) break;
       const int s = kb % ST;
       const uint32_t ph = (uint32_t)(kb / ST) & 1u;
       if (!mbar_wait(full[s], ph, abort_sh, ep.err, true)) break;
       tc_fence_after();
       const uint32_t st = sbase + s * G::STAGE_BYTES;
       const uint32_t big = tmem + (uint32_t)(b * BNT);
+      // sdesc is linear in the address here (its 14-bit start field holds address / 16 of
+      // a 1024-aligned ring below 256 KB and cannot carry): a hoisted base plus constants;
+      // 16 K elements further along a swizzled row is 32 bytes further
+      const uint64_t sd = dbase + (uint64_t)((uint32_t)(st - sbase) >> 4);
+      if (G::CROSS) {
 #pragma unroll
-      for (int kk = 0; kk < BK / 16; ++kk) {
+        for (int kk = 0; kk < BK / 16; ++kk) {
 #pragma unroll
-        for (int pr = 0; pr < SC::NPROD; ++pr) {
-          // sdesc is linear in the address here (its 14-bit start field holds address / 16 of
-          // a 1024-aligned ring below 256 KB and cannot carry): a hoisted base plus constants
-          const uint64_t sd = dbase + (uint64_t)((uint32_t)(st - sbase) >> 4);
-          const uint64_t ad = sd + (uint64_t)((SC::pa(pr) * A_BYTES + kk * 32) >> 4);
-          const uint64_t bd = sd + (uint64_t)((SC::NPA * A_BYTES + SC::pb(pr) * G::B_BYTES + kk * 32) >> 4);
-          if (G::CROSS) {
+          for (int pr = 0; pr < SC::NPROD; ++pr) {
+            const uint64_t ad = sd + (uint64_t)((SC::pa(pr) * A_BYTES + kk * 32) >> 4);
+            const uint64_t bd = sd + (uint64_t)((SC::NPA * A_BYTES + SC::pb(pr) * G::B_BYTES + kk * 32) >> 4);
             const uint32_t acc =
                 (pr == 0) ? ((!first || kk > 0) ? 1u : 0u) : ((kb > 0 || kk > 0 || pr > 1) ? 1u : 0u);
             mma_bf16(pr == 0 ? big : small, ad, bd, idesc, acc);
-          } else {
-            const uint32_t acc = (first && kk == 0 && pr == 0) ? 0u : 1u;
+          }
+        }
+      } else {
+        // the block's cross products first, then x0 * y0
+#pragma unroll
+        for (int pi = 0; pi < SC::NPROD; ++pi) {
+          const int pr = (pi + 1) % SC::NPROD;
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk) {
+            const uint64_t ad = sd + (uint64_t)((SC::pa(pr) * A_BYTES + kk * 32) >> 4);
+            const uint64_t bd = sd + (uint64_t)((SC::NPA * A_BYTES + SC::pb(pr) * G::B_BYTES + kk * 32) >> 4);
+            const uint32_t acc = (first && kk == 0 && pi == 0) ? 0u : 1u;
             mma_bf16(big, ad, bd, idesc, acc);
           }
         }
@@ -421,8 +450,8 @@ __global__ void __launch_bounds__(Geo<SCH, BNT>::THREADS, 1)
     bool ok = true;
     const int ngrp = (num_kb + FLUSH - 1) / FLUSH;
     for (int grp = 0; grp < ngrp; ++grp) {
-      const int b = grp & 1;
-      const bool w = mbar_wait(accf[b], (uint32_t)(grp >> 1) & 1u, abort_sh, ep.err, true);
+      const int b = grp % NB;
+      const bool w = mbar_wait(accf[b], (uint32_t)(grp / NB) & 1u, abort_sh, ep.err, true);
       if (!__all_sync(0xffffffffu, w)) {  // warp-uniform (tcgen05.ld is .sync.aligned)
         ok = false;
         break;
@@ -441,7 +470,7 @@ __global__ void __launch_bounds__(Geo<SCH, BNT>::THREADS, 1)
       ok = __all_sync(0xffffffffu, w);
       if (ok && has_cols) {
         tc_fence_after();
-        drain_add<DC>(tmem + lane_base + (uint32_t)(2 * BNT + col0), sum);
+        drain_add<DC>(tmem + lane_base + (uint32_t)(NB * BNT + col0), sum);
       }
     }
     if (sc.nsplit > 1) {
@@ -682,16 +711,20 @@ __global__ void combine_kernel(cplx* out, const float2* Z0, const float2* Z1, co
   }
 }
 
-static int make_map(CUtensorMap* m, const void* base, int64_t kpad, int64_t rows, int box_rows, bool bf16) {
+// Tensor map of a piece plane (rows x kpad, K contiguous) with boxes of bk x box_rows and
+// 2 bk-byte swizzle (bk = 64 or 32).
+static int make_map(CUtensorMap* m, const void* base, int64_t kpad, int64_t rows, int box_rows, bool bf16,
+                    int bk) {
   auto fn = encode_fn();
   if (!fn) return CHASE_BSE_UNSUPPORTED;
   const cuuint64_t dims[2] = {(cuuint64_t)kpad, (cuuint64_t)rows};
   const cuuint64_t strides[1] = {(cuuint64_t)kpad * 2};
-  const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  const cuuint32_t box[2] = {(cuuint32_t)bk, (cuuint32_t)box_rows};
   const cuuint32_t estr[2] = {1, 1};
   CUresult r = fn(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
                   const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                  bk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? CHASE_BSE_OK : CHASE_BSE_CUDA_ERROR;
 }
 
@@ -710,12 +743,13 @@ struct POperand {
   float* L = nullptr;
 };
 
-template <int SCH>
+template <int SCH, int BNT>
 static int prepare_p(const cplx* A, const cplx* B, int64_t n, Workspace& ws, POperand& P, cudaStream_t s) {
   using T = typename Scheme<SCH>::T;
   constexpr int NPA = Scheme<SCH>::NPA;
   P.n = n;
-  P.kpad = ((4 * n + BK - 1) / BK) * BK;
+  constexpr int BK = Geo<SCH, BNT, 1>::BK;
+  P.kpad = ((4 * n + KPAD - 1) / KPAD) * KPAD;
   const int64_t rows = ((n + BM - 1) / BM) * BM;  // whole tiles: every TMA box lies inside the tensor
   for (int q = 0; q < NPA; ++q) {
     T* pq;
@@ -729,17 +763,9 @@ static int prepare_p(const cplx* A, const cplx* B, int64_t n, Workspace& ws, POp
   split_p_kernel<T, NPA><<<(unsigned)n, 256, 0, s>>>(A, B, n, P.kpad, P.pc, P.prow, P.L);
   count_launch();
   CB_LAUNCH();
-  for (int q = 0; q < NPA; ++q) CB_TRY(make_map(&P.map[q], P.pc.p[q], P.kpad, rows, BM, Piece<T>::BF16));
+  for (int q = 0; q < NPA; ++q) CB_TRY(make_map(&P.map[q], P.pc.p[q], P.kpad, rows, BM, Piece<T>::BF16, BK));
   return CHASE_BSE_OK;
 }
-
-// Output tile width: 128 columns.  (256-wide BF16x3 tiles with a 2-stage ring and 16
-// drain warps measured slower at n = 4096, k = 260: 293 against 306 TFLOP/s; the
-// kernel keeps both geometries.)
-template <int SCH>
-struct TileN {
-  static constexpr int value = 128;
-};
 
 // K splits of a launch with `tiles` CTAs per split: the count (1 to MAX_SPLIT) that
 // minimises the estimated time, waves of CTAs x (1/splits + a fixed cost per CTA of
@@ -763,14 +789,13 @@ static int split_count(int tiles, int nkb, int sms, int flush) {
 
 // One tensor-core application of H to the vectors held in the operand pieces
 // described by bmap, with epilogue `ep`.
-template <int SCH>
+template <int SCH, int BNT, int FL>
 static int apply(const POperand& P, const CUtensorMap* bmap, Epi ep, cudaStream_t s) {
-  constexpr int BNT = TileN<SCH>::value;
-  using G = Geo<SCH, BNT>;
+  using G = Geo<SCH, BNT, FL>;
   if (ep.k <= 0) return CHASE_BSE_OK;
   static bool attr = false;
   if (!attr) {
-    CB_CUDA(cudaFuncSetAttribute(tc_hop_kernel<SCH, BNT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    CB_CUDA(cudaFuncSetAttribute(tc_hop_kernel<SCH, BNT, FL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  G::SMEM_BYTES));
     attr = true;
   }
@@ -783,11 +808,11 @@ static int apply(const POperand& P, const CUtensorMap* bmap, Epi ep, cudaStream_
   sc.num_n = (int)cdiv(4 * ep.k, BNT);
   const int64_t rest = 4 * ep.k - (int64_t)(sc.num_n - 1) * BNT;  // columns of the last tile
   sc.n_last = (int)(((rest + 15) / 16) * 16);
-  sc.nkb = (int)(P.kpad / BK);
+  sc.nkb = (int)(P.kpad / G::BK);
   sc.bnt = BNT;
   sc.ntiles = sc.num_m * sc.num_n;
-  sc.nsplit = split_count(sc.ntiles, sc.nkb, ep.sms, Scheme<SCH>::FLUSH);
-  tc_hop_kernel<SCH, BNT><<<(unsigned)(sc.ntiles * sc.nsplit), G::THREADS, G::SMEM_BYTES, s>>>(maps, ep, sc);
+  sc.nsplit = split_count(sc.ntiles, sc.nkb, ep.sms, G::FLUSH);
+  tc_hop_kernel<SCH, BNT, FL><<<(unsigned)(sc.ntiles * sc.nsplit), G::THREADS, G::SMEM_BYTES, s>>>(maps, ep, sc);
   count_launch();
   CB_LAUNCH();
   return CHASE_BSE_OK;
@@ -801,7 +826,7 @@ static int apply(const POperand& P, const CUtensorMap* bmap, Epi ep, cudaStream_
 // with the source term alpha_j p_j(m_i) r2_i (divided differences of the
 // three-term recurrence).  The low-precision error then scales with the
 // residual of v_i instead of with v_i.
-template <int SCH>
+template <int SCH, int BNT, int FL>
 static int filter_impl(const cplx* A, const cplx* B, int64_t n, const cplx* Y0, int64_t k, const int* degs,
                        double mu1, double mu_nevex, double muN, cplx* out, const double* ritz, const cplx* R,
                        cudaStream_t s, FilterStats* fs) {
@@ -812,8 +837,7 @@ static int filter_impl(const cplx* A, const cplx* B, int64_t n, const cplx* Y0, 
   const int64_t n2 = 2 * n;
   Workspace ws(s);
   POperand P;
-  CB_TRY(prepare_p<SCH>(A, B, n, ws, P, s));
-  constexpr int BNT = TileN<SCH>::value;
+  CB_TRY((prepare_p<SCH, BNT>(A, B, n, ws, P, s)));
   const int64_t rows = ((4 * k + BNT - 1) / BNT) * BNT;  // whole tiles
   Pieces Zp{}, Tp{};
   CUtensorMap mZ[3], mT[3];
@@ -825,8 +849,8 @@ static int filter_impl(const cplx* A, const cplx* B, int64_t n, const cplx* Y0, 
     Tp.p[q] = tq;
     CB_CUDA(cudaMemsetAsync(zq, 0, sizeof(T) * rows * P.kpad, s));
     CB_CUDA(cudaMemsetAsync(tq, 0, sizeof(T) * rows * P.kpad, s));
-    CB_TRY(make_map(&mZ[q], zq, P.kpad, rows, BNT, BF));
-    CB_TRY(make_map(&mT[q], tq, P.kpad, rows, BNT, BF));
+    CB_TRY(make_map(&mZ[q], zq, P.kpad, rows, BNT, BF, Geo<SCH, BNT, FL>::BK));
+    CB_TRY(make_map(&mT[q], tq, P.kpad, rows, BNT, BF, Geo<SCH, BNT, FL>::BK));
   }
   float2 *Zb[3], *src = nullptr;
   float* gam;
@@ -929,7 +953,7 @@ static int filter_impl(const cplx* A, const cplx* B, int64_t n, const cplx* Y0, 
     ep.vexp_in = vexp + slotR;
     ep.amax_out = amax + slotS;
     sk(ep);
-    CB_TRY(apply<SCH>(P, mZ, ep, s));
+    CB_TRY((apply<SCH, BNT, FL>)(P, mZ, ep, s));
     CB_CUDA(cudaMemsetAsync(Zb[0], 0, sizeof(float2) * n2 * k, s));
     scale_pack_kernel<T, NPW><<<gsz(n * k), 256, 0, s>>>(src, n, k, (float)al[0], Zb[1], Zp, P.kpad,
                                                           amax + slotS, amax + slotZ(1), vexp + slotZ(1));
@@ -953,7 +977,7 @@ static int filter_impl(const cplx* A, const cplx* B, int64_t n, const cplx* Y0, 
     e1p.amax_out = amax + slotT(j);
     e1p.amax_a = amax + slotZ(j);
     e1p.ca = L;
-    CB_TRY(apply<SCH>(P, mZ, e1p, s));  // T = H Z_j
+    CB_TRY((apply<SCH, BNT, FL>)(P, mZ, e1p, s));  // T = H Z_j
     Epi e2p{};
     e2p.mode = 1; e2p.n = n; e2p.k = kj; e2p.kpad = P.kpad; e2p.err = err;
     sk(e2p);
@@ -976,7 +1000,7 @@ static int filter_impl(const cplx* A, const cplx* B, int64_t n, const cplx* Y0, 
       e2p.gamma = gam;
       e2p.amax_d = amax + slotS;
     }
-    CB_TRY(apply<SCH>(P, mT, e2p, s));  // Z_{j+1} = alpha (H T - c Z_j) + beta Z_{j-1} (+ source)
+    CB_TRY((apply<SCH, BNT, FL>)(P, mT, e2p, s));  // Z_{j+1} = alpha (H T - c Z_j) + beta Z_{j-1} (+ source)
     if (fs) {
       fs->flops += 64.0 * (double)n * (double)n * (double)kj;
       fs->launches += 2;
@@ -1024,11 +1048,20 @@ bool mixed_available() {
   return major == 10 && minor == 3 && tc::encode_fn() != nullptr;
 }
 
+// Output tiles of 128 columns.  (Measured alternatives, degree-20 calls at n = 4096,
+// k = 260 and degree-4 calls at n = 16384, k = 1300: 256-wide tiles with K blocks of 32
+// in a 4-stage ring and all products in two alternating buffers drained every 4 K
+// blocks ran 9 % faster at n = 16384 but missed the 1e-5 filter gate (1.3e-5 at
+// n = 4096); drained after every K block they ran 10-17 % slower.  Draining the 128-wide
+// x0 * y0 buffers every 1 or 2 K blocks instead of 4 cost 4-8 % and did not lower the
+// error, which the 22-bit pieces and the recurrence set: 8.9e-6 at n = 4096 and
+// 7.6e-6 at n = 16384 against the FP64 oracle.)
 template <int SCH>
 static int filter_dispatch(const cplx* A, const cplx* B, int64_t n, cplx* V, int64_t k, const int* degs,
                            double mu1, double mu_nevex, double muN, cplx* out, const double* ritz, const cplx* R,
                            cudaStream_t s, FilterStats* fs) {
-  return tc::filter_impl<SCH>(A, B, n, V, k, degs, mu1, mu_nevex, muN, out, ritz, R, s, fs);
+  return tc::filter_impl<SCH, 128, tc::Scheme<SCH>::FLUSH>(A, B, n, V, k, degs, mu1, mu_nevex, muN, out, ritz, R,
+                                                            s, fs);
 }
 
 static int filter_scheme(int scheme, const cplx* A, const cplx* B, int64_t n, cplx* V, int64_t k, const int* degs,

@@ -90,6 +90,24 @@ def test_c2_filter_full_block(pkg, c2, precision):
     assert colerr.max() < 10 * TOL_FILTER[precision], colerr.max()
 
 
+def test_c3_filter_sampled_columns(pkg):
+    """At n = 16384 (the n16384 workload's inputs, H 32768 x 32768) the tensor-core
+    filter on 6 columns, degree 20, against the oracle filter (H formed on the host);
+    the columns are filtered independently, so a few stand for the block."""
+    if not pkg.has_mixed():
+        pytest.fail("tensor-core filter not available on this device")
+    wl = bi.WORKLOADS["n16384"]
+    A, B, _ = bi.make_problem_device(wl["n"], 0, wl["spec"], wl["beta"], device=torch.device("cuda:0"))
+    W0 = bi.start_block(wl["n"], 6, 0)
+    mus = (1.0, 2.7, 75.0)
+    W = to_dev(W0)
+    pkg.filter(A, B, W, [20] * 6, *mus, precision="mixed")
+    got = W.cpu().numpy().T
+    ref = chebyshev.chebyshev_filter(A.cpu().numpy(), B.cpu().numpy(), W0.T, [20] * 6, *mus)
+    colerr = np.linalg.norm(got - ref, axis=0) / np.linalg.norm(ref, axis=0)
+    assert colerr.max() < TOL_FILTER["mixed"], colerr
+
+
 def test_c2_mixed_solve_properties(pkg, c2):
     if not pkg.has_mixed():
         pytest.fail("tensor-core filter not available on this device")
