@@ -199,6 +199,24 @@ int chase_bse_residuals_noalloc(const void* A, const void* B, int64_t n, const v
 int chase_bse_grad(const void* V, const double* w, int64_t n, int64_t nev, void* gA,
                    void* gB, void* stream);
 
+/* Dense hermitian eigensolver of the Rayleigh-Ritz step (Algorithm 2, the HEEVD call
+ * G y = theta y), as the solver runs it: G V = V diag(theta).
+ *   G       device, k x k complex128 column-major, hermitian (not modified)
+ *   theta   device, k doubles: the eigenvalues, in the order of V's columns (unsorted)
+ *   V       device, k x k complex128: unit eigenvectors as columns
+ *   k       even, >= 2
+ *   method  0: FP64 Jacobi with scalar rotations (one round of k/2 disjoint rotations
+ *              per grid barrier); 1: mixed precision as in a mixed solve (FP32 block
+ *              Jacobi, two Ogita-Aishima refinement steps in FP64-accurate tensor-core
+ *              GEMMs, FP64 Jacobi on the indices still coupled; needs compute
+ *              capability 10.3); 2: FP64 block Jacobi (blocks of 32 indices)
+ *   thr     rotations stop when every |g_pq| <= thr sqrt|g_pp g_qq| (thr >= 2e-16;
+ *           the mixed method's FP32 phase stops at 2e-6)
+ * Returns BAD_ARG, UNSUPPORTED (method 1 on another device), DEVICE_TIMEOUT.
+ * Synchronises `stream`. */
+int chase_bse_eigh(const void* G, int64_t k, double* theta, void* V, int32_t method, double thr,
+                   void* stream);
+
 /* FP64-accurate real GEMM on the BF16 tensor cores, the building block of the
  * mixed solve's QR and Rayleigh-Ritz products (the paper has no counterpart: it
  * serves the GB300, whose FP64 pipe runs at 1/64 of its FP32 rate).

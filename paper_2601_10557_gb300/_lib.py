@@ -87,7 +87,7 @@ _lib: Optional[ctypes.CDLL] = None
 EXPORTS = ["chase_bse_solve", "chase_bse_filter", "chase_bse_rr", "chase_bse_residuals", "chase_bse_grad",
            "chase_bse_strerror", "chase_bse_version", "chase_bse_has_mixed", "chase_bse_launch_count",
            "chase_bse_residuals_noalloc", "chase_bse_dgemm_sliced", "chase_bse_trim_memory",
-           "chase_bse_alloc_count", "chase_bse_degrees"]
+           "chase_bse_alloc_count", "chase_bse_degrees", "chase_bse_eigh"]
 
 # 2n * k limit of chase_bse_residuals_noalloc (its fixed device scratch, complex128 entries)
 NOALLOC_MAX_ENTRIES = 1 << 19
@@ -112,6 +112,7 @@ def lib() -> ctypes.CDLL:
     L.chase_bse_grad.argtypes = [vp, vp, i64, i64, vp, vp, vp]
     L.chase_bse_dgemm_sliced.argtypes = [vp, i64, vp, i64, i64, i64, i64, dbl, vp, i64, vp]
     L.chase_bse_degrees.argtypes = [vp, vp, vp, vp, i64, dbl, dbl, dbl, i32, i32, vp]
+    L.chase_bse_eigh.argtypes = [vp, i64, vp, vp, i32, dbl, vp]
     L.chase_bse_strerror.argtypes = [ctypes.c_int]
     L.chase_bse_strerror.restype = ctypes.c_char_p
     L.chase_bse_launch_count.restype = ctypes.c_int64
@@ -119,7 +120,7 @@ def lib() -> ctypes.CDLL:
     L.chase_bse_trim_memory.restype = None
     for name in ["chase_bse_solve", "chase_bse_filter", "chase_bse_rr", "chase_bse_residuals", "chase_bse_grad",
                  "chase_bse_version", "chase_bse_has_mixed", "chase_bse_residuals_noalloc",
-                 "chase_bse_dgemm_sliced", "chase_bse_degrees"]:
+                 "chase_bse_dgemm_sliced", "chase_bse_degrees", "chase_bse_eigh"]:
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -316,6 +317,24 @@ def degrees(ritz, res, prev_res, prev_deg, tol: float, mu_nevex: float, muN: flo
     _check(lib().chase_bse_degrees(ritz.ctypes.data, res.ctypes.data, prev_res.ctypes.data, prev_deg.ctypes.data,
                                    k, tol, mu_nevex, muN, deg_min, deg_max, out.ctypes.data), "chase_bse_degrees")
     return out.tolist()
+
+
+EIGH_METHODS = {"jacobi": 0, "mixed": 1, "block": 2, "block32": 3}
+
+
+def eigh(G: torch.Tensor, method: str = "mixed", thr: float = 2e-16, stream=None):
+    """chase_bse_eigh: (theta (k,), V (k, k)) with G V = V diag(theta) for a hermitian CUDA
+    complex128 matrix G (k even); the columns of V (k, k) are the eigenvectors."""
+    if not (isinstance(G, torch.Tensor) and G.is_cuda and G.dtype == torch.complex128 and G.dim() == 2
+            and G.shape[0] == G.shape[1]):
+        raise ValueError("G must be a square CUDA complex128 matrix")
+    k = G.shape[0]
+    Gc = G.transpose(0, 1).contiguous()  # column-major storage of G
+    theta = torch.empty(k, dtype=torch.float64, device=G.device)
+    Vt = torch.empty((k, k), dtype=torch.complex128, device=G.device)  # column-major V
+    _check(lib().chase_bse_eigh(_ptr(Gc), k, _ptr(theta), _ptr(Vt), EIGH_METHODS[method], thr,
+                                ctypes.c_void_p(_stream(stream))), "chase_bse_eigh")
+    return theta, Vt.transpose(0, 1)
 
 
 def grad(V: torch.Tensor, w: torch.Tensor, stream=None):

@@ -2,6 +2,7 @@
 #include <exception>
 #include <vector>
 
+#include "dense_kernels.cuh"
 #include "solver.cuh"
 #include "tc_dgemm.cuh"
 
@@ -26,6 +27,26 @@ static int degrees_host(const double* ritz, const double* res, const double* pre
   std::vector<int> d;
   cb::degrees_update(r, q, p, pd, tol, mu_nevex, muN, deg_min, deg_max, d);
   for (int64_t i = 0; i < k; ++i) degs[i] = d[i];
+  return CHASE_BSE_OK;
+}
+
+static int eigh_impl(const cplx* G, int64_t k, double* theta, cplx* V, int method, double thr, cudaStream_t s) {
+  cb::Workspace ws(s);
+  cplx *Gc, *rot;
+  double* red;
+  CB_TRY(ws.alloc(&Gc, k * k));
+  CB_TRY(ws.alloc(&rot, 2 * k));
+  CB_TRY(ws.alloc(&red, 2));
+  CB_CUDA(cudaMemcpyAsync(Gc, G, sizeof(cplx) * k * k, cudaMemcpyDeviceToDevice, s));
+  int sw = 0, sw32 = 0;
+  int st = CHASE_BSE_OK;
+  if (method == 0) st = cb::jacobi_eigh(Gc, k, V, theta, rot, red, 40, &sw, s, thr);
+  else if (method == 1) st = cb::jacobi_eigh_mixed(Gc, k, V, theta, rot, red, &sw32, &sw, s, thr);
+  else if (method == 3) st = cb::jacobi_block(Gc, k, V, theta, true, 2e-6, 1e-8, 30, &sw, s);
+  else st = cb::jacobi_block(Gc, k, V, theta, false, thr, 0.5 * thr, 40, &sw, s);
+  if (cb::verbose()) fprintf(stderr, "[chase_bse] eigh method %d k %ld sweeps %d (FP32 %d)\n", method, (long)k, sw, sw32);
+  if (st != CHASE_BSE_OK) return st;
+  CB_CUDA(cudaStreamSynchronize(s));
   return CHASE_BSE_OK;
 }
 
@@ -106,6 +127,13 @@ int chase_bse_degrees(const double* ritz, const double* res, const double* prev_
       deg_max < deg_min || !(mu_nevex > 0) || !(muN > mu_nevex))
     return CHASE_BSE_BAD_ARG;
   CB_GUARD(return degrees_host(ritz, res, prev_res, prev_deg, k, tol, mu_nevex, muN, deg_min, deg_max, degs);)
+}
+
+int chase_bse_eigh(const void* G, int64_t k, double* theta, void* V, int32_t method, double thr, void* stream) {
+  if (!G || !theta || !V || k < 2 || (k % 2) != 0 || method < 0 || method > 3 || !(thr >= 2e-16))
+    return CHASE_BSE_BAD_ARG;
+  if (method == 1 && !cb::mixed_available()) return CHASE_BSE_UNSUPPORTED;
+  CB_GUARD(return eigh_impl((const cplx*)G, k, theta, (cplx*)V, method, thr, (cudaStream_t)stream);)
 }
 
 int chase_bse_dgemm_sliced(const double* A, int64_t lda, const double* B, int64_t ldb, int64_t M, int64_t N,

@@ -2,6 +2,9 @@
 // Householder QR, Lanczos pieces and column utilities.  Matrices are
 // column-major complex128 unless stated otherwise.
 #pragma once
+#include <utility>
+#include <vector>
+
 #include "common.cuh"
 
 namespace cb {
@@ -30,6 +33,24 @@ int jacobi_eigh(cplx* G, int64_t k, cplx* V, double* theta, cplx* rot, double* r
 // nearly diagonal G.  Needs the tensor cores (compute capability 10.3).
 int jacobi_eigh_mixed(cplx* G, int64_t k, cplx* V, double* theta, cplx* rot, double* red, int* sweeps32_out,
                       int* sweeps64_out, cudaStream_t s, double thr);
+
+// Block Jacobi (jacobi_block.cu): blocks of 32 indices paired round-robin, each pair's
+// 64 x 64 sub-problem swept in shared memory, coalesced 64 x 64 tile updates of G and V;
+// FP32 (fp32) or FP64 arithmetic.  G (k x k, hermitian, FP64) is not modified; V (k x k)
+// receives the eigenvectors and theta (device, optional) the diagonal of the rotated G.
+// Rotations stop when every |g_pq| <= thr sqrt|g_pp g_qq| or <= floor_rel ||G||_F.
+int jacobi_block(const cplx* G, int64_t k, cplx* V, double* theta, bool fp32, double thr, double floor_rel,
+                 int max_sweeps, int* sweeps_out, cudaStream_t s);
+
+// The pairs i < j with |g_ij| > t sqrt|g_ii g_jj| and |g_ij| > floor_abs (at most cap
+// of them, else OOM).
+int coupled_pairs(const cplx* G, int64_t k, double t, double floor_abs, std::vector<std::pair<int, int>>& out,
+                  int cap, cudaStream_t s);
+// For disjoint index sets (set j = idx[off[j] .. off[j+1]), at most 64 each): FP64 Jacobi
+// on G[set, set] (one CTA per set), its eigenvectors into those rows and columns of V2
+// (k x k, preset to the identity) and its eigenvalues into theta.
+int cluster_eig(const cplx* G, int64_t k, const std::vector<int>& idx, const std::vector<int>& off, double thr,
+                double floor_abs, cplx* V2, double* theta, cudaStream_t s);
 
 // Unblocked Householder QR: Q (N x m, column-major, ld N) receives the
 // orthonormal factor of X (N x m), which is destroyed.  Vs: N*m, Us: N*m,
