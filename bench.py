@@ -4,7 +4,11 @@
 One step = one full pass of the hot path on the synthetic workload: Lanczos
 bounds, the filtered subspace iteration (filter, CholeskyQR2, oblique
 Rayleigh-Ritz, residuals, locking, per-vector degrees) until nev pairs are
-locked, and the eigenvalue-gradient backward of L = sum_i w_i lambda_i.
+locked, and the eigenvalue-gradient backward of L = sum_i w_i lambda_i.  The
+default workload is n16384: H of size 32768, nev 1000, nex 300, degrees up to
+36, tol 1e-10, a dense band of 5 % of the eigenvalues at the bottom of the
+spectrum, mixed precision (FP16x3 tensor-core filter, FP64-accurate products
+elsewhere).
 
 Printed JSON line (rank 0):
   value            filter TFLOP/s over the timed steps (algorithmic flops
@@ -14,6 +18,8 @@ Printed JSON line (rank 0):
                    host buffers, host<->device copies inside the timed region
   roofline         the dominant kernel (the filter GEMM) against the measured peak
   cpu_baseline     the CPU oracle (a bounded sample) on the host cores
+  eig_error        per-eigenvalue error bounds of the returned pairs, from FP64
+                   products computed independently of the solver
 
 Under torchrun (N > 1) every rank solves its own independent problem instance
 (replicas: the method has no data-path exchange on one problem per GPU).
@@ -21,8 +27,10 @@ Under torchrun (N > 1) every rank solves its own independent problem instance
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -35,7 +43,13 @@ sys.path.insert(0, ROOT)
 METRIC = "filter TFLOP/s + time to nev eigenpairs at tol=1e-10, mixed vs FP64 on 1 GB300"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 # nominal dense rates (TFLOP/s) used to scale a measured bf16 peak to another dtype
-NOMINAL = {"bf16": 2250.0, "fp64": 1.25}
+NOMINAL = {"bf16": 2250.0, "fp16": 2250.0, "fp64": 1.25}
+# workloads whose inputs are assembled on the device (the host QR of the Haar-unitary
+# factor takes minutes at these sizes)
+DEVICE_INPUTS_FROM = 8192
+# the ncu summary that holds the DRAM traffic of the filter GEMM per workload
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "tc_hop_fp16x3_traffic.md")
+FILTER_SOURCE = os.path.join(ROOT, "paper_2601_10557_gb300", "csrc", "tc_filter.cu")
 
 
 def parse():
@@ -44,40 +58,15 @@ def parse():
     p.add_argument("--steps", type=int, default=2)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="n4096")
+    p.add_argument("--workload", default="n16384")
     p.add_argument("--precision", default="auto", choices=["auto", "fp64", "mixed", "fp16x3", "bf16x3", "bf16x6"])
     p.add_argument("--no-fp64-compare", action="store_true")
-    p.add_argument("--e2e-steps", type=int, default=None)
+    p.add_argument("--e2e-steps", type=int, default=None,
+                   help="end-to-end steps (default: 1 for n >= 16384, else --steps)")
     p.add_argument("--filter-only", action="store_true",
                    help="only the filter roofline measurement (one warm and one timed chase_bse_filter call)")
     p.add_argument("--deg", type=int, default=None, help="filter degree for --filter-only")
     return p.parse_args()
-
-
-def filter_only(args, wl):
-    import torch
-    import paper_2601_10557_gb300 as pkg
-    P, W0n, _, _ = make_inputs(wl, 0)
-    dev = torch.device("cuda", 0)
-    A = torch.from_numpy(P.A).to(dev)
-    B = torch.from_numpy(P.B).to(dev)
-    W = torch.from_numpy(W0n).to(dev)
-    prec = args.precision if args.precision != "auto" else ("mixed" if pkg.has_mixed() else "fp64")
-    deg = args.deg or wl["deg"]
-    k = W.shape[0]
-    pkg.filter(A, B, W.clone(), [deg] * k, 1.0, 2.0, 60.0, precision=prec)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    Wt = W.clone()
-    e0.record()
-    pkg.filter(A, B, Wt, [deg] * k, 1.0, 2.0, 60.0, precision=prec)
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    fl = 64.0 * wl["n"] ** 2 * k * deg
-    print(json.dumps({"filter_only": True, "precision": prec, "n": wl["n"], "k": k, "deg": deg, "ms": ms,
-                      "tflops": fl / ms / 1e9}), flush=True)
 
 
 def load_peaks():
@@ -89,7 +78,25 @@ def load_peaks():
     return dict(PEAKS_FALLBACK), "fallback"
 
 
-TC_TRAFFIC_N4096_K260 = (486640128 + 43591680 + 503699456 + 50020864) / 2.0  # bytes per launch
+def filter_source_hash() -> str:
+    with open(FILTER_SOURCE, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def traffic_for(workload: str):
+    """DRAM bytes per filter-GEMM launch (dram__bytes_read.sum + dram__bytes_write.sum)
+    from the committed ncu summary, or None when it has no line for this workload or
+    was taken on another version of the kernel source."""
+    if not os.path.exists(TRAFFIC_PROFILE):
+        return None, "no capture"
+    txt = open(TRAFFIC_PROFILE).read()
+    m = re.search(r"kernel source sha256\[:16\]:\s*([0-9a-f]{16})", txt)
+    if not m or m.group(1) != filter_source_hash():
+        return None, "capture predates the current kernel source"
+    m = re.search(rf"traffic_bytes_per_launch\[{re.escape(workload)}\]:\s*([0-9.e+]+)", txt)
+    if not m:
+        return None, f"no capture for {workload}"
+    return float(m.group(1)), "ncu capture (profiles/" + os.path.basename(TRAFFIC_PROFILE) + ")"
 
 
 class ClockSampler:
@@ -160,54 +167,151 @@ def whole_job_tflops(dist, flops: float, ms: float, device) -> float:
     return reduce_scalar(dist, flops, "sum", device) / (reduce_scalar(dist, ms, "max", device) / 1e3) / 1e12
 
 
-def make_inputs(wl: dict, seed: int):
+def make_inputs(wl: dict, seed: int, device=None):
+    """(A, B, d, W0, V0, w): A, B as numpy arrays (host generator) or, for large n with
+    a device given, torch tensors assembled on that device."""
     import bse_inputs as bi
-    P = bi.make_problem(wl["n"], seed=seed, spec=wl["spec"], beta=wl["beta"])
-    nevex = wl["nev"] + wl["nex"]
-    W0 = bi.start_block(wl["n"], nevex, seed)
-    V0 = bi.lanczos_starts(wl["n"], 4, seed)
-    w = bi.loss_weights(wl["nev"], seed)
-    return P, W0, V0, w
-
-
-def cpu_oracle_sample(P, W0, wl):
-    """The oracle as it stands: one H^2 step of its Chebyshev filter (degree 1)
-    over all nev + nex columns, timed on the host cores."""
-    import numpy as np
-    from oracle import chebyshev, dense
     n = wl["n"]
-    k = W0.shape[0]
+    if device is not None and n >= DEVICE_INPUTS_FROM:
+        A, B, d = bi.make_problem_device(n, seed, wl["spec"], wl["beta"], device=device)
+    else:
+        P = bi.make_problem(n, seed=seed, spec=wl["spec"], beta=wl["beta"])
+        A, B, d = P.A, P.B, P.d
+    nevex = wl["nev"] + wl["nex"]
+    W0 = bi.start_block(n, nevex, seed)
+    V0 = bi.lanczos_starts(n, 4, seed)
+    w = bi.loss_weights(wl["nev"], seed)
+    return A, B, d, W0, V0, w
+
+
+def cpu_oracle_sample(A, B, W0, wl, ncols=None):
+    """The oracle as it stands: one H^2 step of its Chebyshev filter (degree 1) over
+    ncols columns (all nev + nex by default), timed on the host cores."""
+    import numpy as np
+    from oracle import chebyshev
+    n = wl["n"]
+    W = W0 if ncols is None else W0[:ncols]
+    k = W.shape[0]
     lam_guess = (0.9, 2.0, 60.0)
     t0 = time.perf_counter()
-    chebyshev.chebyshev_filter(P.A, P.B, W0.T, np.ones(k, dtype=int), *lam_guess)
+    chebyshev.chebyshev_filter(A, B, W.T, np.ones(k, dtype=int), *lam_guess)
     dt = time.perf_counter() - t0
     flops = 64.0 * n * n * k
     return {"value": flops / dt / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"one H^2 step (degree 1) of the oracle filter, n={n}, k={k} columns, "
+            "sample": f"one H^2 step (degree 1) of the oracle filter, n={n}, {k} columns, "
                       f"{dt:.2f} s incl. forming H; the metric's unit scaled by 64 n^2 k flops"}
+
+
+def sample_columns(wl):
+    """Columns of the bounded CPU sample: all nev + nex up to n = 4096, 32 beyond."""
+    return None if wl["n"] <= 4096 else 32
+
+
+def host_inputs(wl, seed):
+    """Inputs as numpy arrays for the CPU oracle (device assembly when large)."""
+    import torch
+    dev = torch.device("cuda", 0) if torch.cuda.is_available() else None
+    A, B, d, W0, V0, w = make_inputs(wl, seed, device=dev)
+    if not isinstance(A, type(W0)):
+        A, B = A.cpu().numpy(), B.cpu().numpy()
+    return A, B, W0
 
 
 def run_reference(args, wl, rank, world):
     if rank != 0:
         return
     import numpy as np
-    P, W0, V0, w = make_inputs(wl, 0)
+    A, B, W0 = host_inputs(wl, 0)
+    ncols = sample_columns(wl)
     steps, warm = max(args.steps, 1), max(args.warmup, 0)
     samples = []
     for i in range(warm + steps):
-        s = cpu_oracle_sample(P, W0, wl)
+        s = cpu_oracle_sample(A, B, W0, wl, ncols)
         if i >= warm:
             samples.append(s["value"])
     v = float(np.mean(samples))
+    cols = W0.shape[0] if ncols is None else ncols
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "TFLOP/s", "n_gpus": args.gpus,
             "steps": steps, "warmup": warm, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "n": wl["n"], "nev": wl["nev"], "nex": wl["nex"]},
+            "config": {"workload": args.workload, "n": wl["n"], "H": 2 * wl["n"], "nev": wl["nev"],
+                       "nex": wl["nex"], "tol": wl["tol"], "spectrum": wl["spec"], "beta": wl["beta"]},
             "cpu_baseline": {"value": v, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": "per step: one H^2 step (degree 1) of the oracle filter over nev+nex "
+                             "sample": f"per step: one H^2 step (degree 1) of the oracle filter over {cols} "
                                        "columns of the same workload"},
             "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def filter_only(args, wl):
+    import torch
+    import paper_2601_10557_gb300 as pkg
+    dev = torch.device("cuda", 0)
+    A, B, d, W0n, _, _ = make_inputs(wl, 0, device=dev)
+    A, B = (torch.as_tensor(A).to(dev), torch.as_tensor(B).to(dev))
+    W = torch.from_numpy(W0n).to(dev)
+    prec = args.precision if args.precision != "auto" else ("mixed" if pkg.has_mixed() else "fp64")
+    deg = args.deg or wl["deg"]
+    k = W.shape[0]
+    pkg.filter(A, B, W.clone(), [deg] * k, 1.0, 2.0, 60.0, precision=prec)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    Wt = W.clone()
+    e0.record()
+    pkg.filter(A, B, Wt, [deg] * k, 1.0, 2.0, 60.0, precision=prec)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    fl = 64.0 * wl["n"] ** 2 * k * deg
+    print(json.dumps({"filter_only": True, "precision": prec, "n": wl["n"], "k": k, "deg": deg, "ms": ms,
+                      "tflops": fl / ms / 1e9}), flush=True)
+
+
+def eig_error_bounds(A, B, lam, V, nsample: int = 100):
+    """Per-eigenvalue error bounds of returned pairs against the exact eigenvalues (what
+    an FP64 solve converges to), from FP64 products done here with torch, not by the
+    solver: r = ||H v - lambda v|| and s = v^* S v give |lambda - lambda_exact| <= r/|s|
+    to first order (v^* S is the left eigenvector, Theorem SH_HPD), and the S-Rayleigh
+    quotient rho = v^* S H v / s differs from lambda by O(r^2).  Every nev/nsample-th pair."""
+    import torch
+    nev = lam.shape[0]
+    idx = torch.arange(0, nev, max(1, nev // nsample), device=V.device)
+    Vs = V[idx].T.contiguous()  # 2n x m
+    n = A.shape[0]
+    X, Y = Vs[:n], Vs[n:]
+    # A, B are the (row-major) matrices themselves: H v = [A x + B y; -conj(B) x - conj(A) y]
+    top = A @ X + B @ Y
+    bot = -(B.conj() @ X) - A.conj() @ Y
+    HV = torch.cat([top, bot], dim=0)
+    lv = lam[idx]
+    R = HV - Vs * lv[None, :]
+    r = torch.linalg.vector_norm(R, dim=0)
+    SV = torch.cat([X, -Y], dim=0)
+    s = torch.real(torch.sum(SV.conj() * Vs, dim=0))
+    rho = torch.real(torch.sum(SV.conj() * HV, dim=0)) / s
+    bound = (r / s.abs()) / lv.abs()
+    rq = (rho - lv).abs() / lv.abs()
+    # second order: |rho - lambda_exact| <~ r^2 / (|s| gap), gap = distance to the nearest
+    # other returned eigenvalue (no eigenvalue is missing from the returned set: the
+    # completeness of the returned set is the inertia test's subject)
+    srt = torch.sort(lam).values
+    gaps = torch.empty_like(lam)
+    d = srt[1:] - srt[:-1]
+    gaps[0], gaps[-1] = d[0], d[-1]
+    gaps[1:-1] = torch.minimum(d[1:], d[:-1])
+    gsel = gaps[idx]
+    bound2 = (r * r / (s.abs() * gsel)) / lv.abs()
+    return {"reference": "exact eigenvalue; first-order bound ||Hv - lambda v|| / (|v^* S v| lambda), "
+                         "second-order bound ||Hv - lambda v||^2 / (|v^* S v| gap lambda) and "
+                         "|rho_S - lambda| / lambda with rho_S the S-Rayleigh quotient, FP64 torch products",
+            "sampled_pairs": int(idx.numel()), "max_rel_bound": float(bound.max()),
+            "max_rel_bound_second_order": float(bound2.max()),
+            "max_rel_rayleigh_diff": float(rq.max()),
+            "per_eigenvalue": [{"i": int(i), "lambda": float(l), "rel_bound": float(b), "rel_bound2": float(b2),
+                                "rel_rq_diff": float(q)}
+                               for i, l, b, b2, q in zip(idx.tolist(), lv.tolist(), bound.tolist(), bound2.tolist(),
+                                                         rq.tolist())]}
 
 
 def main():
@@ -239,9 +343,9 @@ def main():
         precision = "mixed" if pkg.has_mixed() else "fp64"
     n, nev, nex = wl["n"], wl["nev"], wl["nex"]
     nevex = nev + nex
-    P, W0n, V0n, wn = make_inputs(wl, rank)
-    A = torch.from_numpy(P.A).to(dev)
-    B = torch.from_numpy(P.B).to(dev)
+    A, B, d, W0n, V0n, wn = make_inputs(wl, rank, device=dev)
+    A = torch.as_tensor(A).to(dev)
+    B = torch.as_tensor(B).to(dev)
     W0 = torch.from_numpy(W0n).to(dev)
     V0 = torch.from_numpy(V0n).to(dev)
     w = torch.from_numpy(wn).to(dev)
@@ -257,7 +361,8 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    for _ in range(max(args.warmup, 3)):
+    warm = max(args.warmup, 3)
+    for _ in range(warm):
         step(precision)
     stream = torch.cuda.current_stream()
     clocks = ClockSampler(local)
@@ -289,14 +394,16 @@ def main():
 
     value = whole_job_tflops(dist, fl, fms, dev)
     tts_max = reduce_scalar(dist, tts, "max", dev)
-
-    # correctness of the timed result against cheap oracle-side properties
     lam_np = lam.cpu().numpy()
 
+    # ---- per-eigenvalue error bounds of the last timed result (independent FP64 products)
+    eig_err = eig_error_bounds(A, B, lam, V) if rank == 0 else None
+    torch.cuda.synchronize()
+
     # ---- e2e through the public API with host buffers
-    e2e_steps = args.e2e_steps if args.e2e_steps is not None else args.steps
-    hA = torch.from_numpy(P.A).pin_memory()
-    hB = torch.from_numpy(P.B).pin_memory()
+    e2e_steps = args.e2e_steps if args.e2e_steps is not None else (1 if n >= 16384 else args.steps)
+    hA = A.cpu().pin_memory()
+    hB = B.cpu().pin_memory()
     hW0 = torch.from_numpy(W0n).pin_memory()
     hV0 = torch.from_numpy(V0n).pin_memory()
     hw = torch.from_numpy(wn).pin_memory()
@@ -323,13 +430,15 @@ def main():
         out_gA.copy_(g2A, non_blocking=True)
         out_gB.copy_(g2B, non_blocking=True)
         efl += st2["filter_flops"]
+        del dA, dB, g2A, g2B
     e1.record(stream)
     barrier()
     e2e_ms = reduce_scalar(dist, e0.elapsed_time(e1), "max", dev)
     e2e_val = whole_job_tflops(dist, efl, e2e_ms, dev)
+    del hA, hB, out_gA, out_gB
 
-    # ---- roofline of the dominant kernel: one filter call at the workload's size
-    deg_r = wl["deg"]
+    # ---- roofline of the dominant kernel: one filter call over all nev + nex columns
+    deg_r = wl["deg"] if n < 16384 else 4
     Wr = W0.clone()
     pkg.filter(A, B, Wr, [deg_r] * nevex, 1.0, 2.0, 60.0, precision=precision)  # warm
     barrier()
@@ -349,39 +458,66 @@ def main():
     if precision == "fp64":
         peak = peaks["bf16_tflops"] * NOMINAL["fp64"] / NOMINAL["bf16"]
         peak_note = f"{peak_src} bf16 burst x nominal fp64/bf16 ratio (1.25/2250)"
+    elif precision == "bf16x6":
+        peak = peaks["bf16_tflops"] / 6.0
+        peak_note = f"{peak_src} bf16 burst / 6 (six 16-bit products per FP32-accurate product)"
     else:
         peak = peaks["bf16_tflops"] / 3.0
-        peak_note = f"{peak_src} bf16 burst / 3 (three BF16 products per FP32-accurate product)"
-    # DRAM bytes per launch of the BF16x3 filter kernel (tc_hop_kernel<3, 128>) at this
-    # workload, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, mean of
-    # two launches; profiles/tc_hop_bf16x3_n4096_k260.md); other cases were not captured
-    traffic = TC_TRAFFIC_N4096_K260 if (precision in ("mixed", "bf16x3") and n == 4096 and nevex == 260) else None
+        peak_note = (f"{peak_src} bf16 burst / 3 (three 16-bit products per FP32-accurate product; "
+                     "the nominal FP16 and BF16 dense rates are equal)")
+    traffic, traffic_src = traffic_for(args.workload) if precision in ("mixed", "fp16x3") else (None, "n/a")
     roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": traffic, "kernel": "hop_kernel (FP64 DFMA)" if precision == "fp64" else "tc_filter_gemm",
+            "traffic": traffic, "traffic_source": traffic_src,
+            "kernel": "hop_kernel (FP64 DFMA)" if precision == "fp64" else "tc_hop_kernel (tcgen05 filter GEMM)",
             "peak_source": peak_note, "launches_timed": gemm_launches, "all_launches": rl,
-            "flops_per_launch": flops_per_launch}
+            "flops_per_launch": flops_per_launch, "degree_of_timed_call": deg_r}
 
-    # ---- FP64 comparison solve (time to solution)
-    fp64_tts = None
+    # ---- FP64 comparison
+    fp64 = None
     if precision != "fp64" and not args.no_fp64_compare:
-        barrier()
-        f0 = torch.cuda.Event(enable_timing=True)
-        f1 = torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
-        step("fp64")
-        f1.record(stream)
-        barrier()
-        fp64_tts = reduce_scalar(dist, f0.elapsed_time(f1) / 1e3, "max", dev)
+        if n <= 4096:
+            barrier()
+            f0 = torch.cuda.Event(enable_timing=True)
+            f1 = torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            step("fp64")
+            f1.record(stream)
+            barrier()
+            fp64 = {"time_to_solution_s": reduce_scalar(dist, f0.elapsed_time(f1) / 1e3, "max", dev),
+                    "kind": "measured: one plain FP64 solve + gradient (unwarmed)"}
+        else:
+            # the plain FP64 solve takes hours here: its filter alone, at the FP64 filter
+            # rate measured on a short call, is a lower bound of its time
+            kc = 64
+            Wf = W0[:kc].clone()
+            pkg.filter(A, B, Wf, [1] * kc, 1.0, 2.0, 60.0, precision="fp64")
+            barrier()
+            f0 = torch.cuda.Event(enable_timing=True)
+            f1 = torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            pkg.filter(A, B, Wf, [2] * kc, 1.0, 2.0, 60.0, precision="fp64")
+            f1.record(stream)
+            barrier()
+            rate = 64.0 * n * n * kc * 2 / (f0.elapsed_time(f1) / 1e3)
+            flops_step = fl / max(args.steps, 1)
+            fp64 = {"time_to_solution_s": flops_step / rate,
+                    "kind": "extrapolated lower bound: the mixed solve's filter flops "
+                            f"({flops_step:.3e}) at the FP64 filter rate measured on a degree-2 call over "
+                            f"{kc} columns ({rate / 1e12:.3f} TFLOP/s); QR, Rayleigh-Ritz and the "
+                            "FP64 filter's extra iterations not counted",
+                    "fp64_filter_tflops": rate / 1e12}
 
     cpu = None
     if rank == 0 and world == 1:
-        cpu = cpu_oracle_sample(P, W0n, wl)
+        hAn, hBn = A.cpu().numpy(), B.cpu().numpy()
+        cpu = cpu_oracle_sample(hAn, hBn, W0n, wl, sample_columns(wl))
+        del hAn, hBn
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
-            "warmup": max(args.warmup, 3), "ms_per_step": tts_max * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if precision == "fp64" else "bf16x3+f64",
+            "warmup": warm, "ms_per_step": tts_max * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if precision == "fp64" else "fp16x3+f64",
             "data": "synthetic",
             "config": {"workload": args.workload, "n": n, "H": 2 * n, "nev": nev, "nex": nex,
                        "deg": f"{wl['deg_min']}-{wl['deg_max']} adaptive, first {wl['deg']}", "tol": wl["tol"],
@@ -389,12 +525,14 @@ def main():
                        "l2": "inputs larger than L2 (A and B: %.0f MB)" % (2 * n * n * 16 / 1e6),
                        "parallelism": f"replicas x{world}"},
             "time_to_solution_s": tts_max,
-            "time_to_solution_fp64_s": fp64_tts if precision != "fp64" else tts_max,
+            "time_to_solution_fp64_s": (fp64 or {}).get("time_to_solution_s") if precision != "fp64" else tts_max,
+            "fp64_comparison": fp64,
             "iterations": iters, "max_residual": maxres,
             "phases_ms_per_step": {k2: round(v2, 2) for k2, v2 in phases.items()},
             "lambda_min_max": [float(lam_np[0]), float(lam_np[-1])],
+            "eig_error": eig_err,
             "e2e": {"value": e2e_val, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "ms_per_step": e2e_ms / max(e2e_steps, 1)},
+                    "ms_per_step": e2e_ms / max(e2e_steps, 1), "steps": max(e2e_steps, 1)},
             "gpu_launches": launches,
             "roofline": roof,
             "cpu_baseline": cpu,

@@ -1284,6 +1284,20 @@ int normalize_and_residual(cplx* W, const cplx* SHW, const double* ritz, int64_t
   return CHASE_BSE_OK;
 }
 
+// R[:, j] = HV[:, j] - lam[j] V[:, j]
+__global__ void residual_from_hv_kernel(const cplx* HV, const cplx* V, const double* lam, int64_t n2, int64_t m,
+                                        cplx* R) {
+  GRID_STRIDE(idx, n2 * m) { R[idx] = csub(HV[idx], cscale(V[idx], lam[idx / n2])); }
+}
+int residual_from_hv(const cplx* HV, const cplx* V, const double* lam, int64_t n2, int64_t m, cplx* R,
+                     cudaStream_t s) {
+  if (m == 0) return CHASE_BSE_OK;
+  residual_from_hv_kernel<<<gs(n2 * m), 256, 0, s>>>(HV, V, lam, n2, m, R);
+  count_launch();
+  CB_LAUNCH();
+  return CHASE_BSE_OK;
+}
+
 __global__ void set_identity_kernel(cplx* M, int64_t k) {
   GRID_STRIDE(i, k * k) { M[i] = (i % k == i / k) ? mk(1, 0) : mk(0, 0); }
 }

@@ -86,6 +86,9 @@ int normalize_cols(cplx* X, int64_t rows, int64_t m, cudaStream_t s);
 int normalize_and_residual(cplx* W, const cplx* SHW, const double* ritz, int64_t n, int64_t m, cplx* R,
                            cudaStream_t s);
 int set_identity(cplx* M, int64_t k, cudaStream_t s);
+// R[:, j] = HV[:, j] - lam[j] V[:, j] (n2 x m; lam device)
+int residual_from_hv(const cplx* HV, const cplx* V, const double* lam, int64_t n2, int64_t m, cplx* R,
+                     cudaStream_t s);
 int hermitize(cplx* G, int64_t k, cudaStream_t s);
 int diag_real(const cplx* G, int64_t k, double* out, cudaStream_t s);
 int phase_fix(cplx* V, int64_t n, int64_t m, cudaStream_t s);

@@ -1018,8 +1018,19 @@ int solve(const cplx* A, const cplx* B, int64_t n, int64_t nev, int64_t nex, int
     CB_TRY(gather_cols(evecs, Ylock, od, n2, nout, s));
     CB_TRY(phase_fix(evecs, n, nout, s));
     CB_CUDA(cudaMemcpyAsync(evals, lo.data(), sizeof(double) * nout, cudaMemcpyHostToDevice, s));
-    // residual of the returned pairs
-    CB_TRY(residuals(A, B, n, evecs, evals, nout, res_d, s));
+    // residual of the returned pairs (mixed mode: H V by the FP64-accurate tensor-core
+    // product, as the rest of the iteration)
+    if (sliced) {
+      Workspace rws(s);
+      cplx *HV, *Rr;
+      CB_TRY(rws.alloc(&HV, n2 * nout));
+      CB_TRY(rws.alloc(&Rr, n2 * nout));
+      CB_TRY(hop_sliced(ph, evecs, n, nout, HV, s));
+      CB_TRY(residual_from_hv(HV, evecs, evals, n2, nout, Rr, s));
+      CB_TRY(col_norms(Rr, n2, nout, res_d, s));
+    } else {
+      CB_TRY(residuals(A, B, n, evecs, evals, nout, res_d, s));
+    }
     std::vector<double> rr(nout);
     CB_CUDA(cudaMemcpyAsync(rr.data(), res_d, sizeof(double) * nout, cudaMemcpyDeviceToHost, s));
     CB_CUDA(cudaStreamSynchronize(s));

@@ -40,9 +40,9 @@ def _worker(rank: int, world: int, port: int, q) -> None:
         v = bench.whole_job_tflops(dist, (rank + 1) * 1e12, (rank + 1) * 100.0, "cpu")
         m = bench.reduce_scalar(dist, float(rank), "max", "cpu")
         s = bench.reduce_scalar(dist, float(rank + 1), "sum", "cpu")
-        P, W0, V0, w = bench.make_inputs(WL, rank)
-        P2, W02, V02, w2 = bench.make_inputs(WL, rank)
-        q.put((rank, v, m, s, _digest(P.A, P.B, W0, V0, w), _digest(P2.A, P2.B, W02, V02, w2)))
+        A, B, _, W0, V0, w = bench.make_inputs(WL, rank)
+        A2, B2, _, W02, V02, w2 = bench.make_inputs(WL, rank)
+        q.put((rank, v, m, s, _digest(A, B, W0, V0, w), _digest(A2, B2, W02, V02, w2)))
     finally:
         dist.destroy_process_group()
 
