@@ -48,7 +48,8 @@ typedef enum chase_bse_status {
   CHASE_BSE_NOT_DEFINITE = -4,   /* Cholesky of Q^* S H Q failed: S H not HPD         */
   CHASE_BSE_QR_FAILED = -5,      /* search space rank-deficient even for Householder  */
   CHASE_BSE_DEVICE_TIMEOUT = -6, /* a bounded device-side wait gave up                */
-  CHASE_BSE_UNSUPPORTED = -7     /* feature needs a device this build cannot run on   */
+  CHASE_BSE_UNSUPPORTED = -7,    /* feature needs a device this build cannot run on   */
+  CHASE_BSE_NONFINITE = -8       /* an input (A, B, W0, V0) holds a NaN or an Inf      */
 } chase_bse_status;
 
 typedef enum chase_bse_precision {
@@ -123,7 +124,8 @@ typedef struct chase_bse_stats {
  *            and positive
  *   stats    host, may be NULL
  * Returns OK, NOT_CONVERGED (the first stats->converged entries are valid), or
- * an error.  Synchronises opts->stream. */
+ * an error; NONFINITE (nothing computed) when A, B, opts->W0 or opts->V0 hold a
+ * NaN or an Inf.  Synchronises opts->stream. */
 int chase_bse_solve(const void* A, const void* B, int64_t n, int64_t nev, int64_t nex,
                     int32_t deg, double tol, const chase_bse_opts* opts, double* evals,
                     void* evecs, chase_bse_stats* stats);
@@ -142,6 +144,15 @@ int chase_bse_solve(const void* A, const void* B, int64_t n, int64_t nev, int64_
 int chase_bse_filter(const void* A, const void* B, int64_t n, void* W, int64_t k,
                      const int32_t* degs, double mu1, double mu_nevex, double muN,
                      int32_t precision, void* stream);
+
+/* chase_bse_filter with a precision per column (the precision groups of a mixed solve,
+ * where a column that nears the tolerance moves to the FP64 filter): precs (host, k
+ * entries) are chase_bse_precision codes; the FP64 columns run the FP64 filter and the
+ * others the tensor-core filter, which takes one scheme per call (all non-FP64 entries
+ * equal, else BAD_ARG).  Same arguments otherwise. */
+int chase_bse_filter_cols(const void* A, const void* B, int64_t n, void* W, int64_t k,
+                          const int32_t* degs, const int32_t* precs, double mu1,
+                          double mu_nevex, double muN, void* stream);
 
 /* Oblique Rayleigh-Ritz with hermitian spectral equivalence (Algorithm 2):
  * T = S H Q, M = Q^* T = L L^*, G = L^{-1}(I - 2 Q_2^* Q_2) L^{-*}, G y = theta y,
@@ -270,6 +281,13 @@ void chase_bse_trim_memory(void);
 /* Diagnostics (no counterpart in the paper): the number of CUDA kernels this
  * library has launched since it was loaded, summed over all threads. */
 int64_t chase_bse_launch_count(void);
+
+/* Testing and diagnostics (no counterpart in the paper): the bound, in nanoseconds of
+ * %globaltimer, of every grid-barrier wait of the cooperative kernels (Cholesky, the
+ * Jacobi eigensolvers); 0 restores the default of 2 s.  A wait that runs out makes the
+ * kernel record an error and leave at its next barrier; the call then returns
+ * DEVICE_TIMEOUT and the device stays usable.  Applies to calls made after it. */
+void chase_bse_set_wait_limit(uint64_t ns);
 
 /* Diagnostics (no counterpart in the paper): the number of device allocations
  * (stream-ordered, from the library's pool) the library has requested since it

@@ -87,7 +87,8 @@ _lib: Optional[ctypes.CDLL] = None
 EXPORTS = ["chase_bse_solve", "chase_bse_filter", "chase_bse_rr", "chase_bse_residuals", "chase_bse_grad",
            "chase_bse_strerror", "chase_bse_version", "chase_bse_has_mixed", "chase_bse_launch_count",
            "chase_bse_residuals_noalloc", "chase_bse_dgemm_sliced", "chase_bse_trim_memory",
-           "chase_bse_alloc_count", "chase_bse_degrees", "chase_bse_eigh"]
+           "chase_bse_alloc_count", "chase_bse_degrees", "chase_bse_eigh", "chase_bse_filter_cols",
+           "chase_bse_set_wait_limit"]
 
 # 2n * k limit of chase_bse_residuals_noalloc (its fixed device scratch, complex128 entries)
 NOALLOC_MAX_ENTRIES = 1 << 19
@@ -113,6 +114,10 @@ def lib() -> ctypes.CDLL:
     L.chase_bse_dgemm_sliced.argtypes = [vp, i64, vp, i64, i64, i64, i64, dbl, vp, i64, vp]
     L.chase_bse_degrees.argtypes = [vp, vp, vp, vp, i64, dbl, dbl, dbl, i32, i32, vp]
     L.chase_bse_eigh.argtypes = [vp, i64, vp, vp, i32, dbl, vp]
+    L.chase_bse_filter_cols.argtypes = [vp, vp, i64, vp, i64, ctypes.POINTER(ctypes.c_int32),
+                                        ctypes.POINTER(ctypes.c_int32), dbl, dbl, dbl, vp]
+    L.chase_bse_set_wait_limit.argtypes = [ctypes.c_uint64]
+    L.chase_bse_set_wait_limit.restype = None
     L.chase_bse_strerror.argtypes = [ctypes.c_int]
     L.chase_bse_strerror.restype = ctypes.c_char_p
     L.chase_bse_launch_count.restype = ctypes.c_int64
@@ -120,7 +125,7 @@ def lib() -> ctypes.CDLL:
     L.chase_bse_trim_memory.restype = None
     for name in ["chase_bse_solve", "chase_bse_filter", "chase_bse_rr", "chase_bse_residuals", "chase_bse_grad",
                  "chase_bse_version", "chase_bse_has_mixed", "chase_bse_residuals_noalloc",
-                 "chase_bse_dgemm_sliced", "chase_bse_degrees", "chase_bse_eigh"]:
+                 "chase_bse_dgemm_sliced", "chase_bse_degrees", "chase_bse_eigh", "chase_bse_filter_cols"]:
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -235,6 +240,29 @@ def filter(A: torch.Tensor, B: torch.Tensor, W: torch.Tensor, degs, mu1: float, 
     _check(lib().chase_bse_filter(_ptr(A), _ptr(B), n, _ptr(W), k, d, mu1, mu_nevex, muN, _PREC[precision],
                                   ctypes.c_void_p(_stream(stream))), "chase_bse_filter")
     return W
+
+
+def filter_cols(A: torch.Tensor, B: torch.Tensor, W: torch.Tensor, degs, precs, mu1: float, mu_nevex: float,
+                muN: float, stream=None) -> torch.Tensor:
+    """chase_bse_filter_cols: the filter with a precision per column ("fp64" or a
+    tensor-core scheme name), in place on W (k, 2n); returns W."""
+    A = _mat(A, "A")
+    n = A.shape[0]
+    B = _mat(B, "B", n)
+    W = _block(W, "W", 2 * n)
+    k = W.shape[0]
+    if len(degs) != k or len(precs) != k:
+        raise ValueError("one degree and one precision per vector")
+    d = (ctypes.c_int32 * max(k, 1))(*[int(x) for x in degs])
+    p = (ctypes.c_int32 * max(k, 1))(*[_PREC[x] for x in precs])
+    _check(lib().chase_bse_filter_cols(_ptr(A), _ptr(B), n, _ptr(W), k, d, p, mu1, mu_nevex, muN,
+                                       ctypes.c_void_p(_stream(stream))), "chase_bse_filter_cols")
+    return W
+
+
+def set_wait_limit(ns: int) -> None:
+    """Bound (ns) of the cooperative kernels' grid-barrier waits; 0 = the default 2 s."""
+    lib().chase_bse_set_wait_limit(int(ns))
 
 
 def rayleigh_ritz(A: torch.Tensor, B: torch.Tensor, Q: torch.Tensor, stream=None):

@@ -58,6 +58,8 @@ int64_t chase_bse_launch_count(void) { return cb::launch_count(); }
 
 int64_t chase_bse_alloc_count(void) { return cb::alloc_count(); }
 
+void chase_bse_set_wait_limit(uint64_t ns) { cb::set_wait_limit_ns(ns); }
+
 int chase_bse_has_mixed(void) { return cb::mixed_available() ? 1 : 0; }
 
 void chase_bse_trim_memory(void) { cb::pool_trim(); }
@@ -73,6 +75,7 @@ const char* chase_bse_strerror(int status) {
     case CHASE_BSE_QR_FAILED: return "orthonormalisation failed";
     case CHASE_BSE_DEVICE_TIMEOUT: return "a bounded device-side wait gave up";
     case CHASE_BSE_UNSUPPORTED: return "not supported on this device";
+    case CHASE_BSE_NONFINITE: return "an input holds a NaN or an Inf";
     default: return "unknown status";
   }
 }
@@ -97,6 +100,31 @@ int chase_bse_filter(const void* A, const void* B, int64_t n, void* W, int64_t k
     std::vector<int> prec(k, precision == CHASE_BSE_FP64 ? 0 : 1);
     return cb::filter((const cplx*)A, (const cplx*)B, n, (cplx*)W, k, degs, prec.data(), mu1, mu_nevex, muN,
                       precision, nullptr, nullptr, (cudaStream_t)stream, nullptr);
+  })
+}
+
+int chase_bse_filter_cols(const void* A, const void* B, int64_t n, void* W, int64_t k, const int32_t* degs,
+                          const int32_t* precs, double mu1, double mu_nevex, double muN, void* stream) {
+  if (k == 0) return CHASE_BSE_OK;
+  if (!A || !B || !W || !degs || !precs || n < 1 || k < 0 || !(mu1 > 0) || !(mu_nevex > mu1) ||
+      !(muN > mu_nevex))
+    return CHASE_BSE_BAD_ARG;
+  int scheme = 0;
+  for (int64_t i = 0; i < k; ++i) {
+    if (degs[i] < 1) return CHASE_BSE_BAD_ARG;
+    const int p = precs[i];
+    if (p == CHASE_BSE_FP64) continue;
+    if (p != CHASE_BSE_MIXED_BF16X3 && p != CHASE_BSE_MIXED_BF16X6 && p != CHASE_BSE_MIXED_FP16X3)
+      return CHASE_BSE_BAD_ARG;
+    if (scheme != 0 && p != scheme) return CHASE_BSE_BAD_ARG;
+    scheme = p;
+  }
+  CB_GUARD({
+    std::vector<int> prec(k);
+    for (int64_t i = 0; i < k; ++i) prec[i] = precs[i] == CHASE_BSE_FP64 ? 0 : 1;
+    return cb::filter((const cplx*)A, (const cplx*)B, n, (cplx*)W, k, degs, prec.data(), mu1, mu_nevex, muN,
+                      scheme == 0 ? CHASE_BSE_MIXED_FP16X3 : scheme, nullptr, nullptr, (cudaStream_t)stream,
+                      nullptr);
   })
 }
 

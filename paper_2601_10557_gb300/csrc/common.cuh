@@ -71,6 +71,9 @@ void pool_trim();
 // Number of device allocations the library has requested (every one goes through
 // dalloc), for diagnostics and for the allocation-free entry point's tests.
 int64_t alloc_count();
+// Bound of the grid-barrier waits of the cooperative kernels (0: default 2 s).
+uint64_t wait_limit_ns();
+void set_wait_limit_ns(uint64_t ns);
 
 // Stream-ordered workspace: every buffer is released when the owner goes out
 // of scope (cudaFreeAsync on the same stream).

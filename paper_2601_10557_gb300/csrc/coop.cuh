@@ -9,13 +9,26 @@ namespace cb {
 // ------------------------------------------------------------ grid barrier
 // For kernels launched cooperatively (all CTAs co-resident): a counter plus a
 // generation word in global memory.  Every wait is bounded (2 s of
-// %globaltimer), after which the kernel records an error, and all CTAs leave
-// at their next barrier.  Data written by other CTAs before a barrier is read
+// %globaltimer by default, GridSync::limit_ns when set), after which the kernel
+// records an error, and all CTAs leave at their next barrier.  Data written by other CTAs before a barrier is read
 // with __ldcg (L2) after it.
 struct GridSync {
-  unsigned count;  // arrival word: its top bit flips once per completed barrier
-  unsigned gen;    // unused (kept zero)
+  unsigned count;                // arrival word: its top bit flips once per completed barrier
+  unsigned gen;                  // unused (kept zero)
+  unsigned long long limit_ns;   // bound of a wait; 0: the default of 2 s
 };
+
+// Bound of the grid-barrier waits set by chase_bse_set_wait_limit (0: default).
+uint64_t wait_limit_ns();
+
+// Zero a GridSync on the stream and set its wait bound.
+static inline cudaError_t gsync_init(GridSync* g, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(g, 0, sizeof(GridSync), s);
+  const unsigned long long lim = (unsigned long long)wait_limit_ns();
+  if (e == cudaSuccess && lim != 0)
+    e = cudaMemcpyAsync(&g->limit_ns, &lim, sizeof(lim), cudaMemcpyHostToDevice, s);
+  return e;
+}
 __device__ __forceinline__ unsigned long long gtimer_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -23,7 +36,7 @@ __device__ __forceinline__ unsigned long long gtimer_ns() {
 }
 // CTA 0 adds 2^31 - (gridDim.x - 1), every other CTA adds 1 (release), so the
 // top bit of the word flips exactly when the last CTA arrives; the waiters poll
-// it with acquire loads.  The wait is bounded: after 2 s, or once another CTA
+// it with acquire loads.  The wait is bounded: after the limit, or once another CTA
 // has recorded an error, the CTA records the error and returns false.
 __device__ inline bool grid_barrier(GridSync* gsync, int* err) {
   __shared__ int ok_sh;
@@ -34,14 +47,15 @@ __device__ inline bool grid_barrier(GridSync* gsync, int* err) {
     unsigned old, cur;
     __threadfence();  // the CTA's writes (ordered before by __syncthreads) become visible first
     asm volatile("atom.add.release.gpu.u32 %0, [%1], %2;" : "=r"(old) : "l"(&gsync->count), "r"(inc) : "memory");
+    const unsigned long long lim = gsync->limit_ns ? gsync->limit_ns : 2000000000ull;
     const unsigned long long t0 = gtimer_ns();
     unsigned it = 0;
     while (true) {
       asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(cur) : "l"(&gsync->count) : "memory");
       if (((old ^ cur) & 0x80000000u) != 0) break;
-      if ((++it & 63) == 0) {
+      if ((++it & 7) == 0) {
         if (*(volatile int*)err) { ok_sh = 0; break; }
-        if (gtimer_ns() - t0 > 2000000000ull) {
+        if (gtimer_ns() - t0 > lim) {
           atomicExch(err, 1);
           ok_sh = 0;
           break;

@@ -247,7 +247,7 @@ int cholesky(cplx* G, int64_t k, int* info_dev, int* info_host, cudaStream_t s, 
     int* err = nullptr;
     CB_CUDA(dalloc(&gsync, sizeof(GridSync), s));
     CB_CUDA(dalloc(&err, sizeof(int), s));
-    CB_CUDA(cudaMemsetAsync(gsync, 0, sizeof(GridSync), s));
+    CB_CUDA(gsync_init(gsync, s));
     CB_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
     int64_t kk = k;
     void* args[] = {&G, &kk, &info_dev, &gsync, &err};
@@ -820,7 +820,7 @@ int jacobi_eigh(cplx* G, int64_t k, cplx* V, double* theta, cplx* rot, double* r
       CB_CUDA(dalloc(&cnt, sizeof(int), s));
       CB_CUDA(dalloc(&G2, sizeof(cplx) * k * k, s));
       CB_CUDA(dalloc(&rots, sizeof(Rot) * (size_t)(k - 1) * half + sizeof(Rot), s));
-      CB_CUDA(cudaMemsetAsync(gsync, 0, sizeof(GridSync), s));
+      CB_CUDA(gsync_init(gsync, s));
       CB_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
       int herr = 0, status = CHASE_BSE_OK;
       int hc[2] = {1, 1};
@@ -1281,6 +1281,26 @@ int normalize_and_residual(cplx* W, const cplx* SHW, const double* ritz, int64_t
   normalize_and_residual_kernel<<<(unsigned)m, 256, 0, s>>>(W, SHW, ritz, n, R);
   count_launch();
   CB_LAUNCH();
+  return CHASE_BSE_OK;
+}
+
+__global__ void count_nonfinite_kernel(const cplx* X, int64_t total, int* count) {
+  int local = 0;
+  GRID_STRIDE(i, total) {
+    const cplx v = X[i];
+    if (!isfinite(v.x) || !isfinite(v.y)) ++local;
+  }
+  if (local) atomicAdd(count, local);
+}
+int count_nonfinite(const cplx* X, int64_t total, int* count_dev, int* count_host, cudaStream_t s) {
+  CB_CUDA(cudaMemsetAsync(count_dev, 0, sizeof(int), s));
+  if (total > 0) {
+    count_nonfinite_kernel<<<gs(total), 256, 0, s>>>(X, total, count_dev);
+    count_launch();
+    CB_LAUNCH();
+  }
+  CB_CUDA(cudaMemcpyAsync(count_host, count_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CB_CUDA(cudaStreamSynchronize(s));
   return CHASE_BSE_OK;
 }
 

@@ -86,6 +86,8 @@ int normalize_cols(cplx* X, int64_t rows, int64_t m, cudaStream_t s);
 int normalize_and_residual(cplx* W, const cplx* SHW, const double* ritz, int64_t n, int64_t m, cplx* R,
                            cudaStream_t s);
 int set_identity(cplx* M, int64_t k, cudaStream_t s);
+// *count_host = the number of entries of X (total) with a NaN or Inf part
+int count_nonfinite(const cplx* X, int64_t total, int* count_dev, int* count_host, cudaStream_t s);
 // R[:, j] = HV[:, j] - lam[j] V[:, j] (n2 x m; lam device)
 int residual_from_hv(const cplx* HV, const cplx* V, const double* lam, int64_t n2, int64_t m, cplx* R,
                      cudaStream_t s);

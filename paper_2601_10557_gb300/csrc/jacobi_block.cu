@@ -382,7 +382,7 @@ static int run(const cplx* G, int64_t k, cplx* V, double* theta, double t, doubl
   CB_TRY(ws.alloc(&err, 1));
   CB_TRY(ws.alloc(&cnt, 1));
   CB_TRY(ws.alloc(&red, 2));
-  CB_CUDA(cudaMemsetAsync(gsync, 0, sizeof(GridSync), s));
+  CB_CUDA(gsync_init(gsync, s));
   CB_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
   // scale G to ||G||_F in [1/2, 1): exact, and FP32 keeps its range
   CB_TRY(offdiag_norms(G, k, red, s));

@@ -21,6 +21,10 @@ std::mutex g_pool_mu;
 cudaMemPool_t g_pools[64] = {};
 }  // namespace
 
+static std::atomic<uint64_t> g_wait_limit{0};
+uint64_t wait_limit_ns() { return g_wait_limit.load(std::memory_order_relaxed); }
+void set_wait_limit_ns(uint64_t ns) { g_wait_limit.store(ns, std::memory_order_relaxed); }
+
 static std::atomic<int64_t> g_allocs{0};
 int64_t alloc_count() { return g_allocs.load(std::memory_order_relaxed); }
 
@@ -822,6 +826,25 @@ int solve(const cplx* A, const cplx* B, int64_t n, int64_t nev, int64_t nex, int
   if (mixed && !mixed_available()) return CHASE_BSE_UNSUPPORTED;
   cudaStream_t s = (cudaStream_t)o.stream;
   const int64_t n2 = 2 * n, nevex = nev + nex;
+  {  // inputs with a NaN or an Inf: a defined status, nothing computed
+    Workspace cws(s);
+    int* cnt;
+    CB_TRY(cws.alloc(&cnt, 1));
+    int bad = 0, c = 0;
+    CB_TRY(count_nonfinite(A, n * n, cnt, &c, s));
+    bad += c;
+    CB_TRY(count_nonfinite(B, n * n, cnt, &c, s));
+    bad += c;
+    if (o.W0) {
+      CB_TRY(count_nonfinite((const cplx*)o.W0, n2 * nevex, cnt, &c, s));
+      bad += c;
+    }
+    if (o.V0) {
+      CB_TRY(count_nonfinite((const cplx*)o.V0, n2 * o.lanczos_vecs, cnt, &c, s));
+      bad += c;
+    }
+    if (bad) return CHASE_BSE_NONFINITE;
+  }
   chase_bse_stats st{};
   st.size = sizeof(st);
   auto t_start = std::chrono::steady_clock::now();

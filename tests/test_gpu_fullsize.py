@@ -16,7 +16,10 @@ GPU output with the plain FP64 formulas:
   lambda_1 it is 0;
 * the whole filter block against the oracle filter (element by element);
 * the eigenvalue gradient against the oracle's formula on the same vectors and
-  against central finite differences of the solve.
+  against central finite differences of the solve on 32 random directions;
+* at n = 16384 the same properties, the inertia from the Schur complement of the
+  pencil on the device; at n = 4096 with real A and B, lambda^2 against the
+  eigenvalues of (A - B)(A + B).
 """
 import numpy as np
 import pytest
@@ -144,7 +147,7 @@ def test_c2_mixed_solve_properties(pkg, c2):
 def test_c4_gradient_fullsize(pkg):
     """n = 8192, nev = 100, nex = 40: the adjoint kernel against the oracle's formula
     on the same eigenvectors, and against central differences (h = 1e-6) of the solve
-    along dA = I and along a random hermitian / complex-symmetric direction."""
+    along dA = I and 32 random hermitian / complex-symmetric directions."""
     if not pkg.has_mixed():
         pytest.fail("tensor-core filter not available on this device")
     wl = bi.WORKLOADS["n8192grad"]
@@ -164,20 +167,114 @@ def test_c4_gradient_fullsize(pkg):
     assert rel_fro(gB, rB) < 1e-12
     np.testing.assert_allclose(gA, gA.conj().T, atol=1e-12 * np.abs(gA).max())
     np.testing.assert_allclose(gB, gB.T, atol=1e-12 * np.abs(gB).max())
+    # central differences (h = 1e-6) of the solve on 32 random directions (the
+    # configuration's count): dA hermitian and dB complex symmetric, Wigner-scaled
+    # (entries ~ 1/sqrt(n), ||dA||_2 ~ 2) so that h ||dA|| stays far below the eigenvalue
+    # gaps of the planted spectrum, plus dA = I (which perturbs H by S); each perturbed
+    # solve starts from the converged eigenvectors (a warm restart)
     rng = np.random.default_rng(5)
     h = 1e-6
-    E = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
-    F = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
-    # dA = I perturbs H by S, which couples eigenpairs i != j only through
-    # (S v_i)^* S v_j = v_i^* v_j = 2 y_i^* y_j (S-orthogonality: x_i^* x_j = y_i^* y_j),
-    # small because the lower halves are O(beta); the random direction is
-    # Wigner-scaled (entries ~ 1/sqrt(n), ||dA||_2 ~ 2) so that h ||dA|| stays far
-    # below the eigenvalue gaps of the planted spectrum
-    dirs = [(np.eye(n, dtype=complex), np.zeros((n, n), dtype=complex)),
-            ((E + E.conj().T) / (2 * np.sqrt(n)), (F + F.T) / (2 * np.sqrt(n)))]
+    # the solver scales the start block's lower half by gamma = 1e-3 (Section 4.6): the
+    # converged vectors' lower halves are divided by it beforehand
+    Vc = Vt.cpu().numpy().copy()
+    Vc[:, n:] /= 1e-3
+    W0w = np.concatenate([Vc, W0[nev:]], axis=0)
+    kw_w = dict(kw, W0=to_dev(W0w), deg_min=8)
+    dirs = [(np.eye(n, dtype=complex), np.zeros((n, n), dtype=complex))]
+    for _ in range(32):
+        E = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+        F = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+        dirs.append(((E + E.conj().T) / (2 * np.sqrt(n)), (F + F.T) / (2 * np.sqrt(n))))
+    fds, ans = [], []
     for dA, dB in dirs:
-        lp, _, _ = pkg.solve(to_dev(P.A + h * dA), to_dev(P.B + h * dB), nev, nex, wl["deg"], wl["tol"], **kw)
-        lm, _, _ = pkg.solve(to_dev(P.A - h * dA), to_dev(P.B - h * dB), nev, nex, wl["deg"], wl["tol"], **kw)
-        fd = float(np.dot(w, (lp - lm).cpu().numpy()) / (2 * h))
-        an = float(np.real(np.sum(gA.conj() * dA) + np.sum(gB.conj() * dB)))
-        assert abs(fd - an) <= 1e-6 * abs(an), (fd, an)
+        lp, _, _ = pkg.solve(to_dev(P.A + h * dA), to_dev(P.B + h * dB), nev, nex, wl["deg"], wl["tol"], **kw_w)
+        lm, _, _ = pkg.solve(to_dev(P.A - h * dA), to_dev(P.B - h * dB), nev, nex, wl["deg"], wl["tol"], **kw_w)
+        fds.append(float(np.dot(w, (lp - lm).cpu().numpy()) / (2 * h)))
+        ans.append(float(np.real(np.sum(gA.conj() * dA) + np.sum(gB.conj() * dB))))
+    fds, ans = np.array(fds), np.array(ans)
+    # dA = I on its own; the random directions as one vector of directional derivatives (a
+    # random direction's derivative sum_i w_i dlambda_i can be near zero: its own relative
+    # error would measure the cancellation, not the gradient)
+    assert abs(fds[0] - ans[0]) <= 1e-6 * abs(ans[0]), (fds[0], ans[0])
+    rel = np.linalg.norm(fds[1:] - ans[1:]) / np.linalg.norm(ans[1:])
+    assert rel <= 1e-6, (rel, np.abs(fds[1:] - ans[1:]).max(), np.abs(ans[1:]).min())
+
+
+def _hv_torch(A, B, V):
+    """H V on the device in FP64 (torch products): V (2n x m)."""
+    n = A.shape[0]
+    X, Y = V[:n], V[n:]
+    return torch.cat([A @ X + B @ Y, -(B.conj() @ X) - A.conj() @ Y], dim=0)
+
+
+def _negative_count_schur(A, B, sigma):
+    """Eigenvalues of H in (0, sigma) for the definite pencil (S H, S): the negative
+    eigenvalues of S H - sigma S = [[A - sigma, B], [conj(B), conj(A) + sigma]].  Its
+    lower-right block conj(A) + sigma I is positive definite (A is), so by Sylvester's law
+    of inertia the count is that of the Schur complement
+    M = A - sigma I - B (conj(A) + sigma I)^-1 conj(B) (torch FP64 on the device)."""
+    n = A.shape[0]
+    I = torch.eye(n, dtype=A.dtype, device=A.device)
+    L = torch.linalg.cholesky(A.conj() + sigma * I)
+    Z = torch.cholesky_solve(B.conj(), L)
+    M = A - sigma * I - B @ Z
+    M = 0.5 * (M + M.conj().T)
+    ev = torch.linalg.eigvalsh(M)
+    return int((ev < 0).sum().item())
+
+
+def test_c3_mixed_solve_properties(pkg):
+    """n = 16384 (H 32768), nev 1000, nex 300, degrees 8-36, tol 1e-10, the gapband
+    spectrum (the benchmark's configuration): residuals against the norm bound,
+    lambda = the S-Rayleigh quotient of its vector, completeness by the inertia of the
+    Schur complement just above lambda_nev (nev distinct eigenpairs and exactly nev
+    eigenvalues in (0, lambda_nev] leave none out, below lambda_1 included)."""
+    if not pkg.has_mixed():
+        pytest.fail("tensor-core filter not available on this device")
+    wl = bi.WORKLOADS["n16384"]
+    n, nev, nex, tol = wl["n"], wl["nev"], wl["nex"], wl["tol"]
+    dev = torch.device("cuda:0")
+    A, B, d = bi.make_problem_device(n, 0, wl["spec"], wl["beta"], device=dev)
+    W0, V0 = bi.start_block(n, nev + nex, 0), bi.lanczos_starts(n, 4, 0)
+    lam, V, st = pkg.solve(A, B, nev, nex, wl["deg"], tol, precision="mixed", W0=to_dev(W0), V0=to_dev(V0),
+                           deg_min=wl["deg_min"], deg_max=wl["deg_max"], maxiter=40)
+    assert st["converged"] == nev
+    lam_h = lam.cpu().numpy()
+    assert np.all(np.diff(lam_h) > 0) and lam_h[0] > 0
+    Vt = V.T  # 2n x nev
+    # ||H||_2 <= ||A||_2 + ||B||_2 = max(d) + beta min(d) (A's eigenvalues are d up to
+    # the assembly's FP32 rounding, ~1e-6 ||A||: a 1e-5 margin)
+    hnorm = (d.max() + wl["beta"] * d.min()) * (1 + 1e-5)
+    worst_res, worst_rq = 0.0, 0.0
+    for c0 in range(0, nev, 250):
+        Vb = Vt[:, c0:c0 + 250]
+        lb = lam[c0:c0 + 250]
+        HV = _hv_torch(A, B, Vb)
+        res = torch.linalg.vector_norm(HV - Vb * lb[None, :], dim=0)
+        worst_res = max(worst_res, float(res.max()))
+        SV = torch.cat([Vb[:n], -Vb[n:]], dim=0)
+        rq = torch.real(torch.sum(SV.conj() * HV, dim=0) / torch.sum(SV.conj() * Vb, dim=0))
+        worst_rq = max(worst_rq, float(((rq - lb).abs() / lb).max()))
+    assert worst_res <= tol * hnorm, worst_res / hnorm
+    assert worst_rq < 1e-12, worst_rq
+    assert _negative_count_schur(A, B, float(lam_h[-1]) * (1 + 1e-9)) == nev
+
+
+def test_c2_real_variant_squared_spectrum(pkg):
+    """n = 4096 with real symmetric A and B, mixed precision: lambda^2 are the
+    eigenvalues of (A - B)(A + B); with A + B = L L^T (positive definite for a definite
+    problem) they are those of the symmetric L^T (A - B) L (host LAPACK)."""
+    if not pkg.has_mixed():
+        pytest.fail("tensor-core filter not available on this device")
+    import scipy.linalg as sl
+    wl = bi.WORKLOADS["n4096"]
+    n, nev, nex, tol = wl["n"], wl["nev"], wl["nex"], wl["tol"]
+    P = bi.make_problem(n, seed=2, spec=wl["spec"], beta=wl["beta"], real=True)
+    W0, V0 = bi.start_block(n, nev + nex, 2), bi.lanczos_starts(n, 4, 2)
+    lam, V, st = pkg.solve(to_dev(P.A), to_dev(P.B), nev, nex, wl["deg"], tol, precision="mixed", W0=to_dev(W0),
+                           V0=to_dev(V0), deg_min=wl["deg_min"], deg_max=wl["deg_max"], maxiter=40)
+    assert st["converged"] == nev
+    Ar, Br = P.A.real, P.B.real
+    L = sl.cholesky(Ar + Br, lower=True)
+    mu = sl.eigh(L.T @ (Ar - Br) @ L, eigvals_only=True, subset_by_index=[0, nev - 1])
+    np.testing.assert_allclose(lam.cpu().numpy() ** 2, mu, rtol=2e-10)

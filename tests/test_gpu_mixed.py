@@ -99,3 +99,40 @@ def test_filter_tensor_core_column_scales(pkg, scheme):
     got = W.cpu().numpy().T
     for j in range(k):
         assert rel_fro(got[:, j], Y[:, j]) < TOL[scheme], j
+
+
+def test_filter_precision_groups(pkg):
+    """The precision groups of a mixed solve in one filter call (chase_bse_filter_cols):
+    FP64 columns on the FP64 filter (1e-12 against the oracle), the others on the
+    tensor-core filter (1e-5), with ragged degrees in both groups."""
+    n, k = 300, 24
+    P = bi.make_problem(n, seed=9)
+    A, B = problem_on_device(P)
+    W0 = bi.start_block(n, k, 9)
+    rng = np.random.default_rng(9)
+    degs = rng.integers(1, 7, size=k)
+    precs = ["fp64" if i % 3 == 0 else "fp16x3" for i in range(k)]
+    mu1, mune, muN = _mus(P)
+    W = to_dev(W0)
+    pkg.filter_cols(A, B, W, degs, precs, mu1, mune, muN)
+    Y = chebyshev.chebyshev_filter(P.A, P.B, W0.T, degs, mu1, mune, muN)
+    got = W.cpu().numpy().T
+    for j in range(k):
+        err = rel_fro(got[:, j], Y[:, j])
+        assert err < (1e-12 if precs[j] == "fp64" else TOL["fp16x3"]), (j, precs[j], err)
+
+
+def test_solve_mixed_moves_stalled_columns_to_fp64(pkg):
+    """With switch_tol = 1 every column whose residual stops decreasing moves to the FP64
+    filter (the precision groups inside the solve's filter calls); the result still
+    matches the dense oracle."""
+    n, nev, nex = 64, 8, 6
+    P = bi.make_problem(n, seed=13)
+    A, B = problem_on_device(P)
+    W0, V0 = starts(n, nev + nex, 13)
+    lam, V, st = pkg.solve(A, B, nev, nex, 4, 1e-10, W0=to_dev(W0), V0=to_dev(V0), deg_min=2, deg_max=6,
+                           precision="mixed", switch_tol=1.0, maxiter=60)
+    ref, _ = dense.smallest_positive(P.A, P.B, nev)
+    np.testing.assert_allclose(lam.cpu().numpy(), ref, rtol=1e-10)
+    assert st["filter_flops_fp64"] > 0.0
+    assert st["filter_flops_fp64"] < st["filter_flops"]
