@@ -347,7 +347,7 @@ def degrees(ritz, res, prev_res, prev_deg, tol: float, mu_nevex: float, muN: flo
     return out.tolist()
 
 
-EIGH_METHODS = {"jacobi": 0, "mixed": 1, "block": 2, "block32": 3}
+EIGH_METHODS = {"jacobi": 0, "mixed": 1, "block": 2}
 
 
 def eigh(G: torch.Tensor, method: str = "mixed", thr: float = 2e-16, stream=None):

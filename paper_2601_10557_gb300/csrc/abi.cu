@@ -42,7 +42,6 @@ static int eigh_impl(const cplx* G, int64_t k, double* theta, cplx* V, int metho
   int st = CHASE_BSE_OK;
   if (method == 0) st = cb::jacobi_eigh(Gc, k, V, theta, rot, red, 40, &sw, s, thr);
   else if (method == 1) st = cb::jacobi_eigh_mixed(Gc, k, V, theta, rot, red, &sw32, &sw, s, thr);
-  else if (method == 3) st = cb::jacobi_block(Gc, k, V, theta, true, 2e-6, 1e-8, 30, &sw, s);
   else st = cb::jacobi_block(Gc, k, V, theta, false, thr, 0.5 * thr, 40, &sw, s);
   if (cb::verbose()) fprintf(stderr, "[chase_bse] eigh method %d k %ld sweeps %d (FP32 %d)\n", method, (long)k, sw, sw32);
   if (st != CHASE_BSE_OK) return st;
@@ -158,7 +157,7 @@ int chase_bse_degrees(const double* ritz, const double* res, const double* prev_
 }
 
 int chase_bse_eigh(const void* G, int64_t k, double* theta, void* V, int32_t method, double thr, void* stream) {
-  if (!G || !theta || !V || k < 2 || (k % 2) != 0 || method < 0 || method > 3 || !(thr >= 2e-16))
+  if (!G || !theta || !V || k < 2 || (k % 2) != 0 || method < 0 || method > 2 || !(thr >= 2e-16))
     return CHASE_BSE_BAD_ARG;
   if (method == 1 && !cb::mixed_available()) return CHASE_BSE_UNSUPPORTED;
   CB_GUARD(return eigh_impl((const cplx*)G, k, theta, (cplx*)V, method, thr, (cudaStream_t)stream);)
