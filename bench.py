@@ -396,6 +396,8 @@ def main():
     barrier()
     clocks.start()
     l0 = pkg.launch_count()
+    gemm_kind = "fp64" if precision == "fp64" else "tensor"
+    pkg.gemm_timer(True)  # CUDA events around every filter GEMM launch of the timed steps
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
@@ -416,6 +418,8 @@ def main():
     barrier()
     clocks.stop()
     launches = pkg.launch_count() - l0
+    g_ms, g_flops, g_n = pkg.gemm_time(gemm_kind)
+    pkg.gemm_timer(False)
     total_ms = ev0.elapsed_time(ev1)
     tts = total_ms / 1e3 / args.steps
 
@@ -464,10 +468,13 @@ def main():
     e2e_val = whole_job_tflops(dist, efl, e2e_ms, dev)
     del hA, hB, out_gA, out_gB
 
-    # ---- roofline of the dominant kernel, the filter GEMM: its average launch duration
-    # from two filter calls over all nev + nex columns that differ only in the degree
-    # (d1 and d2 H^2 steps: 2 (d2 - d1) more launches of the same shape; the split of P,
-    # the packing and the final combination, the same in both, cancel)
+    # ---- roofline of the dominant kernel, the filter GEMM: the algorithmic flops of its
+    # launches in the timed steps (32 n^2 k for k vectors) over their summed device time
+    # (a CUDA event pair around each launch, recorded by the library on the launch's
+    # stream).  Cross-check on full-width launches: two filter calls over all nev + nex
+    # columns that differ only in the degree (d1 and d2 H^2 steps: 2 (d2 - d1) more
+    # launches of the same shape; the split of P, the packing and the final combination,
+    # the same in both, cancel)
     d1, d2 = (2, 6) if n >= 16384 else (4, 20)
 
     def filter_ms(deg):
@@ -487,9 +494,12 @@ def main():
     t2 = min(filter_ms(d2) for _ in range(2))
     rl = (pkg.launch_count() - rl0) // 4
     gemm_launches = 2 * (d2 - d1)
-    per_launch_ms = (t2 - t1) / gemm_launches
-    flops_per_launch = 32.0 * n * n * nevex
-    achieved = flops_per_launch / (per_launch_ms / 1e3) / 1e12
+    full_launch_ms = (t2 - t1) / gemm_launches
+    full_flops = 32.0 * n * n * nevex
+    full_achieved = full_flops / (full_launch_ms / 1e3) / 1e12
+    per_launch_ms = g_ms / max(g_n, 1)
+    flops_per_launch = g_flops / max(g_n, 1)
+    achieved = g_flops / (g_ms / 1e3) / 1e12 if g_ms > 0 else 0.0
     peaks, peak_src = load_peaks()
     if precision == "fp64":
         peak = peaks["bf16_tflops"] * NOMINAL["fp64"] / NOMINAL["bf16"]
@@ -501,15 +511,27 @@ def main():
         peak = peaks["bf16_tflops"] / 3.0
         peak_note = (f"{peak_src} bf16 burst / 3 (three 16-bit products per FP32-accurate product; "
                      "the nominal FP16 and BF16 dense rates are equal)")
-    traffic, traffic_src = traffic_for(args.workload) if precision in ("mixed", "fp16x3") else (None, "n/a")
+    traffic_full, traffic_src = traffic_for(args.workload) if precision in ("mixed", "fp16x3") else (None, "n/a")
+    traffic = None
+    if traffic_full is not None:
+        # captured on full-width launches (k = nev + nex); scaled to the timed launches'
+        # average width by the units processed (the operand re-reads grow with the
+        # number of column tiles)
+        traffic = traffic_full * flops_per_launch / full_flops
+        traffic_src += f"; full-width launch {traffic_full:.4g} B scaled by the average width {flops_per_launch / full_flops:.3f}"
     roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": traffic, "traffic_source": traffic_src,
             "kernel": "hop_kernel (FP64 DFMA)" if precision == "fp64" else "tc_hop_kernel (tcgen05 filter GEMM)",
-            "peak_source": peak_note, "launch_ms": per_launch_ms,
-            "method": f"(t(degree {d2}) - t(degree {d1})) / {gemm_launches} launches, filter calls over "
-                      f"{nevex} columns, CUDA events, best of 2",
-            "launches_per_call_avg": rl, "flops_per_launch": flops_per_launch,
-            "filter_call_ms": {str(d1): t1, str(d2): t2}}
+            "peak_source": peak_note, "launch_ms": per_launch_ms, "launches": g_n,
+            "flops_per_launch": flops_per_launch,
+            "method": "sum of 32 n^2 k over the filter GEMM launches of the timed steps / their summed "
+                      "device time (a CUDA event pair around each launch on its stream)",
+            "full_width_check": {
+                "achieved": full_achieved, "frac": full_achieved / peak, "launch_ms": full_launch_ms,
+                "flops_per_launch": full_flops,
+                "method": f"(t(degree {d2}) - t(degree {d1})) / {gemm_launches} launches, filter calls over "
+                          f"{nevex} columns, CUDA events, best of 2",
+                "launches_per_call_avg": rl, "filter_call_ms": {str(d1): t1, str(d2): t2}}}
 
     # ---- FP64 comparison
     fp64 = None

@@ -294,6 +294,21 @@ void chase_bse_set_wait_limit(uint64_t ns);
  * was loaded, summed over all threads. */
 int64_t chase_bse_alloc_count(void);
 
+/* Diagnostics (no counterpart in the paper): device time of the filter's H
+ * applications (the step of Algorithm 2 that applies H to a block of vectors).
+ * chase_bse_gemm_timer(1) clears the record and starts bracketing every such launch
+ * made afterwards, by any thread, with a pair of CUDA events recorded on the launch's
+ * stream: kind 0 the tensor-core GEMM of a mixed-precision filter, kind 1 the FP64 H
+ * application (with its K-split reduction where one is used).  chase_bse_gemm_timer(0)
+ * stops and clears.  chase_bse_gemm_time waits for the recorded launches of `kind`
+ * (blocking the host), writes into *total_ms the sum of their event-to-event device
+ * times in milliseconds, into *flops the sum of their algorithmic flops (32 n^2 k for
+ * k vectors: H is 2n x 2n complex, 8 real flops per complex multiply-add) and into
+ * *launches their number, and clears that kind's record.  Returns BAD_ARG for a NULL
+ * pointer or a kind other than 0 or 1. */
+void chase_bse_gemm_timer(int32_t enable);
+int chase_bse_gemm_time(int32_t kind, double* total_ms, double* flops, int64_t* launches);
+
 #ifdef __cplusplus
 }
 #endif

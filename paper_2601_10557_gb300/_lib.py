@@ -88,7 +88,7 @@ EXPORTS = ["chase_bse_solve", "chase_bse_filter", "chase_bse_rr", "chase_bse_res
            "chase_bse_strerror", "chase_bse_version", "chase_bse_has_mixed", "chase_bse_launch_count",
            "chase_bse_residuals_noalloc", "chase_bse_dgemm_sliced", "chase_bse_trim_memory",
            "chase_bse_alloc_count", "chase_bse_degrees", "chase_bse_eigh", "chase_bse_filter_cols",
-           "chase_bse_set_wait_limit"]
+           "chase_bse_set_wait_limit", "chase_bse_gemm_timer", "chase_bse_gemm_time"]
 
 # 2n * k limit of chase_bse_residuals_noalloc (its fixed device scratch, complex128 entries)
 NOALLOC_MAX_ENTRIES = 1 << 19
@@ -118,6 +118,11 @@ def lib() -> ctypes.CDLL:
                                         ctypes.POINTER(ctypes.c_int32), dbl, dbl, dbl, vp]
     L.chase_bse_set_wait_limit.argtypes = [ctypes.c_uint64]
     L.chase_bse_set_wait_limit.restype = None
+    L.chase_bse_gemm_timer.argtypes = [ctypes.c_int32]
+    L.chase_bse_gemm_timer.restype = None
+    L.chase_bse_gemm_time.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
+    L.chase_bse_gemm_time.restype = ctypes.c_int
     L.chase_bse_strerror.argtypes = [ctypes.c_int]
     L.chase_bse_strerror.restype = ctypes.c_char_p
     L.chase_bse_launch_count.restype = ctypes.c_int64
@@ -263,6 +268,25 @@ def filter_cols(A: torch.Tensor, B: torch.Tensor, W: torch.Tensor, degs, precs, 
 def set_wait_limit(ns: int) -> None:
     """Bound (ns) of the cooperative kernels' grid-barrier waits; 0 = the default 2 s."""
     lib().chase_bse_set_wait_limit(int(ns))
+
+
+def gemm_timer(enable: bool) -> None:
+    """chase_bse_gemm_timer: start (True) or stop (False) the event record of the
+    filter's H applications; both clear it."""
+    lib().chase_bse_gemm_timer(1 if enable else 0)
+
+
+def gemm_time(kind: str = "tensor"):
+    """chase_bse_gemm_time: (total device ms, total algorithmic flops, launches) of the
+    recorded H applications of ``kind`` ("tensor": the tensor-core filter GEMM, "fp64":
+    the FP64 H application) since the record was started or last read; clears that
+    kind's record."""
+    ms = ctypes.c_double(0.0)
+    fl = ctypes.c_double(0.0)
+    cnt = ctypes.c_int64(0)
+    _check(lib().chase_bse_gemm_time({"tensor": 0, "fp64": 1}[kind], ctypes.byref(ms), ctypes.byref(fl),
+                                     ctypes.byref(cnt)), "chase_bse_gemm_time")
+    return float(ms.value), float(fl.value), int(cnt.value)
 
 
 def rayleigh_ritz(A: torch.Tensor, B: torch.Tensor, Q: torch.Tensor, stream=None):

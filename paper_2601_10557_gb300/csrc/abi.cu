@@ -59,6 +59,13 @@ int64_t chase_bse_alloc_count(void) { return cb::alloc_count(); }
 
 void chase_bse_set_wait_limit(uint64_t ns) { cb::set_wait_limit_ns(ns); }
 
+void chase_bse_gemm_timer(int32_t enable) { cb::timer_enable(enable != 0); }
+
+int chase_bse_gemm_time(int32_t kind, double* total_ms, double* flops, int64_t* launches) {
+  if (!total_ms || !flops || !launches || kind < 0 || kind > 1) return CHASE_BSE_BAD_ARG;
+  return cb::timer_read(kind, total_ms, flops, launches);
+}
+
 int chase_bse_has_mixed(void) { return cb::mixed_available() ? 1 : 0; }
 
 void chase_bse_trim_memory(void) { cb::pool_trim(); }

@@ -56,6 +56,15 @@ bool verbose();
 void count_launch();
 int64_t launch_count();
 
+// Device-time record of the filter's H applications (diagnostics): kind 0 the
+// tensor-core filter GEMM, kind 1 the FP64 H application, each with its algorithmic
+// flops.  timer_begin returns an id (-1 while the record is off) that timer_end
+// closes after the launch.
+int64_t timer_begin(int kind, double flops, cudaStream_t s);
+void timer_end(int64_t id, cudaStream_t s);
+void timer_enable(bool on);
+int timer_read(int kind, double* ms, double* flops, int64_t* launches);
+
 inline unsigned cdiv(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
 
 // Stream-ordered device allocation from the library's memory pool (one per

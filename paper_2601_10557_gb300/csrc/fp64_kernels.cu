@@ -167,7 +167,9 @@ static int hop_launch(const HopArgs& a, cudaStream_t s) {
   const int64_t nsplit = a.no_split ? 1 : split_count(tiles, n2, 256);
   if (nsplit <= 1) {
     dim3 grid(cdiv(a.n, BM), cdiv(a.k, BNW));
+    const int64_t tid = timer_begin(1, 32.0 * (double)a.n * (double)a.n * (double)a.k, s);
     hop_kernel<BM, BNW, TM, TNW, 16><<<grid, (BM / TM) * (BNW / TNW), 0, s>>>(a, nullptr, 0);
+    timer_end(tid, s);
     count_launch();
     CB_LAUNCH();
     return CHASE_BSE_OK;
@@ -177,11 +179,14 @@ static int hop_launch(const HopArgs& a, cudaStream_t s) {
   cplx* part = nullptr;
   CB_CUDA(dalloc(&part, sizeof(cplx) * ns * 2 * a.n * a.k, s));
   dim3 grid(cdiv(a.n, BM), cdiv(a.k, BNW), (unsigned)ns);
+  // the split product and its reduction: one H application
+  const int64_t tid = timer_begin(1, 32.0 * (double)a.n * (double)a.n * (double)a.k, s);
   hop_kernel<BM, BNW, TM, TNW, 16><<<grid, (BM / TM) * (BNW / TNW), 0, s>>>(a, part, kchunk);
   count_launch();
   const int64_t total = a.n * a.k;
   const unsigned rb = (unsigned)((total + 255) / 256 < 8192 ? (total + 255) / 256 : 8192);
   hop_reduce_kernel<BM, BNW><<<rb, 256, 0, s>>>(a, part, (int)ns);
+  timer_end(tid, s);
   count_launch();
   cudaError_t e = cudaGetLastError();
   cudaFreeAsync(part, s);

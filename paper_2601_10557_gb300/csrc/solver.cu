@@ -66,6 +66,116 @@ static std::atomic<int64_t> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
+// Device-time record of the filter's H applications (diagnostics).  While it is
+// on, every launch of the tensor-core filter GEMM (kind 0) and of the FP64 H
+// application (kind 1) is bracketed by a pair of CUDA events on its stream.
+// Completed pairs are harvested without blocking at the next bracket, so the
+// record holds at most a few launches in flight.
+namespace {
+struct TimerPair {
+  cudaEvent_t a, b;
+  int kind;
+  int64_t id;
+  double flops;
+  bool closed;  // the end event has been recorded
+};
+std::mutex g_timer_mu;
+bool g_timer_on = false;
+std::vector<TimerPair> g_timer_open;   // recorded, not yet harvested
+std::vector<TimerPair> g_timer_spare;  // harvested, events reusable
+double g_timer_ms[2] = {0.0, 0.0};
+double g_timer_flops[2] = {0.0, 0.0};
+int64_t g_timer_n[2] = {0, 0};
+int64_t g_timer_next = 0;
+
+void timer_harvest(bool wait) {
+  size_t keep = 0;
+  for (size_t i = 0; i < g_timer_open.size(); ++i) {
+    TimerPair& t = g_timer_open[i];
+    if (!t.closed) {
+      g_timer_open[keep++] = t;
+      continue;
+    }
+    cudaError_t q = wait ? cudaEventSynchronize(t.b) : cudaEventQuery(t.b);
+    if (q == cudaSuccess) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) {
+        g_timer_ms[t.kind] += ms;
+        g_timer_flops[t.kind] += t.flops;
+        g_timer_n[t.kind] += 1;
+      }
+      g_timer_spare.push_back(t);
+    } else {
+      if (q != cudaErrorNotReady) cudaGetLastError();
+      g_timer_open[keep++] = t;
+    }
+  }
+  g_timer_open.resize(keep);
+}
+}  // namespace
+
+int64_t timer_begin(int kind, double flops, cudaStream_t s) {
+  std::lock_guard<std::mutex> lock(g_timer_mu);
+  if (!g_timer_on) return -1;
+  timer_harvest(false);
+  TimerPair t{};
+  if (!g_timer_spare.empty()) {
+    t = g_timer_spare.back();
+    g_timer_spare.pop_back();
+  } else if (cudaEventCreate(&t.a) != cudaSuccess || cudaEventCreate(&t.b) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  t.kind = kind;
+  t.flops = flops;
+  t.id = g_timer_next++;
+  t.closed = false;
+  if (cudaEventRecord(t.a, s) != cudaSuccess) {
+    cudaGetLastError();
+    g_timer_spare.push_back(t);
+    return -1;
+  }
+  g_timer_open.push_back(t);
+  return t.id;
+}
+
+void timer_end(int64_t id, cudaStream_t s) {
+  if (id < 0) return;
+  std::lock_guard<std::mutex> lock(g_timer_mu);
+  for (size_t i = g_timer_open.size(); i-- > 0;) {
+    if (g_timer_open[i].id == id) {
+      if (cudaEventRecord(g_timer_open[i].b, s) == cudaSuccess)
+        g_timer_open[i].closed = true;
+      else
+        cudaGetLastError();
+      return;
+    }
+  }
+}
+
+void timer_enable(bool on) {
+  std::lock_guard<std::mutex> lock(g_timer_mu);
+  timer_harvest(true);
+  for (const TimerPair& t : g_timer_open) g_timer_spare.push_back(t);  // brackets never closed
+  g_timer_open.clear();
+  g_timer_on = on;
+  g_timer_ms[0] = g_timer_ms[1] = 0.0;
+  g_timer_flops[0] = g_timer_flops[1] = 0.0;
+  g_timer_n[0] = g_timer_n[1] = 0;
+}
+
+int timer_read(int kind, double* ms, double* flops, int64_t* launches) {
+  std::lock_guard<std::mutex> lock(g_timer_mu);
+  timer_harvest(true);
+  *ms = g_timer_ms[kind];
+  *flops = g_timer_flops[kind];
+  *launches = g_timer_n[kind];
+  g_timer_ms[kind] = 0.0;
+  g_timer_flops[kind] = 0.0;
+  g_timer_n[kind] = 0;
+  return CHASE_BSE_OK;
+}
+
 bool verbose() {
   static int v = -1;
   if (v < 0) {

@@ -815,7 +815,9 @@ static int apply(const POperand& P, const CUtensorMap* bmap, Epi ep, cudaStream_
   // 8 row tiles per raster group: of 4, 8, 12 and 16 the least DRAM traffic at n = 16384,
   // k = 1300 (40 GB per launch against 41-59), with the same duration
   sc.group_m = 8;
+  const int64_t tid = timer_begin(0, 32.0 * (double)P.n * (double)P.n * (double)ep.k, s);
   tc_hop_kernel<SCH, BNT, FL><<<(unsigned)(sc.ntiles * sc.nsplit), G::THREADS, G::SMEM_BYTES, s>>>(maps, ep, sc);
+  timer_end(tid, s);
   count_launch();
   CB_LAUNCH();
   return CHASE_BSE_OK;

@@ -55,3 +55,16 @@ def test_bad_arguments_rejected_without_touching_device(lib):
     assert lib.chase_bse_solve(None, None, 0, 1, 0, 1, 1e-10, None, None, None, None) == -1
     assert lib.chase_bse_rr(None, None, 4, None, 3, None, None, None) == -1
     assert lib.chase_bse_grad(None, None, 4, 1, None, None, None) == -1
+
+
+def test_gemm_timer_host_side(lib):
+    """The filter-GEMM event record answers without a GPU while it holds nothing, and
+    rejects a NULL pointer or an unknown kind."""
+    import ctypes
+    ms, fl, cnt = ctypes.c_double(1.0), ctypes.c_double(1.0), ctypes.c_int64(7)
+    lib.chase_bse_gemm_timer(0)
+    args = (ctypes.byref(ms), ctypes.byref(fl), ctypes.byref(cnt))
+    assert lib.chase_bse_gemm_time(0, *args) == 0
+    assert (ms.value, fl.value, cnt.value) == (0.0, 0.0, 0)
+    assert lib.chase_bse_gemm_time(2, *args) == -1
+    assert lib.chase_bse_gemm_time(0, None, ctypes.byref(fl), ctypes.byref(cnt)) == -1

@@ -136,3 +136,35 @@ def test_solve_mixed_moves_stalled_columns_to_fp64(pkg):
     np.testing.assert_allclose(lam.cpu().numpy(), ref, rtol=1e-10)
     assert st["filter_flops_fp64"] > 0.0
     assert st["filter_flops_fp64"] < st["filter_flops"]
+
+
+@pytest.mark.parametrize("precision,kind", [("fp16x3", "tensor"), ("fp64", "fp64")])
+def test_gemm_timer_counts_the_filter_launches(pkg, precision, kind):
+    """The event record of the filter's H applications (the bench's roofline source):
+    a filter over columns with degrees d_i applies H 2 d_i times to column i, so the
+    record holds 2 max(d) launches of 32 n^2 k_j flops each, 64 n^2 sum(d) flops in
+    all, with a positive device time; reading clears it, and nothing is recorded while
+    the record is off."""
+    n, k = 256, 40
+    P = bi.make_problem(n, seed=21)
+    A, B = problem_on_device(P)
+    degs = np.sort(np.random.default_rng(21).integers(1, 6, size=k))[::-1].copy()
+    mu1, mune, muN = _mus(P)
+    pkg.gemm_timer(True)
+    try:
+        W = to_dev(bi.start_block(n, k, 21))
+        pkg.filter(A, B, W, degs, mu1, mune, muN, precision=precision)
+        torch.cuda.synchronize()
+        ms, flops, launches = pkg.gemm_time(kind)
+        other = pkg.gemm_time("fp64" if kind == "tensor" else "tensor")
+        again = pkg.gemm_time(kind)
+    finally:
+        pkg.gemm_timer(False)
+    assert launches == 2 * int(degs.max())
+    assert flops == 64.0 * n * n * float(degs.sum())
+    assert ms > 0.0
+    assert other == (0.0, 0.0, 0)
+    assert again == (0.0, 0.0, 0)
+    W = to_dev(bi.start_block(n, k, 21))
+    pkg.filter(A, B, W, degs, mu1, mune, muN, precision=precision)
+    assert pkg.gemm_time(kind) == (0.0, 0.0, 0)
