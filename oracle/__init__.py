@@ -18,8 +18,10 @@ rayleigh_ritz  oblique Rayleigh-Ritz with hermitian spectral equivalence (Algori
 solver         the outer subspace iteration (Algorithm 3)
 gradient       eigenvalue gradient with respect to A and B (Theorem SH_HPD: u = S v)
 
-Parity status: every function is pinned by tests in ``tests/test_oracle_*.py``
-except the Lanczos estimates of mu_1 and mu_nevex and the iteration/degree
-trajectory of the solver, which are "parity unpinned" (they change speed, not the
-converged result); mu_N is pinned as an upper bound of the spectral radius.
+Parity status: every function is pinned by tests in ``tests/test_oracle_*.py``:
+the DOS estimate of mu_nevex and the per-vector degree rule by hand-worked cases
+(``tests/test_oracle_pins.py``), mu_N as an upper bound of the spectral radius.
+Only the iteration trajectory of the solver as a whole (how many iterations, which
+degrees in which iteration) is "parity unpinned": it changes speed, not the
+converged result, and is reported, not compared.
 """
