@@ -58,11 +58,16 @@ typedef enum chase_bse_precision {
                                   pieces, x = x0 + x1, 3 products, FP32 accumulation
                                   (about 16-bit accurate); everything else FP64      */
   CHASE_BSE_MIXED_BF16X6 = 2,  /* as above with 3 pieces and 6 products (FP32 class) */
-  CHASE_BSE_MIXED_FP16X3 = 3   /* filter products from FP16 pieces x = x0 + x1 (11 +
+  CHASE_BSE_MIXED_FP16X3 = 3,  /* filter products from FP16 pieces x = x0 + x1 (11 +
                                   11 bits, every operand row scaled by a power of two
                                   into FP16's range), 3 products, FP32 accumulation:
                                   FP32-class accuracy at the cost of BF16X3; the
                                   default mixed precision                            */
+  CHASE_BSE_FP64_TC = 4        /* FP64-accurate throughout, with every large product
+                                  (the filter's H applications, QR, Rayleigh-Ritz,
+                                  Lanczos) an FP64-accurate sliced GEMM on the tensor
+                                  cores (see chase_bse_dgemm_sliced); needs compute
+                                  capability 10.3                                    */
 } chase_bse_precision;
 /* In chase_bse_solve the mixed filter runs, from the second iteration on, on the
  * correction q(H^2) r2 with r2 = (H^2 - lambda^2) v of each Ritz pair (FP64
@@ -138,7 +143,9 @@ int chase_bse_solve(const void* A, const void* B, int64_t n, int64_t nev, int64_
  *   sigma_{j+1} = 1/(2/sigma_1 - sigma_j).
  *   W        device, 2n x k complex128, in: Y_0, out: column i = Y_{degs[i]}
  *   degs     host, k ints >= 1 (any order)
- *   precision chase_bse_precision
+ *   precision chase_bse_precision (FP64_TC: the FP64 recurrence with both H
+ *            applications of a step as sliced tensor-core GEMMs; the sliced form of
+ *            H, 7 * 8 n^2 bytes, is built for the call)
  * 0 < mu1 < mu_nevex < muN.  k = 0 is a no-op.  Asynchronous on `stream` except
  * for workspace bookkeeping; the result is ready when the stream reaches it. */
 int chase_bse_filter(const void* A, const void* B, int64_t n, void* W, int64_t k,
@@ -147,9 +154,10 @@ int chase_bse_filter(const void* A, const void* B, int64_t n, void* W, int64_t k
 
 /* chase_bse_filter with a precision per column (the precision groups of a mixed solve,
  * where a column that nears the tolerance moves to the FP64 filter): precs (host, k
- * entries) are chase_bse_precision codes; the FP64 columns run the FP64 filter and the
- * others the tensor-core filter, which takes one scheme per call (all non-FP64 entries
- * equal, else BAD_ARG).  Same arguments otherwise. */
+ * entries) are chase_bse_precision codes; the FP64 (or FP64_TC) columns run the FP64
+ * filter and the others the tensor-core filter, which takes one scheme per call (all
+ * mixed entries equal, and FP64 and FP64_TC not both present, else BAD_ARG).  Same
+ * arguments otherwise. */
 int chase_bse_filter_cols(const void* A, const void* B, int64_t n, void* W, int64_t k,
                           const int32_t* degs, const int32_t* precs, double mu1,
                           double mu_nevex, double muN, void* stream);
@@ -209,6 +217,32 @@ int chase_bse_residuals_noalloc(const void* A, const void* B, int64_t n, const v
  * the FP64 pipe. */
 int chase_bse_grad(const void* V, const double* w, int64_t n, int64_t nev, void* gA,
                    void* gB, void* stream);
+
+/* Non-hermitian fallback Rayleigh-Ritz (Section 4.4, last paragraph), for a search space
+ * where Q^* S Q is singular or Q^* S H Q is not positive definite, so that Algorithm 2's
+ * hermitian equivalence does not apply: with M = Q^* S Q, the dual basis
+ *   Q_L = (S Q - Q (M - diag M)) diag(M)^{-1}    (Q_L^* Q = I; M itself may be singular),
+ * G = Q_L^* H Q (not hermitian), G Z = Z diag(lam) by a complex Schur decomposition
+ * (see chase_bse_eig_general); the Ritz pairs are those with Re lam > 0, ascending.
+ *   Q      device, 2n x k complex128 with orthonormal columns, 1 <= k <= 2n, k <= 32768
+ *   ritz   host, k doubles: Re lam of the returned pairs, ascending
+ *   W      device, 2n x k complex128: columns 0 .. *npos - 1 receive Q Z_+ (unit norm)
+ *   npos   host: the number of pairs returned
+ * Returns QR_FAILED when a diagonal entry of M is zero (relative to the largest) or not
+ * real, NOT_CONVERGED when the QR iteration does not converge.  Synchronises `stream`. */
+int chase_bse_rr_fallback(const void* A, const void* B, int64_t n, const void* Q, int64_t k,
+                          double* ritz, void* W, int64_t* npos, void* stream);
+
+/* Dense eigensolver for a general complex matrix (the eigenproblem of the fallback
+ * Rayleigh-Ritz step; the paper calls a library routine): Householder reduction to
+ * Hessenberg form, shifted QR iteration to the complex Schur form G = Z T Z^*, and the
+ * eigenvectors of T by back substitution: G V = V diag(lam).
+ *   G    device, k x k complex128 column-major (not modified), 0 <= k <= 32768
+ *   lam  device, k complex128 eigenvalues, in the order of V's columns (unsorted)
+ *   V    device, k x k complex128, unit columns
+ * Returns NOT_CONVERGED when an eigenvalue needs more than 30 k QR sweeps in all.
+ * Synchronises `stream`. */
+int chase_bse_eig_general(const void* G, int64_t k, void* lam, void* V, void* stream);
 
 /* Dense hermitian eigensolver of the Rayleigh-Ritz step (Algorithm 2, the HEEVD call
  * G y = theta y), as the solver runs it: G V = V diag(theta).
@@ -299,13 +333,14 @@ int64_t chase_bse_alloc_count(void);
  * chase_bse_gemm_timer(1) clears the record and starts bracketing every such launch
  * made afterwards, by any thread, with a pair of CUDA events recorded on the launch's
  * stream: kind 0 the tensor-core GEMM of a mixed-precision filter, kind 1 the FP64 H
- * application (with its K-split reduction where one is used).  chase_bse_gemm_timer(0)
+ * application (with its K-split reduction where one is used), kind 2 the FP64-accurate
+ * sliced H application (its vector slicing, GEMM and recombination).  chase_bse_gemm_timer(0)
  * stops and clears.  chase_bse_gemm_time waits for the recorded launches of `kind`
  * (blocking the host), writes into *total_ms the sum of their event-to-event device
  * times in milliseconds, into *flops the sum of their algorithmic flops (32 n^2 k for
  * k vectors: H is 2n x 2n complex, 8 real flops per complex multiply-add) and into
  * *launches their number, and clears that kind's record.  Returns BAD_ARG for a NULL
- * pointer or a kind other than 0 or 1. */
+ * pointer or a kind other than 0, 1 or 2. */
 void chase_bse_gemm_timer(int32_t enable);
 int chase_bse_gemm_time(int32_t kind, double* total_ms, double* flops, int64_t* launches);
 

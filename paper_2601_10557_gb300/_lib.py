@@ -22,8 +22,9 @@ MIXED_BF16X3 = 1
 MIXED_BF16X6 = 2
 MIXED_FP16X3 = 3
 # "mixed" is the default tensor-core scheme (FP16 pieces, FP32-class products)
+FP64_TC = 4
 _PREC = {"fp64": FP64, "mixed": MIXED_FP16X3, "fp16x3": MIXED_FP16X3, "bf16x3": MIXED_BF16X3,
-         "bf16x6": MIXED_BF16X6}
+         "bf16x6": MIXED_BF16X6, "fp64_tc": FP64_TC}
 
 
 class ChaseBSEError(RuntimeError):
@@ -88,7 +89,8 @@ EXPORTS = ["chase_bse_solve", "chase_bse_filter", "chase_bse_rr", "chase_bse_res
            "chase_bse_strerror", "chase_bse_version", "chase_bse_has_mixed", "chase_bse_launch_count",
            "chase_bse_residuals_noalloc", "chase_bse_dgemm_sliced", "chase_bse_trim_memory",
            "chase_bse_alloc_count", "chase_bse_degrees", "chase_bse_eigh", "chase_bse_filter_cols",
-           "chase_bse_set_wait_limit", "chase_bse_gemm_timer", "chase_bse_gemm_time"]
+           "chase_bse_set_wait_limit", "chase_bse_gemm_timer", "chase_bse_gemm_time", "chase_bse_rr_fallback",
+           "chase_bse_eig_general"]
 
 # 2n * k limit of chase_bse_residuals_noalloc (its fixed device scratch, complex128 entries)
 NOALLOC_MAX_ENTRIES = 1 << 19
@@ -116,6 +118,9 @@ def lib() -> ctypes.CDLL:
     L.chase_bse_eigh.argtypes = [vp, i64, vp, vp, i32, dbl, vp]
     L.chase_bse_filter_cols.argtypes = [vp, vp, i64, vp, i64, ctypes.POINTER(ctypes.c_int32),
                                         ctypes.POINTER(ctypes.c_int32), dbl, dbl, dbl, vp]
+    L.chase_bse_rr_fallback.argtypes = [vp, vp, i64, vp, i64, ctypes.POINTER(ctypes.c_double), vp,
+                                        ctypes.POINTER(ctypes.c_int64), vp]
+    L.chase_bse_eig_general.argtypes = [vp, i64, vp, vp, vp]
     L.chase_bse_set_wait_limit.argtypes = [ctypes.c_uint64]
     L.chase_bse_set_wait_limit.restype = None
     L.chase_bse_gemm_timer.argtypes = [ctypes.c_int32]
@@ -130,7 +135,8 @@ def lib() -> ctypes.CDLL:
     L.chase_bse_trim_memory.restype = None
     for name in ["chase_bse_solve", "chase_bse_filter", "chase_bse_rr", "chase_bse_residuals", "chase_bse_grad",
                  "chase_bse_version", "chase_bse_has_mixed", "chase_bse_residuals_noalloc",
-                 "chase_bse_dgemm_sliced", "chase_bse_degrees", "chase_bse_eigh", "chase_bse_filter_cols"]:
+                 "chase_bse_dgemm_sliced", "chase_bse_degrees", "chase_bse_eigh", "chase_bse_filter_cols",
+                 "chase_bse_rr_fallback", "chase_bse_eig_general"]:
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -200,6 +206,8 @@ def solve(A: torch.Tensor, B: torch.Tensor, nev: int, nex: int, deg: int = 20, t
           seed: int = 0, stream=None, allow_partial: bool = False, fp64_products: str = "tensor"):
     """chase_bse_solve: returns (evals (nev,) float64, evecs (nev, 2n) complex128, stats dict).
 
+    precision: "fp64" (FP64 pipe), "fp64_tc" (FP64-accurate throughout, every large
+    product a sliced tensor-core GEMM), "mixed" (= "fp16x3"), "bf16x6", "bf16x3".
     fp64_products ("tensor" or "fp64"): in mixed precision, where the FP64-accurate
     products of QR and Rayleigh-Ritz run (sliced tensor-core GEMM or FP64 pipe)."""
     if fp64_products not in ("tensor", "fp64"):
@@ -249,8 +257,8 @@ def filter(A: torch.Tensor, B: torch.Tensor, W: torch.Tensor, degs, mu1: float, 
 
 def filter_cols(A: torch.Tensor, B: torch.Tensor, W: torch.Tensor, degs, precs, mu1: float, mu_nevex: float,
                 muN: float, stream=None) -> torch.Tensor:
-    """chase_bse_filter_cols: the filter with a precision per column ("fp64" or a
-    tensor-core scheme name), in place on W (k, 2n); returns W."""
+    """chase_bse_filter_cols: the filter with a precision per column ("fp64" or "fp64_tc",
+    not both, or one tensor-core scheme name), in place on W (k, 2n); returns W."""
     A = _mat(A, "A")
     n = A.shape[0]
     B = _mat(B, "B", n)
@@ -263,6 +271,41 @@ def filter_cols(A: torch.Tensor, B: torch.Tensor, W: torch.Tensor, degs, precs, 
     _check(lib().chase_bse_filter_cols(_ptr(A), _ptr(B), n, _ptr(W), k, d, p, mu1, mu_nevex, muN,
                                        ctypes.c_void_p(_stream(stream))), "chase_bse_filter_cols")
     return W
+
+
+def rayleigh_ritz_fallback(A: torch.Tensor, B: torch.Tensor, Q: torch.Tensor, stream=None):
+    """chase_bse_rr_fallback: the non-hermitian fallback Rayleigh-Ritz on Q (k, 2n) with
+    orthonormal rows-as-vectors; returns (ritz numpy (m,), W (m, 2n)) for the m Ritz pairs
+    with positive real part, ascending."""
+    import numpy as np
+    A = _mat(A, "A")
+    n = A.shape[0]
+    B = _mat(B, "B", n)
+    Q = _block(Q, "Q", 2 * n)
+    k = Q.shape[0]
+    ritz = (ctypes.c_double * k)()
+    W = torch.zeros((k, 2 * n), dtype=torch.complex128, device=A.device)
+    npos = ctypes.c_int64(0)
+    _check(lib().chase_bse_rr_fallback(_ptr(A), _ptr(B), n, _ptr(Q), k, ritz, _ptr(W), ctypes.byref(npos),
+                                       ctypes.c_void_p(_stream(stream))), "chase_bse_rr_fallback")
+    m = int(npos.value)
+    return np.array(ritz[:m]), W[:m]
+
+
+def eig_general(G: torch.Tensor, stream=None):
+    """chase_bse_eig_general: eigenpairs of a general complex matrix.  G is a (k, k)
+    complex128 device tensor holding the matrix in row-major order (G[i, j] = g_ij);
+    returns (lam (k,) complex128, V (k, k)) with G V = V diag(lam), unit columns of V
+    (V[:, j] is the j-th eigenvector)."""
+    if G.dtype != torch.complex128 or G.dim() != 2 or G.shape[0] != G.shape[1] or not G.is_cuda:
+        raise ValueError("G must be a square complex128 CUDA tensor")
+    k = G.shape[0]
+    Gc = G.t().contiguous()  # column-major storage of G
+    lam = torch.zeros(k, dtype=torch.complex128, device=G.device)
+    Vc = torch.zeros((k, k), dtype=torch.complex128, device=G.device)  # column-major V
+    _check(lib().chase_bse_eig_general(_ptr(Gc), k, _ptr(lam), _ptr(Vc), ctypes.c_void_p(_stream(stream))),
+           "chase_bse_eig_general")
+    return lam, Vc.t()
 
 
 def set_wait_limit(ns: int) -> None:
@@ -279,12 +322,12 @@ def gemm_timer(enable: bool) -> None:
 def gemm_time(kind: str = "tensor"):
     """chase_bse_gemm_time: (total device ms, total algorithmic flops, launches) of the
     recorded H applications of ``kind`` ("tensor": the tensor-core filter GEMM, "fp64":
-    the FP64 H application) since the record was started or last read; clears that
-    kind's record."""
+    the FP64 H application, "sliced": the FP64-accurate sliced H application) since the
+    record was started or last read; clears that kind's record."""
     ms = ctypes.c_double(0.0)
     fl = ctypes.c_double(0.0)
     cnt = ctypes.c_int64(0)
-    _check(lib().chase_bse_gemm_time({"tensor": 0, "fp64": 1}[kind], ctypes.byref(ms), ctypes.byref(fl),
+    _check(lib().chase_bse_gemm_time({"tensor": 0, "fp64": 1, "sliced": 2}[kind], ctypes.byref(ms), ctypes.byref(fl),
                                      ctypes.byref(cnt)), "chase_bse_gemm_time")
     return float(ms.value), float(fl.value), int(cnt.value)
 

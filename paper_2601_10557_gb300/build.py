@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libchase_bse.so")
-SOURCES = ["fp64_kernels.cu", "dense_kernels.cu", "solver.cu", "tc_filter.cu", "tc_dgemm.cu", "jacobi_mixed.cu", "jacobi_block.cu", "abi.cu", "noalloc.cu"]
+SOURCES = ["fp64_kernels.cu", "dense_kernels.cu", "solver.cu", "tc_filter.cu", "tc_dgemm.cu", "jacobi_mixed.cu", "jacobi_block.cu", "geev.cu", "abi.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

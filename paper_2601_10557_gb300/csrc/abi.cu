@@ -30,6 +30,20 @@ static int degrees_host(const double* ritz, const double* res, const double* pre
   return CHASE_BSE_OK;
 }
 
+// Filter call of the ABI: with tc64 the FP64 columns apply H by sliced tensor-core GEMMs
+// (the sliced form of H is cut for this call).
+static int filter_call(const cplx* A, const cplx* B, int64_t n, cplx* W, int64_t k, const int* degs, const int* prec,
+                       double mu1, double mu_nevex, double muN, int scheme, bool tc64, cudaStream_t s) {
+  if (!tc64) return cb::filter(A, B, n, W, k, degs, prec, mu1, mu_nevex, muN, scheme, nullptr, nullptr, s, nullptr);
+  cb::Workspace ws(s);
+  cb::SlicedOp ph;
+  CB_TRY(cb::sliced_alloc(ws, ph, 2 * n, 2 * n, s));
+  CB_TRY(cb::slice_hamiltonian(A, B, n, ph, s));
+  CB_TRY(cb::filter(A, B, n, W, k, degs, prec, mu1, mu_nevex, muN, scheme, nullptr, nullptr, s, nullptr, &ph));
+  // the workspace (and the sliced H) is released on the stream after the filter
+  return CHASE_BSE_OK;
+}
+
 static int eigh_impl(const cplx* G, int64_t k, double* theta, cplx* V, int method, double thr, cudaStream_t s) {
   cb::Workspace ws(s);
   cplx *Gc, *rot;
@@ -62,7 +76,7 @@ void chase_bse_set_wait_limit(uint64_t ns) { cb::set_wait_limit_ns(ns); }
 void chase_bse_gemm_timer(int32_t enable) { cb::timer_enable(enable != 0); }
 
 int chase_bse_gemm_time(int32_t kind, double* total_ms, double* flops, int64_t* launches) {
-  if (!total_ms || !flops || !launches || kind < 0 || kind > 1) return CHASE_BSE_BAD_ARG;
+  if (!total_ms || !flops || !launches || kind < 0 || kind > 2) return CHASE_BSE_BAD_ARG;
   return cb::timer_read(kind, total_ms, flops, launches);
 }
 
@@ -98,14 +112,17 @@ int chase_bse_filter(const void* A, const void* B, int64_t n, void* W, int64_t k
   if (!A || !B || !W || !degs || n < 1 || k < 0 || !(mu1 > 0) || !(mu_nevex > mu1) || !(muN > mu_nevex))
     return CHASE_BSE_BAD_ARG;
   if (precision != CHASE_BSE_FP64 && precision != CHASE_BSE_MIXED_BF16X3 && precision != CHASE_BSE_MIXED_BF16X6 &&
-      precision != CHASE_BSE_MIXED_FP16X3)
+      precision != CHASE_BSE_MIXED_FP16X3 && precision != CHASE_BSE_FP64_TC)
     return CHASE_BSE_BAD_ARG;
   for (int64_t i = 0; i < k; ++i)
     if (degs[i] < 1) return CHASE_BSE_BAD_ARG;
+  if (precision == CHASE_BSE_FP64_TC && !cb::mixed_available()) return CHASE_BSE_UNSUPPORTED;
   CB_GUARD({
-    std::vector<int> prec(k, precision == CHASE_BSE_FP64 ? 0 : 1);
-    return cb::filter((const cplx*)A, (const cplx*)B, n, (cplx*)W, k, degs, prec.data(), mu1, mu_nevex, muN,
-                      precision, nullptr, nullptr, (cudaStream_t)stream, nullptr);
+    const bool fp64 = precision == CHASE_BSE_FP64 || precision == CHASE_BSE_FP64_TC;
+    std::vector<int> prec(k, fp64 ? 0 : 1);
+    return filter_call((const cplx*)A, (const cplx*)B, n, (cplx*)W, k, degs, prec.data(), mu1, mu_nevex, muN,
+                       fp64 ? (int)CHASE_BSE_MIXED_FP16X3 : precision, precision == CHASE_BSE_FP64_TC,
+                       (cudaStream_t)stream);
   })
 }
 
@@ -116,21 +133,31 @@ int chase_bse_filter_cols(const void* A, const void* B, int64_t n, void* W, int6
       !(muN > mu_nevex))
     return CHASE_BSE_BAD_ARG;
   int scheme = 0;
+  bool dfma = false, tc64 = false;
   for (int64_t i = 0; i < k; ++i) {
     if (degs[i] < 1) return CHASE_BSE_BAD_ARG;
     const int p = precs[i];
-    if (p == CHASE_BSE_FP64) continue;
+    if (p == CHASE_BSE_FP64) {
+      dfma = true;
+      continue;
+    }
+    if (p == CHASE_BSE_FP64_TC) {
+      tc64 = true;
+      continue;
+    }
     if (p != CHASE_BSE_MIXED_BF16X3 && p != CHASE_BSE_MIXED_BF16X6 && p != CHASE_BSE_MIXED_FP16X3)
       return CHASE_BSE_BAD_ARG;
     if (scheme != 0 && p != scheme) return CHASE_BSE_BAD_ARG;
     scheme = p;
   }
+  if (dfma && tc64) return CHASE_BSE_BAD_ARG;
+  if (tc64 && !cb::mixed_available()) return CHASE_BSE_UNSUPPORTED;
   CB_GUARD({
     std::vector<int> prec(k);
-    for (int64_t i = 0; i < k; ++i) prec[i] = precs[i] == CHASE_BSE_FP64 ? 0 : 1;
-    return cb::filter((const cplx*)A, (const cplx*)B, n, (cplx*)W, k, degs, prec.data(), mu1, mu_nevex, muN,
-                      scheme == 0 ? CHASE_BSE_MIXED_FP16X3 : scheme, nullptr, nullptr, (cudaStream_t)stream,
-                      nullptr);
+    for (int64_t i = 0; i < k; ++i)
+      prec[i] = (precs[i] == CHASE_BSE_FP64 || precs[i] == CHASE_BSE_FP64_TC) ? 0 : 1;
+    return filter_call((const cplx*)A, (const cplx*)B, n, (cplx*)W, k, degs, prec.data(), mu1, mu_nevex, muN,
+                       scheme == 0 ? CHASE_BSE_MIXED_FP16X3 : scheme, tc64, (cudaStream_t)stream);
   })
 }
 
@@ -168,6 +195,20 @@ int chase_bse_eigh(const void* G, int64_t k, double* theta, void* V, int32_t met
     return CHASE_BSE_BAD_ARG;
   if (method == 1 && !cb::mixed_available()) return CHASE_BSE_UNSUPPORTED;
   CB_GUARD(return eigh_impl((const cplx*)G, k, theta, (cplx*)V, method, thr, (cudaStream_t)stream);)
+}
+
+int chase_bse_eig_general(const void* G, int64_t k, void* lam, void* V, void* stream) {
+  if (k == 0) return CHASE_BSE_OK;
+  if (!G || !lam || !V || k < 0 || k > ((int64_t)1 << 15)) return CHASE_BSE_BAD_ARG;
+  CB_GUARD(return cb::geev((const cplx*)G, k, (cplx*)lam, (cplx*)V, (cudaStream_t)stream);)
+}
+
+int chase_bse_rr_fallback(const void* A, const void* B, int64_t n, const void* Q, int64_t k, double* ritz, void* W,
+                          int64_t* npos, void* stream) {
+  if (!A || !B || !Q || !ritz || !W || !npos || n < 1 || k < 1 || k > 2 * n || k > ((int64_t)1 << 15))
+    return CHASE_BSE_BAD_ARG;
+  CB_GUARD(return cb::rayleigh_ritz_fallback((const cplx*)A, (const cplx*)B, n, (const cplx*)Q, k, ritz, (cplx*)W,
+                                             npos, (cudaStream_t)stream);)
 }
 
 int chase_bse_dgemm_sliced(const double* A, int64_t lda, const double* B, int64_t ldb, int64_t M, int64_t N,

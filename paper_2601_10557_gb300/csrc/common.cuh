@@ -57,8 +57,8 @@ void count_launch();
 int64_t launch_count();
 
 // Device-time record of the filter's H applications (diagnostics): kind 0 the
-// tensor-core filter GEMM, kind 1 the FP64 H application, each with its algorithmic
-// flops.  timer_begin returns an id (-1 while the record is off) that timer_end
+// tensor-core filter GEMM, kind 1 the FP64 H application, kind 2 the sliced
+// FP64-accurate H application, each with its algorithmic flops.  timer_begin returns an id (-1 while the record is off) that timer_end
 // closes after the launch.
 int64_t timer_begin(int kind, double flops, cudaStream_t s);
 void timer_end(int64_t id, cudaStream_t s);

@@ -67,8 +67,9 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 // Device-time record of the filter's H applications (diagnostics).  While it is
-// on, every launch of the tensor-core filter GEMM (kind 0) and of the FP64 H
-// application (kind 1) is bracketed by a pair of CUDA events on its stream.
+// on, every launch of the tensor-core filter GEMM (kind 0), of the FP64 H
+// application (kind 1) and every sliced H application (kind 2) is bracketed by a
+// pair of CUDA events on its stream.
 // Completed pairs are harvested without blocking at the next bracket, so the
 // record holds at most a few launches in flight.
 namespace {
@@ -83,9 +84,10 @@ std::mutex g_timer_mu;
 bool g_timer_on = false;
 std::vector<TimerPair> g_timer_open;   // recorded, not yet harvested
 std::vector<TimerPair> g_timer_spare;  // harvested, events reusable
-double g_timer_ms[2] = {0.0, 0.0};
-double g_timer_flops[2] = {0.0, 0.0};
-int64_t g_timer_n[2] = {0, 0};
+constexpr int kTimerKinds = 3;
+double g_timer_ms[kTimerKinds] = {};
+double g_timer_flops[kTimerKinds] = {};
+int64_t g_timer_n[kTimerKinds] = {};
 int64_t g_timer_next = 0;
 
 void timer_harvest(bool wait) {
@@ -159,9 +161,11 @@ void timer_enable(bool on) {
   for (const TimerPair& t : g_timer_open) g_timer_spare.push_back(t);  // brackets never closed
   g_timer_open.clear();
   g_timer_on = on;
-  g_timer_ms[0] = g_timer_ms[1] = 0.0;
-  g_timer_flops[0] = g_timer_flops[1] = 0.0;
-  g_timer_n[0] = g_timer_n[1] = 0;
+  for (int i = 0; i < kTimerKinds; ++i) {
+    g_timer_ms[i] = 0.0;
+    g_timer_flops[i] = 0.0;
+    g_timer_n[i] = 0;
+  }
 }
 
 int timer_read(int kind, double* ms, double* flops, int64_t* launches) {
@@ -186,17 +190,37 @@ bool verbose() {
 }
 
 // ------------------------------------------------------------------- filter
+// nxt = alpha (HT - c cur) + beta prev over `total` entries (the recurrence step of the
+// FP64 filter whose H applications ran as sliced tensor-core GEMMs)
+__global__ void cheb_combine_kernel(cplx* nxt, const cplx* HT, const cplx* cur, const cplx* prev, double alpha,
+                                    double beta, double c, int64_t total) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const cplx h = HT[i], y = cur[i];
+    cplx z = mk(alpha * (h.x - c * y.x), alpha * (h.y - c * y.y));
+    if (beta != 0.0) {
+      const cplx p = prev[i];
+      z.x = fma(beta, p.x, z.x);
+      z.y = fma(beta, p.y, z.y);
+    }
+    nxt[i] = z;
+  }
+}
+
 // FP64 three-term recurrence on H^2 over columns sorted by descending degree:
 // at step j only the prefix of columns with deg >= j+1 is active.  Y_j lives in
 // buffer j mod 3; a finished column keeps its last iterate in buffer deg mod 3.
+// With ph (the sliced operand of slice_hamiltonian) both H applications of a step run
+// as FP64-accurate sliced GEMMs on the tensor cores, else on the FP64 pipe (the second
+// one with the recurrence fused).
 static int filter_fp64_sorted(const cplx* A, const cplx* B, int64_t n, cplx* Y0, int64_t k, const int* degs,
                               double mu1, double mu_nevex, double muN, cplx* out, Workspace& ws, cudaStream_t s,
-                              FilterStats* fs) {
+                              FilterStats* fs, const SlicedOp* ph) {
   const int64_t n2 = 2 * n;
-  cplx *Y1, *Y2, *T;
+  cplx *Y1, *Y2, *T, *HT = nullptr;
   CB_TRY(ws.alloc(&Y1, n2 * k));
   CB_TRY(ws.alloc(&Y2, n2 * k));
   CB_TRY(ws.alloc(&T, n2 * k));
+  if (ph) CB_TRY(ws.alloc(&HT, n2 * k));
   cplx* Yb[3] = {Y0, Y1, Y2};
   const double a = mu_nevex * mu_nevex, b = muN * muN;
   const double c = 0.5 * (a + b), e = 0.5 * (b - a);
@@ -214,9 +238,13 @@ static int filter_fp64_sorted(const cplx* A, const cplx* B, int64_t n, cplx* Y0,
     cplx* cur = Yb[j % 3];
     cplx* nxt = Yb[(j + 1) % 3];
     cplx* prev = Yb[(j + 2) % 3];
-    HopArgs h{};
-    h.A = A; h.B = B; h.n = n; h.W = cur; h.k = kj; h.out = T; h.mode = HOP_STORE;
-    CB_TRY(hop_fp64(h, s));
+    if (ph) {
+      CB_TRY(hop_sliced(*ph, cur, n, kj, T, s));
+    } else {
+      HopArgs h{};
+      h.A = A; h.B = B; h.n = n; h.W = cur; h.k = kj; h.out = T; h.mode = HOP_STORE;
+      CB_TRY(hop_fp64(h, s));
+    }
     double alpha, beta;
     if (j == 0) {
       alpha = sigma1 / e;
@@ -227,10 +255,19 @@ static int filter_fp64_sorted(const cplx* A, const cplx* B, int64_t n, cplx* Y0,
       beta = -sigma * sn;
       sigma = sn;
     }
-    HopArgs g{};
-    g.A = A; g.B = B; g.n = n; g.W = T; g.k = kj; g.out = nxt; g.mode = HOP_CHEB;
-    g.alpha = alpha; g.beta = beta; g.c = c; g.Wc = cur; g.Wp = prev;
-    CB_TRY(hop_fp64(g, s));
+    if (ph) {
+      CB_TRY(hop_sliced(*ph, T, n, kj, HT, s));
+      const int64_t total = n2 * kj;
+      const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 8192);
+      cheb_combine_kernel<<<blocks, 256, 0, s>>>(nxt, HT, cur, prev, alpha, beta, c, total);
+      count_launch();
+      CB_LAUNCH();
+    } else {
+      HopArgs g{};
+      g.A = A; g.B = B; g.n = n; g.W = T; g.k = kj; g.out = nxt; g.mode = HOP_CHEB;
+      g.alpha = alpha; g.beta = beta; g.c = c; g.Wc = cur; g.Wp = prev;
+      CB_TRY(hop_fp64(g, s));
+    }
     if (fs) {
       fs->flops += 64.0 * (double)n * (double)n * (double)kj;
       fs->flops_fp64 += 64.0 * (double)n * (double)n * (double)kj;
@@ -257,7 +294,7 @@ static int filter_fp64_sorted(const cplx* A, const cplx* B, int64_t n, cplx* Y0,
 
 int filter(const cplx* A, const cplx* B, int64_t n, cplx* W, int64_t k, const int* degs, const int* prec,
            double mu1, double mu_nevex, double muN, int scheme, const double* ritz, const cplx* R, cudaStream_t s,
-           FilterStats* fs) {
+           FilterStats* fs, const SlicedOp* ph) {
   if (k == 0) return CHASE_BSE_OK;
   const int64_t n2 = 2 * n;
   Workspace ws(s);
@@ -280,7 +317,7 @@ int filter(const cplx* A, const cplx* B, int64_t n, cplx* W, int64_t k, const in
     CB_CUDA(cudaMemcpyAsync(didx, idx.data(), sizeof(int) * m, cudaMemcpyHostToDevice, s));
     CB_TRY(gather_cols(Y0, W, didx, n2, m, s));
     if (grp == 0) {
-      CB_TRY(filter_fp64_sorted(A, B, n, Y0, m, ds.data(), mu1, mu_nevex, muN, out, gws, s, fs));
+      CB_TRY(filter_fp64_sorted(A, B, n, Y0, m, ds.data(), mu1, mu_nevex, muN, out, gws, s, fs, ph));
     } else {
       if (!mixed_available()) return CHASE_BSE_UNSUPPORTED;
       if (ritz && R) {
@@ -927,13 +964,17 @@ int solve(const cplx* A, const cplx* B, int64_t n, int64_t nev, int64_t nex, int
       o.maxiter < 1 || o.deg_min < 1 || o.deg_max < o.deg_min || o.lanczos_steps < 2 || o.lanczos_vecs < 1 ||
       o.lanczos_vecs > 64 ||
       (o.precision != CHASE_BSE_FP64 && o.precision != CHASE_BSE_MIXED_BF16X3 &&
-       o.precision != CHASE_BSE_MIXED_BF16X6 && o.precision != CHASE_BSE_MIXED_FP16X3))
+       o.precision != CHASE_BSE_MIXED_BF16X6 && o.precision != CHASE_BSE_MIXED_FP16X3 &&
+       o.precision != CHASE_BSE_FP64_TC))
     return CHASE_BSE_BAD_ARG;
   if (o.fp64_products != 0 && o.fp64_products != 1) return CHASE_BSE_BAD_ARG;
-  const bool mixed = o.precision != CHASE_BSE_FP64;
-  const bool sliced = mixed && o.fp64_products == 0;
-  const int scheme = o.precision;  // FilterScheme codes equal the precision codes
-  if (mixed && !mixed_available()) return CHASE_BSE_UNSUPPORTED;
+  const bool fp64tc = o.precision == CHASE_BSE_FP64_TC;
+  const bool mixed = o.precision != CHASE_BSE_FP64 && !fp64tc;
+  // FP64-accurate products on the tensor cores: FP64_TC always, mixed unless fp64_products
+  const bool sliced = fp64tc || (mixed && o.fp64_products == 0);
+  // FilterScheme codes equal the mixed precision codes (unused when no column is mixed)
+  const int scheme = mixed ? o.precision : (int)CHASE_BSE_MIXED_FP16X3;
+  if ((mixed || fp64tc) && !mixed_available()) return CHASE_BSE_UNSUPPORTED;
   cudaStream_t s = (cudaStream_t)o.stream;
   const int64_t n2 = 2 * n, nevex = nev + nex;
   {  // inputs with a NaN or an Inf: a defined status, nothing computed
@@ -1025,7 +1066,7 @@ int solve(const cplx* A, const cplx* B, int64_t n, int64_t nev, int64_t nex, int
     clk.start();
     const bool corr = mixed && !ritz_keep.empty();
     CB_TRY(filter(A, B, n, W, kf, degs.data(), prec.data(), mu1, mu_ne, muN, scheme,
-                  corr ? ritz_keep.data() : nullptr, corr ? Rkeep : nullptr, s, &fs));
+                  corr ? ritz_keep.data() : nullptr, corr ? Rkeep : nullptr, s, &fs, sliced ? &ph : nullptr));
     st.ms_filter += clk.stop();
     // orthonormalisation: W- = K conj(W+), Q = [S Y+, S Y-, W+, W-] R^{-1}, drop the locked part;
     // J-fixed basis (top halves) unless its CholeskyQR2 breaks down

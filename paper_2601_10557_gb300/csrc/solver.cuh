@@ -18,13 +18,15 @@ enum FilterScheme : int { SCHEME_BF16X3 = 1, SCHEME_BF16X6 = 2, SCHEME_FP16X3 = 
 // (host).  prec[i] = 0: FP64 path, 1: tensor-core path with `scheme`
 // (FilterScheme).  With ritz (host, per column) and R (device, 2n x k, the FP64
 // residual vectors H w - ritz w) the tensor-core columns use the correction form.
+// With ph (the sliced operand of slice_hamiltonian) the FP64 columns apply H by
+// FP64-accurate sliced GEMMs on the tensor cores instead of the FP64 pipe.
+struct SlicedOp;
 int filter(const cplx* A, const cplx* B, int64_t n, cplx* W, int64_t k, const int* degs, const int* prec,
            double mu1, double mu_nevex, double muN, int scheme, const double* ritz, const cplx* R, cudaStream_t s,
-           FilterStats* fs);
+           FilterStats* fs, const SlicedOp* ph = nullptr);
 
 // Lanczos bounds: mu1, mu_nevex, muN and rho_hat (max |theta|); with ph (the sliced
 // operand of slice_hamiltonian) H is applied on the tensor cores, FP64-accurate.
-struct SlicedOp;
 int lanczos_bounds(const cplx* A, const cplx* B, int64_t n, const cplx* V0, int64_t nvec, int steps,
                    int64_t nevex, double out[4], cudaStream_t s, const SlicedOp* ph = nullptr);
 
@@ -50,6 +52,17 @@ int solve(const cplx* A, const cplx* B, int64_t n, int64_t nev, int64_t nex, int
 void degrees_update(const std::vector<double>& ritz, const std::vector<double>& res,
                     const std::vector<double>& prev_res, const std::vector<int>& prev_deg, double tol, double mu_ne,
                     double muN, int dmin, int dmax, std::vector<int>& degs);
+
+// Eigen-decomposition of a general complex k x k matrix G (column-major; not
+// modified): G V = V diag(lam), unit columns (geev.cu).  NOT_CONVERGED if the shifted
+// QR iteration needs more than 30 k sweeps.
+int geev(const cplx* G, int64_t k, cplx* lam, cplx* V, cudaStream_t s);
+
+// Non-hermitian fallback Rayleigh-Ritz (Section 4.4, last paragraph; geev.cu): the dual
+// basis of Q, G = Q_L^* H Q, and the Ritz pairs with positive real part (ascending):
+// ritz_host[0 .. *npos), W (2n x *npos) = Q Z_+ with unit columns.
+int rayleigh_ritz_fallback(const cplx* A, const cplx* B, int64_t n, const cplx* Q, int64_t k, double* ritz_host,
+                           cplx* W, int64_t* npos, cudaStream_t s);
 
 int gradient(const cplx* V, const double* w, int64_t n, int64_t nev, cplx* gA, cplx* gB, cudaStream_t s);
 

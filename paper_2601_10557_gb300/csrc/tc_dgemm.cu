@@ -515,14 +515,16 @@ int hop_sliced(const SlicedOp& ph, const cplx* W, int64_t n, int64_t k, cplx* ou
   cplx *Z, *T;
   CB_TRY(ws.alloc(&Z, n * 2 * k));
   CB_TRY(ws.alloc(&T, n * 2 * k));
+  SlicedOp sz;
+  CB_TRY(sliced_alloc(ws, sz, 2 * k, 2 * n, s));
+  const int64_t tid = timer_begin(2, 32.0 * (double)n * (double)n * (double)k, s);
   tcd::jsplit_kernel<<<tcd::gsz(n * k), 256, 0, s>>>(W, n, k, Z);
   count_launch();
   CB_LAUNCH();
-  SlicedOp sz;
-  CB_TRY(sliced_alloc(ws, sz, 2 * k, 2 * n, s));
   CB_TRY(slice_rows(reinterpret_cast<const double*>(Z), 2 * n, 0, sz, s));
   CB_TRY(sliced_gemm(ph, sz, 1.0, reinterpret_cast<double*>(T), 1, 2 * n, false, s));
   tcd::jcombine_kernel<<<tcd::gsz(n * k), 256, 0, s>>>(T, n, k, out);
+  timer_end(tid, s);
   count_launch();
   CB_LAUNCH();
   return CHASE_BSE_OK;

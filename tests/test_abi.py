@@ -66,5 +66,6 @@ def test_gemm_timer_host_side(lib):
     args = (ctypes.byref(ms), ctypes.byref(fl), ctypes.byref(cnt))
     assert lib.chase_bse_gemm_time(0, *args) == 0
     assert (ms.value, fl.value, cnt.value) == (0.0, 0.0, 0)
-    assert lib.chase_bse_gemm_time(2, *args) == -1
+    assert lib.chase_bse_gemm_time(2, *args) == 0
+    assert lib.chase_bse_gemm_time(3, *args) == -1
     assert lib.chase_bse_gemm_time(0, None, ctypes.byref(fl), ctypes.byref(cnt)) == -1

@@ -207,3 +207,82 @@ def test_error_statuses(pkg):
     assert e.value.status == -1
     lam, V, st = pkg.solve(A, B, 4, 4, 2, 1e-14, maxiter=1, allow_partial=True)
     assert st["status"] == 1 and st["converged"] < 4
+
+
+# ------------------------------------------------ FP64 on the tensor cores (FP64_TC)
+@pytest.mark.parametrize("n,k", [(37, 5), (130, 70), (300, 24)])
+def test_filter_fp64_tc_matches_oracle(pkg, n, k):
+    """The FP64 recurrence with both H applications of every step as sliced tensor-core
+    GEMMs: the oracle filter's result to 1e-12, ragged degrees; 2 max(deg) recorded
+    sliced H applications."""
+    P = bi.make_problem(n, seed=n + 1)
+    A, B = problem_on_device(P)
+    W0 = bi.start_block(n, k, 4)
+    degs = np.random.default_rng(k + 1).integers(1, 9, size=k)
+    mu1, mune, muN = _mus(P)
+    W = to_dev(W0)
+    pkg.gemm_timer(True)
+    try:
+        pkg.filter(A, B, W, degs, mu1, mune, muN, precision="fp64_tc")
+        torch.cuda.synchronize()
+        _, flops, launches = pkg.gemm_time("sliced")
+    finally:
+        pkg.gemm_timer(False)
+    Y = chebyshev.chebyshev_filter(P.A, P.B, W0.T, degs, mu1, mune, muN)
+    assert rel_fro(W.cpu().numpy().T, Y) < TOL_FP64_FILTER
+    assert launches == 2 * int(degs.max())
+    assert flops == 64.0 * n * n * float(degs.sum())
+
+
+def test_filter_cols_fp64_tc_group_with_mixed(pkg):
+    """Precision groups of one call: FP64_TC columns (1e-12) beside FP16x3 columns (1e-5);
+    FP64 and FP64_TC in one call are rejected."""
+    n, k = 200, 18
+    P = bi.make_problem(n, seed=12)
+    A, B = problem_on_device(P)
+    W0 = bi.start_block(n, k, 12)
+    degs = np.random.default_rng(12).integers(1, 7, size=k)
+    precs = ["fp64_tc" if i % 2 == 0 else "fp16x3" for i in range(k)]
+    mu1, mune, muN = _mus(P)
+    W = to_dev(W0)
+    pkg.filter_cols(A, B, W, degs, precs, mu1, mune, muN)
+    Y = chebyshev.chebyshev_filter(P.A, P.B, W0.T, degs, mu1, mune, muN)
+    got = W.cpu().numpy().T
+    for j in range(k):
+        err = rel_fro(got[:, j], Y[:, j])
+        assert err < (TOL_FP64_FILTER if precs[j] == "fp64_tc" else 1e-5), (j, precs[j], err)
+    with pytest.raises(pkg.ChaseBSEError):
+        pkg.filter_cols(A, B, to_dev(W0), degs, ["fp64", "fp64_tc"] * (k // 2), mu1, mune, muN)
+
+
+@pytest.mark.parametrize("kind", ["complex", "real"])
+def test_solve_fp64_tc_matches_brute_force(pkg, kind):
+    """An FP64_TC solve (every large product FP64-accurate on the tensor cores) reaches the
+    dense eigenpairs like the FP64 solve, with the same residual bound."""
+    n, nev, nex = 64, 8, 6
+    P = bi.make_problem(n, seed=11, real=(kind == "real"))
+    A, B = problem_on_device(P)
+    W0, V0 = starts(n, nev + nex, 0)
+    lam, V, st = pkg.solve(A, B, nev, nex, 12, 1e-10, W0=to_dev(W0), V0=to_dev(V0), deg_min=4, deg_max=24,
+                           precision="fp64_tc")
+    ref, _ = dense.smallest_positive(P.A, P.B, nev)
+    lam = lam.cpu().numpy()
+    np.testing.assert_allclose(lam, ref, rtol=TOL_EIG)
+    Vg = V.cpu().numpy().T
+    H = dense.hamiltonian(P.A, P.B)
+    R = H @ Vg - Vg * lam
+    assert np.linalg.norm(R, axis=0).max() / np.linalg.norm(H, 2) <= 1e-10
+    assert st["filter_flops_fp64"] == st["filter_flops"]
+
+
+def test_solve_fp64_tc_n512_workload(pkg):
+    cfg = bi.WORKLOADS["n512"]
+    n, nev, nex = cfg["n"], cfg["nev"], cfg["nex"]
+    P = bi.make_problem(n, seed=0, spec=cfg["spec"], beta=cfg["beta"])
+    A, B = problem_on_device(P)
+    W0, V0 = starts(n, nev + nex, 0)
+    lam, V, st = pkg.solve(A, B, nev, nex, cfg["deg"], cfg["tol"], W0=to_dev(W0), V0=to_dev(V0),
+                           deg_min=cfg["deg_min"], deg_max=cfg["deg_max"], precision="fp64_tc")
+    ref, _ = dense.smallest_positive(P.A, P.B, nev)
+    np.testing.assert_allclose(lam.cpu().numpy(), ref, rtol=TOL_EIG)
+    assert st["max_residual"] <= cfg["tol"]
