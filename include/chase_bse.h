@@ -45,7 +45,9 @@ typedef enum chase_bse_status {
   CHASE_BSE_BAD_ARG = -1,        /* invalid size, NULL pointer, bad option            */
   CHASE_BSE_CUDA_ERROR = -2,     /* a CUDA runtime call or kernel launch failed       */
   CHASE_BSE_OOM = -3,            /* workspace allocation failed                       */
-  CHASE_BSE_NOT_DEFINITE = -4,   /* Cholesky of Q^* S H Q failed: S H not HPD         */
+  CHASE_BSE_NOT_DEFINITE = -4,   /* Cholesky of Q^* S H Q failed: S H not HPD (in a
+                                    solve: and the non-hermitian fallback found fewer
+                                    Ritz values with positive real part than needed) */
   CHASE_BSE_QR_FAILED = -5,      /* search space rank-deficient even for Householder  */
   CHASE_BSE_DEVICE_TIMEOUT = -6, /* a bounded device-side wait gave up                */
   CHASE_BSE_UNSUPPORTED = -7,    /* feature needs a device this build cannot run on   */
@@ -95,6 +97,15 @@ typedef struct chase_bse_opts {
   const void* W0;          /* device, 2n x (nev+nex) raw start block, or NULL         */
   const void* V0;          /* device, 2n x lanczos_vecs Lanczos start vectors, or NULL*/
   void* stream;            /* cudaStream_t                                            */
+  int32_t rr;              /* Rayleigh-Ritz step: 0 = Algorithm 2, with the non-hermitian
+                              fallback (see chase_bse_rr_fallback) in an iteration where
+                              Q^* S H Q is not positive definite (default); 1 = the
+                              fallback in every iteration                             */
+  int32_t h2;              /* mixed precision only: 0 = the filter applies H twice per
+                              step (Section 4.2, default); 1 = the explicit-H^2 variant,
+                              not the paper's method: the blocks of H^2 are formed once
+                              (chase_bse_h2_blocks) and applied with one tensor-core
+                              product per step                                        */
 } chase_bse_opts;
 
 /* Statistics of chase_bse_solve (host struct, filled when non-NULL). */
@@ -113,6 +124,8 @@ typedef struct chase_bse_stats {
   double max_residual;     /* largest scaled residual of the returned pairs           */
   double lanczos_mu1, lanczos_mu_nevex, lanczos_muN;  /* the bounds of Section 4.1 as the
                               Lanczos estimate returned them, before any update     */
+  int32_t fallback_rr;     /* iterations that ran the non-hermitian fallback RR       */
+  double ms_h2;            /* explicit-H^2 variant: time to form the blocks of H^2    */
 } chase_bse_stats;
 
 /* Full solve (Algorithm 3).
@@ -134,6 +147,23 @@ typedef struct chase_bse_stats {
 int chase_bse_solve(const void* A, const void* B, int64_t n, int64_t nev, int64_t nex,
                     int32_t deg, double tol, const chase_bse_opts* opts, double* evals,
                     void* evecs, chase_bse_stats* stats);
+
+/* The blocks of H^2 = [[P, Q], [conj Q, conj P]] for H = [[A, B], [-conj B, -conj A]]:
+ * P = A A - B conj(B), Q = A B - B conj(A), as the top block row
+ * [A | -B] [[A, B], [conj B, conj A]] in FP64-accurate sliced tensor-core GEMMs (see
+ * chase_bse_dgemm_sliced; 32 n^3 flops).  No counterpart in the paper's method, which
+ * applies H twice: the operand of the explicit-H^2 variant.
+ *   P, Q   device, n x n complex128 each, row-major like A and B
+ * Needs compute capability 10.3 (UNSUPPORTED otherwise).  Synchronises `stream`. */
+int chase_bse_h2_blocks(const void* A, const void* B, int64_t n, void* P, void* Q, void* stream);
+
+/* The tensor-core filter of chase_bse_filter in the explicit-H^2 variant (not the paper's
+ * method): the blocks of H^2 are formed for the call (chase_bse_h2_blocks) and each step
+ * applies H^2 with one product instead of two applications of H.  precision: one of the
+ * MIXED schemes; other arguments as chase_bse_filter. */
+int chase_bse_filter_h2(const void* A, const void* B, int64_t n, void* W, int64_t k,
+                        const int32_t* degs, double mu1, double mu_nevex, double muN,
+                        int32_t precision, void* stream);
 
 /* Chebyshev filter on H^2 (Section 4.2, eq. three-term_recurrence_pseudo-hermitian),
  * scaled three-term recurrence with a = mu_nevex^2, b = muN^2, c = (a+b)/2,

@@ -3,12 +3,12 @@
 thin Python binding."""
 from ._lib import (ChaseBSEError, FP64, FP64_TC, MIXED_BF16X3, MIXED_BF16X6, MIXED_FP16X3, BSEEigvals,
                    alloc_count, degrees, dgemm_sliced, eig_general, eigh, eigvals, filter, filter_cols,
-                   gemm_time, gemm_timer, grad, has_mixed, launch_count, lib, rayleigh_ritz,
+                   gemm_time, gemm_timer, grad, h2_blocks, filter_h2, has_mixed, launch_count, lib, rayleigh_ritz,
                    rayleigh_ritz_fallback, residuals, set_wait_limit, solve, strerror, trim_memory, LIB_PATH,
                    EXPORTS)
 
 __all__ = ["ChaseBSEError", "FP64", "FP64_TC", "MIXED_BF16X3", "MIXED_BF16X6", "MIXED_FP16X3", "BSEEigvals",
            "alloc_count", "degrees", "dgemm_sliced", "eig_general", "eigh", "eigvals", "filter", "filter_cols",
-           "gemm_time", "gemm_timer", "grad", "has_mixed", "launch_count", "lib", "rayleigh_ritz",
+           "gemm_time", "gemm_timer", "grad", "h2_blocks", "filter_h2", "has_mixed", "launch_count", "lib", "rayleigh_ritz",
            "rayleigh_ritz_fallback", "residuals", "set_wait_limit", "solve", "strerror", "trim_memory",
            "LIB_PATH", "EXPORTS"]

@@ -49,6 +49,8 @@ class Opts(ctypes.Structure):
         ("W0", ctypes.c_void_p),
         ("V0", ctypes.c_void_p),
         ("stream", ctypes.c_void_p),
+        ("rr", ctypes.c_int32),
+        ("h2", ctypes.c_int32),
     ]
 
 
@@ -77,6 +79,8 @@ class Stats(ctypes.Structure):
         ("lanczos_mu1", ctypes.c_double),
         ("lanczos_mu_nevex", ctypes.c_double),
         ("lanczos_muN", ctypes.c_double),
+        ("fallback_rr", ctypes.c_int32),
+        ("ms_h2", ctypes.c_double),
     ]
 
     def as_dict(self) -> dict:
@@ -90,7 +94,7 @@ EXPORTS = ["chase_bse_solve", "chase_bse_filter", "chase_bse_rr", "chase_bse_res
            "chase_bse_residuals_noalloc", "chase_bse_dgemm_sliced", "chase_bse_trim_memory",
            "chase_bse_alloc_count", "chase_bse_degrees", "chase_bse_eigh", "chase_bse_filter_cols",
            "chase_bse_set_wait_limit", "chase_bse_gemm_timer", "chase_bse_gemm_time", "chase_bse_rr_fallback",
-           "chase_bse_eig_general"]
+           "chase_bse_eig_general", "chase_bse_h2_blocks", "chase_bse_filter_h2"]
 
 # 2n * k limit of chase_bse_residuals_noalloc (its fixed device scratch, complex128 entries)
 NOALLOC_MAX_ENTRIES = 1 << 19
@@ -121,6 +125,8 @@ def lib() -> ctypes.CDLL:
     L.chase_bse_rr_fallback.argtypes = [vp, vp, i64, vp, i64, ctypes.POINTER(ctypes.c_double), vp,
                                         ctypes.POINTER(ctypes.c_int64), vp]
     L.chase_bse_eig_general.argtypes = [vp, i64, vp, vp, vp]
+    L.chase_bse_h2_blocks.argtypes = [vp, vp, i64, vp, vp, vp]
+    L.chase_bse_filter_h2.argtypes = [vp, vp, i64, vp, i64, ctypes.POINTER(ctypes.c_int32), dbl, dbl, dbl, i32, vp]
     L.chase_bse_set_wait_limit.argtypes = [ctypes.c_uint64]
     L.chase_bse_set_wait_limit.restype = None
     L.chase_bse_gemm_timer.argtypes = [ctypes.c_int32]
@@ -136,7 +142,7 @@ def lib() -> ctypes.CDLL:
     for name in ["chase_bse_solve", "chase_bse_filter", "chase_bse_rr", "chase_bse_residuals", "chase_bse_grad",
                  "chase_bse_version", "chase_bse_has_mixed", "chase_bse_residuals_noalloc",
                  "chase_bse_dgemm_sliced", "chase_bse_degrees", "chase_bse_eigh", "chase_bse_filter_cols",
-                 "chase_bse_rr_fallback", "chase_bse_eig_general"]:
+                 "chase_bse_rr_fallback", "chase_bse_eig_general", "chase_bse_h2_blocks", "chase_bse_filter_h2"]:
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -203,15 +209,24 @@ def solve(A: torch.Tensor, B: torch.Tensor, nev: int, nex: int, deg: int = 20, t
           precision: str = "fp64", W0: Optional[torch.Tensor] = None, V0: Optional[torch.Tensor] = None,
           maxiter: int = 25, deg_min: Optional[int] = None, deg_max: Optional[int] = None,
           lanczos_steps: int = 26, lanczos_vecs: int = 4, gamma: float = 1e-3, switch_tol: float = 1e-8,
-          seed: int = 0, stream=None, allow_partial: bool = False, fp64_products: str = "tensor"):
+          seed: int = 0, stream=None, allow_partial: bool = False, fp64_products: str = "tensor",
+          rr: str = "oblique", h2: str = "implicit"):
     """chase_bse_solve: returns (evals (nev,) float64, evecs (nev, 2n) complex128, stats dict).
 
     precision: "fp64" (FP64 pipe), "fp64_tc" (FP64-accurate throughout, every large
     product a sliced tensor-core GEMM), "mixed" (= "fp16x3"), "bf16x6", "bf16x3".
     fp64_products ("tensor" or "fp64"): in mixed precision, where the FP64-accurate
-    products of QR and Rayleigh-Ritz run (sliced tensor-core GEMM or FP64 pipe)."""
+    products of QR and Rayleigh-Ritz run (sliced tensor-core GEMM or FP64 pipe).
+    rr: "oblique" (Algorithm 2, the non-hermitian fallback only where Q^* S H Q is not
+    positive definite) or "fallback" (the non-hermitian fallback in every iteration).
+    h2: "implicit" (H applied twice per filter step, the paper's method) or "explicit"
+    (mixed precision only: the blocks of H^2 formed once, one product per step)."""
+    if h2 not in ("implicit", "explicit"):
+        raise ValueError("h2 must be 'implicit' or 'explicit'")
     if fp64_products not in ("tensor", "fp64"):
         raise ValueError("fp64_products must be 'tensor' or 'fp64'")
+    if rr not in ("oblique", "fallback"):
+        raise ValueError("rr must be 'oblique' or 'fallback'")
     A = _mat(A, "A")
     n = A.shape[0]
     B = _mat(B, "B", n)
@@ -227,7 +242,8 @@ def solve(A: torch.Tensor, B: torch.Tensor, nev: int, nex: int, deg: int = 20, t
              deg_min=deg if deg_min is None else deg_min, deg_max=deg if deg_max is None else deg_max,
              lanczos_steps=lanczos_steps, lanczos_vecs=lanczos_vecs, gamma=gamma, switch_tol=switch_tol,
              seed=seed, W0=_ptr(W0), V0=_ptr(V0), stream=ctypes.c_void_p(_stream(stream)),
-             fp64_products=0 if fp64_products == "tensor" else 1)
+             fp64_products=0 if fp64_products == "tensor" else 1, rr=0 if rr == "oblique" else 1,
+             h2=0 if h2 == "implicit" else 1)
     evals = torch.zeros(nev, dtype=torch.float64, device=A.device)
     evecs = torch.zeros((nev, 2 * n), dtype=torch.complex128, device=A.device)
     st = Stats(size=ctypes.sizeof(Stats))
@@ -306,6 +322,34 @@ def eig_general(G: torch.Tensor, stream=None):
     _check(lib().chase_bse_eig_general(_ptr(Gc), k, _ptr(lam), _ptr(Vc), ctypes.c_void_p(_stream(stream))),
            "chase_bse_eig_general")
     return lam, Vc.t()
+
+
+def h2_blocks(A: torch.Tensor, B: torch.Tensor, stream=None):
+    """chase_bse_h2_blocks: (P, Q) with H^2 = [[P, Q], [conj Q, conj P]], (n, n) complex128
+    row-major like A and B (FP64-accurate)."""
+    A = _mat(A, "A")
+    n = A.shape[0]
+    B = _mat(B, "B", n)
+    P = torch.empty((n, n), dtype=torch.complex128, device=A.device)
+    Q = torch.empty((n, n), dtype=torch.complex128, device=A.device)
+    _check(lib().chase_bse_h2_blocks(_ptr(A), _ptr(B), n, _ptr(P), _ptr(Q), ctypes.c_void_p(_stream(stream))),
+           "chase_bse_h2_blocks")
+    return P, Q
+
+
+def filter_h2(A: torch.Tensor, B: torch.Tensor, W: torch.Tensor, degs, mu1: float, mu_nevex: float, muN: float,
+              precision: str = "mixed", stream=None) -> torch.Tensor:
+    """chase_bse_filter_h2: the tensor-core filter with H^2 applied from its blocks (the
+    explicit-H^2 variant), in place on W (k, 2n); returns W."""
+    A = _mat(A, "A")
+    n = A.shape[0]
+    B = _mat(B, "B", n)
+    W = _block(W, "W", 2 * n)
+    k = W.shape[0]
+    d = (ctypes.c_int32 * max(k, 1))(*[int(x) for x in degs])
+    _check(lib().chase_bse_filter_h2(_ptr(A), _ptr(B), n, _ptr(W), k, d, mu1, mu_nevex, muN, _PREC[precision],
+                                     ctypes.c_void_p(_stream(stream))), "chase_bse_filter_h2")
+    return W
 
 
 def set_wait_limit(ns: int) -> None:

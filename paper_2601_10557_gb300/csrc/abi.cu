@@ -197,6 +197,37 @@ int chase_bse_eigh(const void* G, int64_t k, double* theta, void* V, int32_t met
   CB_GUARD(return eigh_impl((const cplx*)G, k, theta, (cplx*)V, method, thr, (cudaStream_t)stream);)
 }
 
+int chase_bse_h2_blocks(const void* A, const void* B, int64_t n, void* P, void* Q, void* stream) {
+  if (!A || !B || !P || !Q || n < 1) return CHASE_BSE_BAD_ARG;
+  if (!cb::mixed_available()) return CHASE_BSE_UNSUPPORTED;
+  CB_GUARD(return cb::form_h2((const cplx*)A, (const cplx*)B, n, (cplx*)P, (cplx*)Q, (cudaStream_t)stream);)
+}
+
+int chase_bse_filter_h2(const void* A, const void* B, int64_t n, void* W, int64_t k, const int32_t* degs, double mu1,
+                        double mu_nevex, double muN, int32_t precision, void* stream) {
+  if (k == 0) return CHASE_BSE_OK;
+  if (!A || !B || !W || !degs || n < 1 || k < 0 || !(mu1 > 0) || !(mu_nevex > mu1) || !(muN > mu_nevex))
+    return CHASE_BSE_BAD_ARG;
+  if (precision != CHASE_BSE_MIXED_BF16X3 && precision != CHASE_BSE_MIXED_BF16X6 &&
+      precision != CHASE_BSE_MIXED_FP16X3)
+    return CHASE_BSE_BAD_ARG;
+  for (int64_t i = 0; i < k; ++i)
+    if (degs[i] < 1) return CHASE_BSE_BAD_ARG;
+  if (!cb::mixed_available()) return CHASE_BSE_UNSUPPORTED;
+  CB_GUARD({
+    cudaStream_t s = (cudaStream_t)stream;
+    cb::Workspace ws(s);
+    cplx* P2 = nullptr;
+    cplx* Q2 = nullptr;
+    CB_TRY(ws.alloc(&P2, n * n));
+    CB_TRY(ws.alloc(&Q2, n * n));
+    CB_TRY(cb::form_h2((const cplx*)A, (const cplx*)B, n, P2, Q2, s));
+    std::vector<int> prec(k, 1);
+    return cb::filter((const cplx*)A, (const cplx*)B, n, (cplx*)W, k, degs, prec.data(), mu1, mu_nevex, muN,
+                      precision, nullptr, nullptr, s, nullptr, nullptr, P2, Q2);
+  })
+}
+
 int chase_bse_eig_general(const void* G, int64_t k, void* lam, void* V, void* stream) {
   if (k == 0) return CHASE_BSE_OK;
   if (!G || !lam || !V || k < 0 || k > ((int64_t)1 << 15)) return CHASE_BSE_BAD_ARG;

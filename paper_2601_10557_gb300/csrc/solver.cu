@@ -294,7 +294,7 @@ static int filter_fp64_sorted(const cplx* A, const cplx* B, int64_t n, cplx* Y0,
 
 int filter(const cplx* A, const cplx* B, int64_t n, cplx* W, int64_t k, const int* degs, const int* prec,
            double mu1, double mu_nevex, double muN, int scheme, const double* ritz, const cplx* R, cudaStream_t s,
-           FilterStats* fs, const SlicedOp* ph) {
+           FilterStats* fs, const SlicedOp* ph, const cplx* P2, const cplx* Q2) {
   if (k == 0) return CHASE_BSE_OK;
   const int64_t n2 = 2 * n;
   Workspace ws(s);
@@ -327,9 +327,9 @@ int filter(const cplx* A, const cplx* B, int64_t n, cplx* W, int64_t k, const in
         std::vector<double> rs(m);
         for (int64_t i = 0; i < m; ++i) rs[i] = ritz[idx[i]];
         CB_TRY(filter_mixed_correction_sorted(A, B, n, Y0, m, ds.data(), rs.data(), Rs, mu1, mu_nevex, muN, out,
-                                              scheme, s, fs));
+                                              scheme, s, fs, P2, Q2));
       } else {
-        CB_TRY(filter_mixed_sorted(A, B, n, Y0, m, ds.data(), mu1, mu_nevex, muN, out, scheme, s, fs));
+        CB_TRY(filter_mixed_sorted(A, B, n, Y0, m, ds.data(), mu1, mu_nevex, muN, out, scheme, s, fs, P2, Q2));
       }
     }
     CB_TRY(scatter_cols(W, out, didx, n2, m, s));
@@ -943,6 +943,30 @@ void degrees_update(const std::vector<double>& ritz, const std::vector<double>& 
   }
 }
 
+// One fallback Rayleigh-Ritz step of the solver on the general basis Q (2n x 2 kf): the kf
+// positive Ritz pairs (ritz host, Wpos 2n x kf) and their FP64 residual vectors and norms
+// (R 2n x kf, res device).  Fewer than kf Ritz values with positive real part:
+// QR_FAILED.
+static int rayleigh_ritz_fallback_step(const cplx* A, const cplx* B, int64_t n, const cplx* Q, int64_t kf,
+                                       double* ritz, cplx* Wpos, cplx* R, double* res, cudaStream_t s) {
+  const int64_t n2 = 2 * n, k = 2 * kf;
+  Workspace ws(s);
+  cplx* Wall;
+  double* lam;
+  CB_TRY(ws.alloc(&Wall, n2 * k));
+  CB_TRY(ws.alloc(&lam, kf));
+  std::vector<double> rz(k);
+  int64_t npos = 0;
+  CB_TRY(rayleigh_ritz_fallback(A, B, n, Q, k, rz.data(), Wall, &npos, s));
+  if (npos < kf) return CHASE_BSE_QR_FAILED;
+  for (int64_t i = 0; i < kf; ++i) ritz[i] = rz[i];
+  CB_CUDA(cudaMemcpyAsync(Wpos, Wall, sizeof(cplx) * n2 * kf, cudaMemcpyDeviceToDevice, s));
+  CB_CUDA(cudaMemcpyAsync(lam, ritz, sizeof(double) * kf, cudaMemcpyHostToDevice, s));
+  CB_TRY(residuals(A, B, n, Wpos, lam, kf, res, s, R));
+  CB_CUDA(cudaStreamSynchronize(s));
+  return CHASE_BSE_OK;
+}
+
 int solve(const cplx* A, const cplx* B, int64_t n, int64_t nev, int64_t nex, int deg, double tol,
           const chase_bse_opts* opts_in, double* evals, cplx* evecs, chase_bse_stats* stats) {
   chase_bse_opts o{};
@@ -968,6 +992,9 @@ int solve(const cplx* A, const cplx* B, int64_t n, int64_t nev, int64_t nex, int
        o.precision != CHASE_BSE_FP64_TC))
     return CHASE_BSE_BAD_ARG;
   if (o.fp64_products != 0 && o.fp64_products != 1) return CHASE_BSE_BAD_ARG;
+  if (o.rr != 0 && o.rr != 1) return CHASE_BSE_BAD_ARG;
+  if (o.h2 != 0 && o.h2 != 1) return CHASE_BSE_BAD_ARG;
+  if (o.h2 == 1 && (o.precision == CHASE_BSE_FP64 || o.precision == CHASE_BSE_FP64_TC)) return CHASE_BSE_BAD_ARG;
   const bool fp64tc = o.precision == CHASE_BSE_FP64_TC;
   const bool mixed = o.precision != CHASE_BSE_FP64 && !fp64tc;
   // FP64-accurate products on the tensor cores: FP64_TC always, mixed unless fp64_products
@@ -1034,6 +1061,16 @@ int solve(const cplx* A, const cplx* B, int64_t n, int64_t nev, int64_t nex, int
     CB_TRY(slice_hamiltonian(A, B, n, ph, s));
   }
 
+  // explicit-H^2 variant (not the paper's method): the blocks of H^2, formed once
+  cplx *P2 = nullptr, *Q2 = nullptr;
+  if (o.h2 == 1) {
+    clk.start();
+    CB_TRY(ws.alloc(&P2, n * n));
+    CB_TRY(ws.alloc(&Q2, n * n));
+    CB_TRY(form_h2(A, B, n, P2, Q2, s));
+    st.ms_h2 = clk.stop();
+  }
+
   // spectral bounds
   clk.start();
   double mu[4];
@@ -1066,14 +1103,18 @@ int solve(const cplx* A, const cplx* B, int64_t n, int64_t nev, int64_t nex, int
     clk.start();
     const bool corr = mixed && !ritz_keep.empty();
     CB_TRY(filter(A, B, n, W, kf, degs.data(), prec.data(), mu1, mu_ne, muN, scheme,
-                  corr ? ritz_keep.data() : nullptr, corr ? Rkeep : nullptr, s, &fs, sliced ? &ph : nullptr));
+                  corr ? ritz_keep.data() : nullptr, corr ? Rkeep : nullptr, s, &fs, sliced ? &ph : nullptr, P2,
+                  Q2));
     st.ms_filter += clk.stop();
     // orthonormalisation: W- = K conj(W+), Q = [S Y+, S Y-, W+, W-] R^{-1}, drop the locked part;
     // J-fixed basis (top halves) unless its CholeskyQR2 breaks down
     clk.start();
-    CB_TRY(build_jfixed(X, Ylock, locked, W, kf, n, s));
+    const bool force_fallback = o.rr == 1;
     bool jok = false;
-    CB_TRY(qr_jfixed(X, n, 2 * nevex, Qf, &jok, s, sliced));
+    if (!force_fallback) {
+      CB_TRY(build_jfixed(X, Ylock, locked, W, kf, n, s));
+      CB_TRY(qr_jfixed(X, n, 2 * nevex, Qf, &jok, s, sliced));
+    }
     int hh = 0;
     if (!jok) {
       CB_TRY(build_qr_input(X, Ylock, locked, W, kf, n, s));
@@ -1093,9 +1134,25 @@ int solve(const cplx* A, const cplx* B, int64_t n, int64_t nev, int64_t nex, int
     double jthr = 1e-8;
     for (int64_t i = 0; i < kf; ++i) jthr = std::min(jthr, 1e-4 * prev_res[i]);
     jthr = std::max(jthr, 2e-16);
-    int rs = jok ? rayleigh_ritz_jfixed(A, B, n, Qf + 2 * locked * n, 2 * kf, ritz.data(), Wpos, Rvec, res_d, s,
-                                        sliced ? &ph : nullptr, jthr)
-                 : rayleigh_ritz(A, B, n, Qf + 2 * locked * n2, 2 * kf, ritz.data(), Wpos, s, Rvec, res_d);
+    int rs = CHASE_BSE_NOT_DEFINITE;
+    if (!force_fallback)
+      rs = jok ? rayleigh_ritz_jfixed(A, B, n, Qf + 2 * locked * n, 2 * kf, ritz.data(), Wpos, Rvec, res_d, s,
+                                      sliced ? &ph : nullptr, jthr)
+               : rayleigh_ritz(A, B, n, Qf + 2 * locked * n2, 2 * kf, ritz.data(), Wpos, s, Rvec, res_d);
+    if (rs == CHASE_BSE_NOT_DEFINITE) {
+      // Q^* S H Q not positive definite (or the fallback asked for): the non-hermitian
+      // fallback (Section 4.4, last paragraph) in the general basis, where the diagonal of
+      // Q^* S Q is not identically zero as in the J-fixed one
+      if (jok) {
+        CB_TRY(build_qr_input(X, Ylock, locked, W, kf, n, s));
+        CB_TRY(qr(X, n2, 2 * nevex, Qf, &hh, s));
+        st.householder += hh;
+      }
+      const int fb = rayleigh_ritz_fallback_step(A, B, n, Qf + 2 * locked * n2, kf, ritz.data(), Wpos, Rvec, res_d, s);
+      // no usable positive Ritz values either: the problem is not definite
+      rs = (fb == CHASE_BSE_QR_FAILED && !force_fallback) ? CHASE_BSE_NOT_DEFINITE : fb;
+      st.fallback_rr += 1;
+    }
     st.ms_rr += clk.stop();
     if (rs != CHASE_BSE_OK) { status = rs; break; }
     clk.start();

@@ -19,11 +19,18 @@ enum FilterScheme : int { SCHEME_BF16X3 = 1, SCHEME_BF16X6 = 2, SCHEME_FP16X3 = 
 // (FilterScheme).  With ritz (host, per column) and R (device, 2n x k, the FP64
 // residual vectors H w - ritz w) the tensor-core columns use the correction form.
 // With ph (the sliced operand of slice_hamiltonian) the FP64 columns apply H by
-// FP64-accurate sliced GEMMs on the tensor cores instead of the FP64 pipe.
+// FP64-accurate sliced GEMMs on the tensor cores instead of the FP64 pipe.  With P2, Q2
+// (the blocks of H^2, see form_h2) the tensor-core columns apply H^2 from its blocks
+// (the explicit-H^2 variant).
 struct SlicedOp;
 int filter(const cplx* A, const cplx* B, int64_t n, cplx* W, int64_t k, const int* degs, const int* prec,
            double mu1, double mu_nevex, double muN, int scheme, const double* ritz, const cplx* R, cudaStream_t s,
-           FilterStats* fs, const SlicedOp* ph = nullptr);
+           FilterStats* fs, const SlicedOp* ph = nullptr, const cplx* P2 = nullptr, const cplx* Q2 = nullptr);
+
+// The blocks of H^2 = [[P2, Q2], [conj Q2, conj P2]]: P2 = A A - B conj(B),
+// Q2 = A B - B conj(A) (row-major n x n, like A and B), as the top block row
+// [A | -B] [[A, B], [conj B, conj A]], FP64-accurate sliced GEMMs (tc_dgemm.cu).
+int form_h2(const cplx* A, const cplx* B, int64_t n, cplx* P2, cplx* Q2, cudaStream_t s);
 
 // Lanczos bounds: mu1, mu_nevex, muN and rho_hat (max |theta|); with ph (the sliced
 // operand of slice_hamiltonian) H is applied on the tensor cores, FP64-accurate.
@@ -69,15 +76,16 @@ int gradient(const cplx* V, const double* w, int64_t n, int64_t nev, cplx* gA, c
 // Mixed-precision (tcgen05) filter on a column group whose columns are sorted
 // by descending degree; defined in the tensor-core translation unit.
 // scheme: a FilterScheme.
+// With P2, Q2 (the blocks of H^2, see form_h2) the filter applies H^2 from its blocks.
 int filter_mixed_sorted(const cplx* A, const cplx* B, int64_t n, cplx* Y0, int64_t k, const int* degs_sorted,
                         double mu1, double mu_nevex, double muN, cplx* out, int scheme, cudaStream_t s,
-                        FilterStats* fs);
+                        FilterStats* fs, const cplx* P2 = nullptr, const cplx* Q2 = nullptr);
 // Correction form (see tc_filter.cu): V holds Ritz vectors, ritz their values,
 // R = H V - V diag(ritz) (FP64); out = p(H^2) V.
 int filter_mixed_correction_sorted(const cplx* A, const cplx* B, int64_t n, cplx* V, int64_t k,
                                    const int* degs_sorted, const double* ritz_sorted, const cplx* R, double mu1,
                                    double mu_nevex, double muN, cplx* out, int scheme, cudaStream_t s,
-                                   FilterStats* fs);
+                                   FilterStats* fs, const cplx* P2 = nullptr, const cplx* Q2 = nullptr);
 bool mixed_available();
 
 }  // namespace cb

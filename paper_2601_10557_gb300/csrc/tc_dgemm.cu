@@ -22,6 +22,7 @@
 #include <cmath>
 
 #include "tc_common.cuh"
+#include "solver.cuh"
 #include "tc_dgemm.cuh"
 
 namespace cb {
@@ -371,6 +372,38 @@ struct HamSrc {  // rows of P': y = A x + B conj(x) in (re, im) interleaved form
   }
 };
 
+// The blocks of H^2 as C = [A | -B] R, R = [[A, B], [conj B, conj A]], computed as
+// C^T = R^T [A | -B]^T so that the result lands row-major: the A operand holds the
+// real-form rows of the columns j0 + r/2 of R's left (part 0: P2) or right (part 1: Q2)
+// block column, the B operand the rows of [A | -B] as (re, im) pairs.
+struct H2ColsSrc {
+  const cplx* A;
+  const cplx* B;
+  int64_t n, j0;
+  int part;
+  __device__ double2 pair(int64_t r, int64_t l) const {
+    const int64_t j = j0 + (r >> 1);
+    cplx v;
+    if (l < n) v = part == 0 ? A[l * n + j] : B[l * n + j];
+    else v = cconj(part == 0 ? B[(l - n) * n + j] : A[(l - n) * n + j]);
+    // row 2j: (Re, -Im); row 2j + 1: (Im, Re) -> (Re, Im) of sum_l R_lj w_l for w pairs (Re, Im)
+    return (r & 1) == 0 ? make_double2(v.x, -v.y) : make_double2(v.y, v.x);
+  }
+};
+struct H2RowsSrc {  // row i of [A | -B] as (re, im) pairs
+  const cplx* A;
+  const cplx* B;
+  int64_t n;
+  __device__ double2 pair(int64_t i, int64_t l) const {
+    if (l < n) {
+      const cplx v = A[i * n + l];
+      return make_double2(v.x, v.y);
+    }
+    const cplx v = B[i * n + (l - n)];
+    return make_double2(-v.x, -v.y);
+  }
+};
+
 struct ComplexRowsSrc {  // row r of the complex column-major M, optionally conjugated
   const cplx* M;
   int64_t ld;
@@ -527,6 +560,30 @@ int hop_sliced(const SlicedOp& ph, const cplx* W, int64_t n, int64_t k, cplx* ou
   timer_end(tid, s);
   count_launch();
   CB_LAUNCH();
+  return CHASE_BSE_OK;
+}
+
+int form_h2(const cplx* A, const cplx* B, int64_t n, cplx* P2, cplx* Q2, cudaStream_t s) {
+  Workspace ws(s);
+  SlicedOp rows;  // [A | -B]: n rows of 2n complex entries
+  CB_TRY(sliced_alloc(ws, rows, n, 4 * n, s));
+  CB_TRY(tcd::run_slice(tcd::H2RowsSrc{A, B, n}, rows, s));
+  // columns of R in chunks: the A operand of a chunk of cj columns holds 7 digit planes of
+  // 2 cj x 4n BF16 values (about 8 GB at most)
+  int64_t cj = std::max<int64_t>(64, (int64_t)(8.0e9 / (112.0 * (double)n)) / 64 * 64);
+  cj = std::min(cj, n);
+  for (int part = 0; part < 2; ++part) {
+    cplx* out = part == 0 ? P2 : Q2;
+    for (int64_t j0 = 0; j0 < n; j0 += cj) {
+      const int64_t m = std::min(cj, n - j0);
+      Workspace cws(s);
+      SlicedOp cols;
+      CB_TRY(sliced_alloc(cws, cols, 2 * m, 4 * n, s));
+      CB_TRY(tcd::run_slice(tcd::H2ColsSrc{A, B, n, j0, part}, cols, s));
+      // C^T[2(j - j0) + t][i] -> (Re, Im) of C_ij at double 2 (i n + j) + t
+      CB_TRY(sliced_gemm(cols, rows, 1.0, reinterpret_cast<double*>(out + j0), 1, 2 * n, false, s));
+    }
+  }
   return CHASE_BSE_OK;
 }
 

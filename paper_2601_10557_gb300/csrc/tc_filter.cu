@@ -153,6 +153,7 @@ struct Geo {
 
 struct Epi {
   int mode;           // 0: operand pieces, 1: recurrence, 2: H X + gamma X
+  int h2;             // 1: the operand holds [P | Q] of H^2 = [[P, Q], [conj Q, conj P]]
   int64_t n, k;       // rows of P, active vectors
   int64_t kpad;       // elements per piece row
   void* out[3];       // output operand pieces (NPW used)
@@ -518,7 +519,9 @@ __global__ void __launch_bounds__(Geo<SCH, BNT, FL>::THREADS, 1)
           const float* v = sum + c * 32;
           const float vs = exp2i(-ep.vexp_in[vg]);  // and the scaling of the input vector
           const float2 ht = make_float2(v[4 * t] * rs * vs, v[4 * t + 1] * rs * vs);        // (H x)_top(row)
-          const float2 hb = make_float2(-v[4 * t + 2] * rs * vs, v[4 * t + 3] * rs * vs);   // (H x)_bot(row)
+          // (H x)_bot(row) = -conj(P u); with the blocks of H^2, +conj(P u)
+          const float2 hb = ep.h2 ? make_float2(v[4 * t + 2] * rs * vs, -v[4 * t + 3] * rs * vs)
+                                  : make_float2(-v[4 * t + 2] * rs * vs, v[4 * t + 3] * rs * vs);
           const int64_t ot = vg * n2 + row, ob = ot + n;
           float2 zt = ht, zb = hb;
           if (ep.mode == 1 && rvalid) {
@@ -831,32 +834,44 @@ static int apply(const POperand& P, const CUtensorMap* bmap, Epi ep, cudaStream_
 // with the source term alpha_j p_j(m_i) r2_i (divided differences of the
 // three-term recurrence).  The low-precision error then scales with the
 // residual of v_i instead of with v_i.
+//
+// With P2, Q2 (the blocks of H^2 = [[P2, Q2], [conj Q2, conj P2]], row-major n x n) the
+// filter applies H^2 from its blocks, one launch per step (the explicit-H^2 variant, not
+// the paper's method); H itself (A, B) is then used only for the correction source.
 template <int SCH, int BNT, int FL>
 static int filter_impl(const cplx* A, const cplx* B, int64_t n, const cplx* Y0, int64_t k, const int* degs,
                        double mu1, double mu_nevex, double muN, cplx* out, const double* ritz, const cplx* R,
-                       cudaStream_t s, FilterStats* fs) {
+                       cudaStream_t s, FilterStats* fs, const cplx* P2, const cplx* Q2) {
   using T = typename Scheme<SCH>::T;
   constexpr int NPW = Scheme<SCH>::NPW;
   constexpr bool BF = Piece<T>::BF16;
   if (k == 0) return CHASE_BSE_OK;
   const int64_t n2 = 2 * n;
+  const bool expl = P2 != nullptr && Q2 != nullptr;
+  const bool corr = (ritz != nullptr && R != nullptr);
   Workspace ws(s);
-  POperand P;
-  CB_TRY((prepare_p<SCH, BNT>(A, B, n, ws, P, s)));
+  POperand P, PH2;  // [A | B] (H), [P2 | Q2] (H^2)
+  if (!expl || corr) CB_TRY((prepare_p<SCH, BNT>(A, B, n, ws, P, s)));
+  if (expl) CB_TRY((prepare_p<SCH, BNT>(P2, Q2, n, ws, PH2, s)));
+  const POperand& PK = expl ? PH2 : P;  // the operand of the recurrence (its kpad and pieces layout)
+  const int64_t kpad = PK.kpad;  // the same for both operands (4n padded)
   const int64_t rows = ((4 * k + BNT - 1) / BNT) * BNT;  // whole tiles
   Pieces Zp{}, Tp{};
   CUtensorMap mZ[3], mT[3];
   for (int q = 0; q < NPW; ++q) {
     T *zq, *tq;
-    CB_TRY(ws.alloc(&zq, rows * P.kpad));
-    CB_TRY(ws.alloc(&tq, rows * P.kpad));
+    CB_TRY(ws.alloc(&zq, rows * kpad));
+    CB_TRY(ws.alloc(&tq, rows * kpad));
     Zp.p[q] = zq;
     Tp.p[q] = tq;
-    CB_CUDA(cudaMemsetAsync(zq, 0, sizeof(T) * rows * P.kpad, s));
-    CB_CUDA(cudaMemsetAsync(tq, 0, sizeof(T) * rows * P.kpad, s));
-    CB_TRY(make_map(&mZ[q], zq, P.kpad, rows, BNT, BF, Geo<SCH, BNT, FL>::BK));
-    CB_TRY(make_map(&mT[q], tq, P.kpad, rows, BNT, BF, Geo<SCH, BNT, FL>::BK));
+    CB_CUDA(cudaMemsetAsync(zq, 0, sizeof(T) * rows * kpad, s));
+    CB_CUDA(cudaMemsetAsync(tq, 0, sizeof(T) * rows * kpad, s));
+    CB_TRY(make_map(&mZ[q], zq, kpad, rows, BNT, BF, Geo<SCH, BNT, FL>::BK));
+    CB_TRY(make_map(&mT[q], tq, kpad, rows, BNT, BF, Geo<SCH, BNT, FL>::BK));
   }
+  // explicit H^2: the pieces of Z_j alternate between the two sets (j even: Zp)
+  Pieces* zbuf[2] = {&Zp, &Tp};
+  const CUtensorMap* zmap[2] = {mZ, mT};
   float2 *Zb[3], *src = nullptr;
   float* gam;
   int* err;
@@ -899,8 +914,9 @@ static int filter_impl(const cplx* A, const cplx* B, int64_t n, const cplx* Y0, 
   auto slotZ = [&](int j) { return (int64_t)j * k; };
   auto slotT = [&](int j) { return (int64_t)(maxdeg + 1 + j) * k; };
   const int64_t slotR = (int64_t)(2 * maxdeg + 1) * k, slotS = (int64_t)(2 * maxdeg + 2) * k;
-  float L = 0.0f;
-  CB_CUDA(cudaMemcpyAsync(&L, P.L, sizeof(float), cudaMemcpyDeviceToHost, s));
+  float L = 0.0f, L2 = 0.0f;  // largest absolute row sums of [A | B] and [P2 | Q2]
+  if (!expl || corr) CB_CUDA(cudaMemcpyAsync(&L, P.L, sizeof(float), cudaMemcpyDeviceToHost, s));
+  if (expl) CB_CUDA(cudaMemcpyAsync(&L2, PH2.L, sizeof(float), cudaMemcpyDeviceToHost, s));
   CB_CUDA(cudaStreamSynchronize(s));
 
   std::vector<double> al(maxdeg), be(maxdeg);  // alpha_j, beta_j of the scaled recurrence
@@ -915,7 +931,6 @@ static int filter_impl(const cplx* A, const cplx* B, int64_t n, const cplx* Y0, 
       sigma = sn;
     }
   }
-  const bool corr = (ritz != nullptr && R != nullptr);
   std::vector<double> pj;  // p_j(m_i), j = 0 .. maxdeg
   if (corr) {
     pj.assign((size_t)(maxdeg + 1) * k, 0.0);
@@ -941,7 +956,7 @@ static int filter_impl(const cplx* A, const cplx* B, int64_t n, const cplx* Y0, 
   if (!corr) {
     col_amax_kernel<<<(unsigned)k, 256, 0, s>>>(Y0, n2, amax + slotZ(0), vexp + slotZ(0));
     count_launch();
-    pack_kernel<T, NPW><<<gsz(n * k), 256, 0, s>>>(Y0, n, k, Zb[0], Zp, 1, P.kpad, vexp + slotZ(0));  // Z_0 = W
+    pack_kernel<T, NPW><<<gsz(n * k), 256, 0, s>>>(Y0, n, k, Zb[0], Zp, 1, kpad, vexp + slotZ(0));  // Z_0 = W
     count_launch();
     CB_LAUNCH();
   } else {
@@ -949,18 +964,18 @@ static int filter_impl(const cplx* A, const cplx* B, int64_t n, const cplx* Y0, 
     CB_TRY(ws.alloc(&src, n2 * k));
     col_amax_kernel<<<(unsigned)k, 256, 0, s>>>(R, n2, amax + slotR, vexp + slotR);
     count_launch();
-    pack_kernel<T, NPW><<<gsz(n * k), 256, 0, s>>>(R, n, k, Zb[2], Zp, 1, P.kpad, vexp + slotR);
+    pack_kernel<T, NPW><<<gsz(n * k), 256, 0, s>>>(R, n, k, Zb[2], Zp, 1, kpad, vexp + slotR);
     count_launch();
     for (int64_t i = 0; i < k; ++i) gh[i] = (float)ritz[i];
     CB_CUDA(cudaMemcpyAsync(gam, gh.data(), sizeof(float) * k, cudaMemcpyHostToDevice, s));
     Epi ep{};
-    ep.mode = 2; ep.n = n; ep.k = k; ep.kpad = P.kpad; ep.Znext = src; ep.Zcur = Zb[2]; ep.gamma = gam; ep.err = err;
+    ep.mode = 2; ep.n = n; ep.k = k; ep.kpad = kpad; ep.Znext = src; ep.Zcur = Zb[2]; ep.gamma = gam; ep.err = err;
     ep.vexp_in = vexp + slotR;
     ep.amax_out = amax + slotS;
     sk(ep);
     CB_TRY((apply<SCH, BNT, FL>)(P, mZ, ep, s));
     CB_CUDA(cudaMemsetAsync(Zb[0], 0, sizeof(float2) * n2 * k, s));
-    scale_pack_kernel<T, NPW><<<gsz(n * k), 256, 0, s>>>(src, n, k, (float)al[0], Zb[1], Zp, P.kpad,
+    scale_pack_kernel<T, NPW><<<gsz(n * k), 256, 0, s>>>(src, n, k, (float)al[0], Zb[1], expl ? Tp : Zp, kpad,
                                                           amax + slotS, amax + slotZ(1), vexp + slotZ(1));
     count_launch();
     CB_LAUNCH();
@@ -970,7 +985,39 @@ static int filter_impl(const cplx* A, const cplx* B, int64_t n, const cplx* Y0, 
       fs->launches += 1;
     }
   }
-  for (int j = j0; j < maxdeg; ++j) {
+  for (int j = j0; j < maxdeg && expl; ++j) {
+    // Z_{j+1} = alpha (H^2 Z_j - c Z_j) + beta Z_{j-1} (+ source): one launch on [P2 | Q2]
+    int64_t kj = 0;
+    while (kj < k && degs[kj] >= j + 1) ++kj;
+    Epi ep{};
+    ep.mode = 1; ep.h2 = 1; ep.n = n; ep.k = kj; ep.kpad = kpad; ep.err = err;
+    sk(ep);
+    for (int q = 0; q < NPW; ++q) ep.out[q] = zbuf[(j + 1) % 2]->p[q];
+    ep.Znext = Zb[(j + 1) % 3]; ep.Zcur = Zb[j % 3]; ep.Zprev = Zb[(j + 2) % 3];
+    ep.alpha = (float)al[j]; ep.beta = (float)be[j]; ep.c = (float)c;
+    ep.vexp_in = vexp + slotZ(j);
+    ep.vexp_out = vexp + slotZ(j + 1);
+    ep.amax_out = amax + slotZ(j + 1);
+    ep.amax_a = amax + slotZ(j);
+    ep.amax_b = amax + slotZ(j);
+    ep.amax_c = amax + slotZ(j > 0 ? j - 1 : 0);
+    ep.ca = (float)(std::fabs(al[j]) * L2);
+    ep.cb = (float)std::fabs(al[j] * c);
+    ep.cc = (float)std::fabs(be[j]);
+    if (corr) {
+      for (int64_t i = 0; i < kj; ++i) gh[i] = (float)(al[j] * pj[(size_t)j * k + i]);
+      CB_CUDA(cudaMemcpyAsync(gam, gh.data(), sizeof(float) * kj, cudaMemcpyHostToDevice, s));
+      ep.src = src;
+      ep.gamma = gam;
+      ep.amax_d = amax + slotS;
+    }
+    CB_TRY((apply<SCH, BNT, FL>)(PH2, zmap[j % 2], ep, s));
+    if (fs) {
+      fs->flops += 32.0 * (double)n * (double)n * (double)kj;  // the product with the blocks of H^2
+      fs->launches += 1;
+    }
+  }
+  for (int j = j0; j < maxdeg && !expl; ++j) {
     int64_t kj = 0;
     while (kj < k && degs[kj] >= j + 1) ++kj;
     Epi e1p{};
@@ -1064,21 +1111,21 @@ bool mixed_available() {
 template <int SCH>
 static int filter_dispatch(const cplx* A, const cplx* B, int64_t n, cplx* V, int64_t k, const int* degs,
                            double mu1, double mu_nevex, double muN, cplx* out, const double* ritz, const cplx* R,
-                           cudaStream_t s, FilterStats* fs) {
+                           cudaStream_t s, FilterStats* fs, const cplx* P2, const cplx* Q2) {
   return tc::filter_impl<SCH, 128, tc::Scheme<SCH>::FLUSH>(A, B, n, V, k, degs, mu1, mu_nevex, muN, out, ritz, R,
-                                                            s, fs);
+                                                            s, fs, P2, Q2);
 }
 
 static int filter_scheme(int scheme, const cplx* A, const cplx* B, int64_t n, cplx* V, int64_t k, const int* degs,
                          double mu1, double mu_nevex, double muN, cplx* out, const double* ritz, const cplx* R,
-                         cudaStream_t s, FilterStats* fs) {
+                         cudaStream_t s, FilterStats* fs, const cplx* P2, const cplx* Q2) {
   switch (scheme) {
     case SCHEME_BF16X3:
-      return filter_dispatch<tc::SCH_BF16X3>(A, B, n, V, k, degs, mu1, mu_nevex, muN, out, ritz, R, s, fs);
+      return filter_dispatch<tc::SCH_BF16X3>(A, B, n, V, k, degs, mu1, mu_nevex, muN, out, ritz, R, s, fs, P2, Q2);
     case SCHEME_BF16X6:
-      return filter_dispatch<tc::SCH_BF16X6>(A, B, n, V, k, degs, mu1, mu_nevex, muN, out, ritz, R, s, fs);
+      return filter_dispatch<tc::SCH_BF16X6>(A, B, n, V, k, degs, mu1, mu_nevex, muN, out, ritz, R, s, fs, P2, Q2);
     case SCHEME_FP16X3:
-      return filter_dispatch<tc::SCH_FP16X3>(A, B, n, V, k, degs, mu1, mu_nevex, muN, out, ritz, R, s, fs);
+      return filter_dispatch<tc::SCH_FP16X3>(A, B, n, V, k, degs, mu1, mu_nevex, muN, out, ritz, R, s, fs, P2, Q2);
     default:
       return CHASE_BSE_BAD_ARG;
   }
@@ -1086,15 +1133,16 @@ static int filter_scheme(int scheme, const cplx* A, const cplx* B, int64_t n, cp
 
 int filter_mixed_sorted(const cplx* A, const cplx* B, int64_t n, cplx* Y0, int64_t k, const int* degs_sorted,
                         double mu1, double mu_nevex, double muN, cplx* out, int scheme, cudaStream_t s,
-                        FilterStats* fs) {
-  return filter_scheme(scheme, A, B, n, Y0, k, degs_sorted, mu1, mu_nevex, muN, out, nullptr, nullptr, s, fs);
+                        FilterStats* fs, const cplx* P2, const cplx* Q2) {
+  return filter_scheme(scheme, A, B, n, Y0, k, degs_sorted, mu1, mu_nevex, muN, out, nullptr, nullptr, s, fs, P2,
+                       Q2);
 }
 
 int filter_mixed_correction_sorted(const cplx* A, const cplx* B, int64_t n, cplx* V, int64_t k,
                                    const int* degs_sorted, const double* ritz_sorted, const cplx* R, double mu1,
                                    double mu_nevex, double muN, cplx* out, int scheme, cudaStream_t s,
-                                   FilterStats* fs) {
-  return filter_scheme(scheme, A, B, n, V, k, degs_sorted, mu1, mu_nevex, muN, out, ritz_sorted, R, s, fs);
+                                   FilterStats* fs, const cplx* P2, const cplx* Q2) {
+  return filter_scheme(scheme, A, B, n, V, k, degs_sorted, mu1, mu_nevex, muN, out, ritz_sorted, R, s, fs, P2, Q2);
 }
 
 }  // namespace cb

@@ -126,3 +126,23 @@ def test_fallback_rr_zero_diagonal_is_rejected(pkg):
     with pytest.raises(pkg.ChaseBSEError) as e:
         _rr(pkg, P, Q)
     assert e.value.status == -5
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_solve_with_the_fallback_rr_matches_brute_force(pkg, precision):
+    """Algorithm 3 with the fallback Rayleigh-Ritz in every iteration (as the oracle's
+    solver with rr="fallback") still returns the nev smallest positive eigenpairs."""
+    from tests.gpu_util import starts, to_dev
+    n, nev, nex = 64, 6, 6
+    P = bi.make_problem(n, seed=0)
+    A, B = problem_on_device(P)
+    W0, V0 = starts(n, nev + nex, 0)
+    lam, V, st = pkg.solve(A, B, nev, nex, 12, 1e-10, W0=to_dev(W0), V0=to_dev(V0), deg_min=4, deg_max=24,
+                           maxiter=40, rr="fallback", precision=precision)
+    ref, _ = dense.smallest_positive(P.A, P.B, nev)
+    np.testing.assert_allclose(lam.cpu().numpy(), ref, rtol=1e-10)
+    H = dense.hamiltonian(P.A, P.B)
+    Vg = V.cpu().numpy().T
+    R = H @ Vg - Vg * lam.cpu().numpy()[None, :]
+    assert np.linalg.norm(R, axis=0).max() <= 1e-9 * np.linalg.norm(H, 2)
+    assert st["fallback_rr"] == st["iterations"]
