@@ -500,16 +500,22 @@ def main():
     per_launch_ms = g_ms / max(g_n, 1)
     flops_per_launch = g_flops / max(g_n, 1)
     achieved = g_flops / (g_ms / 1e3) / 1e12 if g_ms > 0 else 0.0
+    # the launches are timed inside steps of tens of seconds under the power cap: the
+    # sustained measured peak is their denominator; the full-width check times short calls
+    # alone and takes the burst peak
     peaks, peak_src = load_peaks()
+    sustained = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+    kind_s = "sustained" if "bf16_tflops_sustained" in peaks else "burst"
     if precision == "fp64":
-        peak = peaks["bf16_tflops"] * NOMINAL["fp64"] / NOMINAL["bf16"]
-        peak_note = f"{peak_src} bf16 burst x nominal fp64/bf16 ratio (1.25/2250)"
+        peak = sustained * NOMINAL["fp64"] / NOMINAL["bf16"]
+        peak_burst = peaks["bf16_tflops"] * NOMINAL["fp64"] / NOMINAL["bf16"]
+        peak_note = f"{peak_src} bf16 {kind_s} x nominal fp64/bf16 ratio (1.25/2250)"
     elif precision == "bf16x6":
-        peak = peaks["bf16_tflops"] / 6.0
-        peak_note = f"{peak_src} bf16 burst / 6 (six 16-bit products per FP32-accurate product)"
+        peak, peak_burst = sustained / 6.0, peaks["bf16_tflops"] / 6.0
+        peak_note = f"{peak_src} bf16 {kind_s} / 6 (six 16-bit products per FP32-accurate product)"
     else:
-        peak = peaks["bf16_tflops"] / 3.0
-        peak_note = (f"{peak_src} bf16 burst / 3 (three 16-bit products per FP32-accurate product; "
+        peak, peak_burst = sustained / 3.0, peaks["bf16_tflops"] / 3.0
+        peak_note = (f"{peak_src} bf16 {kind_s} / 3 (three 16-bit products per FP32-accurate product; "
                      "the nominal FP16 and BF16 dense rates are equal)")
     traffic_full, traffic_src = traffic_for(args.workload) if precision in ("mixed", "fp16x3") else (None, "n/a")
     traffic = None
@@ -527,7 +533,8 @@ def main():
             "method": "sum of 32 n^2 k over the filter GEMM launches of the timed steps / their summed "
                       "device time (a CUDA event pair around each launch on its stream)",
             "full_width_check": {
-                "achieved": full_achieved, "frac": full_achieved / peak, "launch_ms": full_launch_ms,
+                "achieved": full_achieved, "frac": full_achieved / peak_burst, "peak": peak_burst,
+                "peak_source": f"{peak_src} bf16 burst / 3 (short calls timed alone)", "launch_ms": full_launch_ms,
                 "flops_per_launch": full_flops,
                 "method": f"(t(degree {d2}) - t(degree {d1})) / {gemm_launches} launches, filter calls over "
                           f"{nevex} columns, CUDA events, best of 2",
