@@ -18,6 +18,7 @@
 // rotation whose pivot is below the threshold is the identity, so a sweep on a
 // matrix that is already diagonal leaves it unchanged.
 #include <algorithm>
+#include <cstdio>
 #include <cmath>
 #include <utility>
 #include <vector>
@@ -78,6 +79,8 @@ struct Params {
   R t2, f2;
   GridSync* gsync;
   int* err;
+  int* rotated;  // nb/2 flags: pair g of the current round applied a rotation
+  int* nrot;     // rotated pairs, summed over the sweep
 };
 
 // global index of local index l (< 64) of the pair (I, J)
@@ -97,6 +100,8 @@ __device__ void solve_pair(const Params<R>& P, int r, int g, typename Cx<R>::T* 
     S[i + j * LD] = __ldcg(P.G + gidx(i, I, J) + (int64_t)gidx(j, I, J) * P.kp);
     Uu[i + j * LD] = Cx<R>::mk(i == j ? R(1) : R(0), R(0));
   }
+  __shared__ int any;
+  if (tid == 0) any = 0;
   __syncthreads();
   for (int ir = 0; ir < PS - 1; ++ir) {
     if (tid < BS) {
@@ -104,6 +109,7 @@ __device__ void solve_pair(const Params<R>& P, int r, int g, typename Cx<R>::T* 
       jpair32(tid, ir, PS, p, q);
       const C x = S[p + q * LD];
       rot[tid] = rotation<R>(S[p + p * LD].x, S[q + q * LD].x, x.x, x.y, P.t2, P.f2);
+      if (rot[tid].s != R(0)) any = 1;
     }
     __syncthreads();
     // S <- J^* S J on every 2 x 2 block (slots a, b)
@@ -146,8 +152,16 @@ __device__ void solve_pair(const Params<R>& P, int r, int g, typename Cx<R>::T* 
     }
     __syncthreads();
   }
+  // U stays exactly the identity when no rotation was applied: phase B then skips the
+  // tiles of pairs that both kept the identity (a tile with one rotated pair still reads
+  // this U)
   C* Ug = P.U + (int64_t)g * PS * PS;
   for (int e = tid; e < PS * PS; e += THREADS) Ug[e] = Uu[(e % PS) + (e / PS) * LD];
+  if (tid == 0) {
+    P.rotated[g] = any;
+    if (any) atomicAdd(P.nrot, 1);
+  }
+  __syncthreads();
 }
 
 // out (64 x 64, ld LD) = op(X) * Y with X, Y 64 x 64 (ld LD) in shared memory;
@@ -287,10 +301,11 @@ __global__ void __launch_bounds__(THREADS, 1) bj_sweep_kernel(Params<R> P) {
           rem -= half - g;
           ++g;
         }
-        update_tile<R>(P, r, g, g + rem, T, Ua, Ub);
+        // U_g^* T U_h = T when neither pair rotated
+        if (__ldcg(P.rotated + g) || __ldcg(P.rotated + g + rem)) update_tile<R>(P, r, g, g + rem, T, Ua, Ub);
       } else {
         const int v = item - ntile;
-        update_v<R>(P, r, v / half, v % half, T, Ua);
+        if (__ldcg(P.rotated + v % half)) update_v<R>(P, r, v / half, v % half, T, Ua);
       }
     }
     if (!grid_barrier(P.gsync, P.err)) return;
@@ -373,8 +388,10 @@ static int run(const cplx* G, int64_t k, cplx* V, double* theta, double t, doubl
   Workspace ws(s);
   C *Gp, *Vp, *U;
   GridSync* gsync;
-  int *err, *cnt;
+  int *err, *cnt, *rotated, *nrot;
   double* red;
+  CB_TRY(ws.alloc(&rotated, nb / 2));
+  CB_TRY(ws.alloc(&nrot, 1));
   CB_TRY(ws.alloc(&Gp, kp * kp));
   CB_TRY(ws.alloc(&Vp, kp * kp));
   CB_TRY(ws.alloc(&U, (int64_t)(nb / 2) * PS * PS));
@@ -405,6 +422,8 @@ static int run(const cplx* G, int64_t k, cplx* V, double* theta, double t, doubl
   P.f2 = (R)(f * f * n2);
   P.gsync = gsync;
   P.err = err;
+  P.rotated = rotated;
+  P.nrot = nrot;
   const unsigned grid = (unsigned)std::min<int64_t>((int64_t)sms, std::max<int64_t>(1, (int64_t)nb * nb));
   int hc = 1, herr = 0, sw = 0;
   CB_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int), s));
@@ -414,6 +433,7 @@ static int run(const cplx* G, int64_t k, cplx* V, double* theta, double t, doubl
   CB_CUDA(cudaStreamSynchronize(s));
   for (; hc > 0 && sw < max_sweeps; ++sw) {
     CB_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int), s));
+    CB_CUDA(cudaMemsetAsync(nrot, 0, sizeof(int), s));
     void* args[] = {&P};
     if (cudaLaunchCooperativeKernel((const void*)bj_sweep_kernel<R>, dim3(grid), dim3(THREADS), args, smem, s) !=
         cudaSuccess) {
@@ -425,8 +445,13 @@ static int run(const cplx* G, int64_t k, cplx* V, double* theta, double t, doubl
     count_launch();
     CB_CUDA(cudaMemcpyAsync(&hc, cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
     CB_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    int hn = 0;
+    if (verbose()) CB_CUDA(cudaMemcpyAsync(&hn, nrot, sizeof(int), cudaMemcpyDeviceToHost, s));
     CB_CUDA(cudaStreamSynchronize(s));
     if (herr) return CHASE_BSE_DEVICE_TIMEOUT;
+    if (verbose())
+      fprintf(stderr, "[chase_bse] block jacobi k %ld sweep %d: %d of %d block pairs rotated, %d couplings left\n",
+              (long)k, sw + 1, hn, (nb - 1) * (nb / 2), hc);
   }
   if (sweeps_out) *sweeps_out = sw;
   bj_out_kernel<R><<<gsz(k * k), 256, 0, s>>>(Vp, Gp, k, kp, e, V, theta);
