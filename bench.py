@@ -500,12 +500,14 @@ def main():
     per_launch_ms = g_ms / max(g_n, 1)
     flops_per_launch = g_flops / max(g_n, 1)
     achieved = g_flops / (g_ms / 1e3) / 1e12 if g_ms > 0 else 0.0
-    # the launches are timed inside steps of tens of seconds under the power cap: the
-    # sustained measured peak is their denominator; the full-width check times short calls
+    # launches timed inside steps of several seconds or more (the sustained peak was
+    # measured over a 4 s loop) take the sustained measured peak as their denominator,
+    # launches in shorter steps the burst peak; the full-width check times short calls
     # alone and takes the burst peak
     peaks, peak_src = load_peaks()
-    sustained = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
-    kind_s = "sustained" if "bf16_tflops_sustained" in peaks else "burst"
+    long_steps = tts >= 4.0 and "bf16_tflops_sustained" in peaks
+    sustained = peaks["bf16_tflops_sustained"] if long_steps else peaks["bf16_tflops"]
+    kind_s = "sustained (steps of %.1f s)" % tts if long_steps else "burst (steps of %.2f s)" % tts
     if precision == "fp64":
         peak = sustained * NOMINAL["fp64"] / NOMINAL["bf16"]
         peak_burst = peaks["bf16_tflops"] * NOMINAL["fp64"] / NOMINAL["bf16"]
