@@ -219,6 +219,16 @@ def host_inputs(wl, seed):
     return A, B, W0
 
 
+def config_dict(args, wl, precision, world):
+    """The workload's description, the same in both arms' JSON lines."""
+    n = wl["n"]
+    return {"workload": args.workload, "n": n, "H": 2 * n, "nev": wl["nev"], "nex": wl["nex"],
+            "deg": f"{wl['deg_min']}-{wl['deg_max']} adaptive, first {wl['deg']}", "tol": wl["tol"],
+            "spectrum": wl["spec"], "beta": wl["beta"], "precision": precision,
+            "l2": "inputs larger than L2 (A and B: %.0f MB)" % (2 * n * n * 16 / 1e6),
+            "parallelism": f"replicas x{world}"}
+
+
 def run_reference(args, wl, rank, world):
     if rank != 0:
         return
@@ -236,8 +246,7 @@ def run_reference(args, wl, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "TFLOP/s", "n_gpus": args.gpus,
             "steps": steps, "warmup": warm, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "n": wl["n"], "H": 2 * wl["n"], "nev": wl["nev"],
-                       "nex": wl["nex"], "tol": wl["tol"], "spectrum": wl["spec"], "beta": wl["beta"]},
+            "config": config_dict(args, wl, "mixed" if args.precision == "auto" else args.precision, world),
             "cpu_baseline": {"value": v, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
                              "sample": f"per step: one H^2 step (degree 1) of the oracle filter over {cols} "
                                        "columns of the same workload"},
@@ -634,11 +643,7 @@ def main():
             "warmup": warm, "ms_per_step": tts_max * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if precision == "fp64" else "fp16x3+f64",
             "data": "synthetic",
-            "config": {"workload": args.workload, "n": n, "H": 2 * n, "nev": nev, "nex": nex,
-                       "deg": f"{wl['deg_min']}-{wl['deg_max']} adaptive, first {wl['deg']}", "tol": wl["tol"],
-                       "spectrum": wl["spec"], "beta": wl["beta"], "precision": precision,
-                       "l2": "inputs larger than L2 (A and B: %.0f MB)" % (2 * n * n * 16 / 1e6),
-                       "parallelism": f"replicas x{world}"},
+            "config": config_dict(args, wl, precision, world),
             "time_to_solution_s": tts_max,
             "time_to_solution_fp64_s": (fp64 or {}).get("time_to_solution_s") if precision != "fp64" else tts_max,
             "fp64_comparison": fp64,
